@@ -1,0 +1,218 @@
+/*
+ * hz.h -- C ABI of the GB300 matrix-free multilevel deflation Helmholtz library.
+ *
+ * Problem (Section 2): -Laplace(u) - k(x,y)^2 u = b on a rectangle, discretised by the
+ * second-order 5-point stencil on a vertex-centred grid with uniform spacing h
+ * (Section 2.1, Eq. for [A_h]); Sommerfeld rows eliminate the ghost point
+ * u_0 = u_2 + 2 h i k_1 u_1 (Section 2.1, Sommerfeld ghost equation).
+ * Solver: FGMRES right-preconditioned by the recursive two-level deflation of
+ * Algorithm 1 with the CSLP M = -Laplace - (beta1 + i beta2) k^2 (Section 3.1) and the
+ * MADP schedule of Section 4.4.
+ *
+ * Conventions shared by every entry point:
+ *  - Grids are nx * ny nodes (boundary nodes included for Sommerfeld; interior
+ *    unknowns only for homogeneous Dirichlet), row-major [rhs][y][x], x fastest.
+ *  - Complex vectors are interleaved (re, im): HZ_C128 = 16-byte double2 elements,
+ *    HZ_C64 = 8-byte float2 elements.  Batches of nrhs vectors are contiguous.
+ *  - Vector pointers are DEVICE pointers owned by the caller unless a name ends in
+ *    _host.  The library never frees caller memory; it allocates its own workspace
+ *    in hz_setup and frees it in hz_destroy.
+ *  - All work is ordered on the stream given to hz_setup (a cudaStream_t passed as
+ *    void*, 0 = legacy default stream).  Calls return after enqueueing unless the
+ *    algorithm needs a scalar on the host (the Krylov solvers), in which case they
+ *    synchronise that stream.
+ *  - Every call returns an int status (HZ_OK = 0) and never aborts; hz_strerror()
+ *    names a status and hz_last_error() gives the last detailed message of the
+ *    calling thread.  A handle must not be used by two host threads at once.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define HZ_OK          0
+#define HZ_EINVAL      1   /* invalid argument (size, pointer, level, config value) */
+#define HZ_ENOMEM      2   /* device allocation failed or memory budget exceeded */
+#define HZ_ENOTCONV    3   /* iteration cap reached before the tolerance */
+#define HZ_EBREAKDOWN  4   /* NaN/Inf in a residual or a zero Krylov norm without convergence */
+#define HZ_ETIMEOUT    5   /* a host wait on the device exceeded the configured limit */
+#define HZ_ECUDA       6   /* a CUDA runtime call failed (message in hz_last_error) */
+#define HZ_ENOTSUP     7   /* valid request that this build does not support */
+#define HZ_PENDING     8   /* serving: the request has not finished yet */
+
+/* ---- enumerations ---------------------------------------------------------------- */
+#define HZ_BC_SOMMERFELD 0 /* first-order Sommerfeld rows, ghost equation of Section 2.1 */
+#define HZ_BC_DIRICHLET  1 /* homogeneous Dirichlet; only level-1 operator applies */
+
+#define HZ_PREC_FP64   0   /* every vector and scalar in complex FP64 */
+#define HZ_PREC_MIXED  1   /* preconditioner (lines 5-14 of Algorithm 1) and inner levels in
+                              complex FP32; outer Arnoldi, Hessenberg least squares, true
+                              residual and the multigrid coarsest solve in FP64 */
+
+#define HZ_C128 0          /* complex double, 16 bytes per element */
+#define HZ_C64  1          /* complex float, 8 bytes per element */
+
+#define HZ_OP_A 0          /* Helmholtz operator A_l (shift 1) */
+#define HZ_OP_M 1          /* CSLP operator M_l (shift beta1 + i beta2) */
+
+#define HZ_MAX_LEVELS 10
+
+#define HZ_SOLVE_INITIAL_GUESS 1u  /* hz_solve flag: u holds the initial guess on entry */
+
+typedef struct hz_handle_s* hz_handle;
+
+/* Grid of the finest level (Section 2.1). */
+typedef struct {
+  int nx, ny;   /* nodes per side; Sommerfeld: odd and coarsenable levels-1 times */
+  double h;     /* uniform spacing, > 0 */
+  int bc;       /* HZ_BC_* */
+} hz_grid;
+
+/* Solver configuration.  hz_config_init() fills the paper's MADP defaults; every
+ * field is then taken literally. */
+typedef struct {
+  int levels;            /* ml >= 1 deflation levels (Algorithm 1, "predefined coarsest level") */
+  int precision;         /* HZ_PREC_* */
+  double beta1, beta2;   /* CSLP shift, default (1, 0.5) (Section 4.3) */
+  int restart;           /* outer FGMRES restart length, default 30 */
+  int max_outer;         /* cap on total outer iterations, default 300 */
+  double l2_tol;         /* level-2 deflated FGMRES relative tolerance, default 0.3 (Section 4.4) */
+  int l2_maxit;          /* level-2 iteration cap, default 30 */
+  double cslp_tol;       /* GMRES tolerance of the CSLP inverse on levels > mg_max_level, default 0.1 */
+  double c_it;           /* Krylov cap floor(c_it * N_l^(1/4)), default 6 (Section 4.2) */
+  double coarsest_tol;   /* coarsest-level tolerance when indefinite, default 0.1 (Section 4.1) */
+  int negdef_from_level; /* first level treated as negative definite (coarsest then runs one
+                            iteration); 0 = none */
+  int mg_max_level;      /* CSLP by multigrid V-cycle on levels <= this, default 2 (Section 4.4) */
+  double mg_omega;       /* damped-Jacobi weight, default 0.8 */
+  int mg_nu1, mg_nu2;    /* pre/post smoothing sweeps, default 1 and 1 */
+  int mg_coarsest_side;  /* multigrid coarsening stops at this many nodes per side, default 20 */
+  int max_rhs;           /* largest nrhs any call on this handle will pass, default 1 */
+  double timeout_s;      /* limit for every host wait on the device, default 600 s */
+} hz_config;
+
+/* Per-right-hand-side solve statistics. */
+typedef struct {
+  int status;                                  /* HZ_OK or HZ_ENOTCONV / HZ_EBREAKDOWN */
+  int outer_iterations;                        /* level-1 FGMRES iterations, all cycles */
+  int level_iterations[HZ_MAX_LEVELS];         /* [l-1]: deflated FGMRES iterations on level l */
+  int level_calls[HZ_MAX_LEVELS];              /* [l-1]: number of level-l coarse solves */
+  int cslp_gmres_iterations[HZ_MAX_LEVELS];    /* [l-1]: GMRES iterations of CSLP inverses */
+  double true_relres;                          /* ||b - A_h u|| / ||b|| in FP64 */
+  double est_relres;                           /* last Arnoldi least-squares estimate */
+  double ms;                                   /* wall time of the solve in milliseconds */
+} hz_stats;
+
+/* ---- set-up ------------------------------------------------------------------------ */
+
+/* Fill *cfg with the MADP defaults listed above (levels = 1, precision = HZ_PREC_FP64). */
+int hz_config_init(hz_config* cfg);
+
+/* Build the level hierarchy (Section 3.3): per-level sizes n_l = (n_{l-1} + 1) / 2,
+ * spacing 2^(l-1) h, wavenumber injected at coincident nodes, exact Galerkin coarse
+ * stencils (Section 3.3, Appendix A; 1-D recursion with p = [1,4,6,4,1]/8), multigrid
+ * sub-hierarchies with an FP64 dense coarsest inverse, and all workspace for nrhs <=
+ * cfg->max_rhs.  k_dev: nx*ny real FP64 wavenumbers, device, read during the call only.
+ * stream: cudaStream_t used by every later call on the handle.
+ * Errors: HZ_EINVAL (sizes not coarsenable, h <= 0, non-finite or non-positive k,
+ * bad config), HZ_ENOMEM, HZ_ECUDA. */
+int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, void* stream,
+             hz_handle* out);
+
+/* Release every resource of the handle (synchronises its stream first). */
+int hz_destroy(hz_handle h);
+
+/* Bytes of device memory the handle holds. */
+int hz_memory_bytes(hz_handle h, size_t* bytes);
+
+/* ---- the hot-path calls -------------------------------------------------------------- */
+
+/* y = A_h x on the finest level: Section 2.1, Eq. for [A_h] with Sommerfeld ghost rows
+ * (or homogeneous Dirichlet).  x, y: nrhs * nx * ny HZ_C128, device, must not overlap. */
+int hz_apply(hz_handle h, const void* x, void* y, int nrhs);
+
+/* x = P v, the A-DEF1 preconditioner P = M^-1 (I - A Q) + Q of Section 3.1 applied by
+ * Algorithm 1 lines 5-14 at level 1 (coarse system solved by the recursive schedule).
+ * v, x: nrhs * nx * ny HZ_C128, device.  With levels = 1, x = M^-1 v (multigrid). */
+int hz_precond(hz_handle h, const void* v, void* x, int nrhs);
+
+/* Solve A_h u = b for each of nrhs right-hand sides by FGMRES(restart) preconditioned
+ * with P, to relative residual tol in the 2-norm (Section 4: zero initial guess unless
+ * flags has HZ_SOLVE_INITIAL_GUESS, confirmed by the FP64 true residual).
+ * b, u: HZ_C128 device vectors; stats: nrhs host entries or NULL.
+ * Returns HZ_OK when every right-hand side converged, else the first failing status. */
+int hz_solve(hz_handle h, const void* b, void* u, int nrhs, double tol, unsigned flags,
+             hz_stats* stats);
+
+/* hz_solve with HOST buffers: copies b to the device, solves, copies u back (all on
+ * the handle's stream).  b_host, u_host: nrhs * nx * ny complex double, host memory. */
+int hz_solve_host(hz_handle h, const double* b_host, double* u_host, int nrhs, double tol,
+                  unsigned flags, hz_stats* stats);
+
+/* ---- building blocks (each one step of the hot path; used by the parity tests) ---- */
+
+/* Grid size of deflation level l (1-based): *nx, *ny. */
+int hz_level_size(hz_handle h, int level, int* nx, int* ny);
+
+/* y = A_l x (op = HZ_OP_A) or M_l x (HZ_OP_M) on deflation level l.  Level 1: the
+ * 5-point rows of Section 2.1; level >= 2: the re-discretised Galerkin stencils of
+ * Section 3.3 with the boundary treatment of its "Boundary" paragraph.  dtype: HZ_C128
+ * or HZ_C64 for both x and y (the arithmetic follows the dtype). */
+int hz_level_apply(hz_handle h, int level, int op, int dtype, const void* x, void* y, int nrhs);
+
+/* One damped-Jacobi sweep with M_l (multigrid smoother of the CSLP inverse, Section 3.2):
+ * u_out = u + omega (f - M_l u) / diag(M_l).  u, f, u_out: dtype vectors on level l. */
+int hz_level_jacobi(hz_handle h, int level, int dtype, const void* u, const void* f,
+                    void* u_out, int nrhs);
+
+/* Deflation restriction v_hat = Z^T v from level l to level l+1 (Algorithm 1 line 5). */
+int hz_defl_restrict(hz_handle h, int level, int dtype, const void* v, void* vhat, int nrhs);
+
+/* Deflation prolongation t = Z w from level l+1 to level l (Algorithm 1 line 11). */
+int hz_defl_prolong(hz_handle h, int level, int dtype, const void* w, void* t, int nrhs);
+
+/* Fused Algorithm 1 lines 11-13 at level l: t = Z v_til, r_til = v - A_l t.
+ * v_til on level l+1; v, t, r_til on level l; all dtype.  t may be NULL. */
+int hz_defl_prolong_residual(hz_handle h, int level, int dtype, const void* vtil,
+                             const void* v, void* t, void* rtil, int nrhs);
+
+/* One multigrid V-cycle approximating M_l^-1 f on level l <= mg_max_level, zero
+ * initial guess (Section 3.2, CSLP by multigrid).  f, u: dtype vectors on level l. */
+int hz_mg_vcycle(hz_handle h, int level, int dtype, const void* f, void* u, int nrhs);
+
+/* Number of multigrid levels of the level-l CSLP hierarchy and the size of MG level m. */
+int hz_mg_size(hz_handle h, int level, int mg_level, int* nx, int* ny);
+
+/* CSLP inverse by unpreconditioned GMRES on M_l to relative tolerance cfg.cslp_tol,
+ * at most floor(c_it * N_l^(1/4)) iterations (Section 4.2), zero initial guess.
+ * b, x: dtype vectors on level l; iterations (host, nrhs entries) may be NULL. */
+int hz_cslp_gmres(hz_handle h, int level, int dtype, const void* b, void* x, int nrhs,
+                  int* iterations);
+
+/* ---- diagnostics ------------------------------------------------------------------- */
+
+/* Name of a status code. */
+const char* hz_strerror(int status);
+
+/* Last detailed error message of the calling thread ("" if none). */
+const char* hz_last_error(void);
+
+/* Per-kernel timing with CUDA events on the handle's stream: enable records an event
+ * pair around every launch of the kernel family `family` (see hz_kernel_family_name);
+ * read returns the number of launches, their summed milliseconds and their summed
+ * algorithmic bytes since enable.  Reading synchronises the stream. */
+int hz_profile_enable(hz_handle h, int family, int enable);
+int hz_profile_read(hz_handle h, int family, long long* launches, double* ms, double* bytes);
+const char* hz_kernel_family_name(int family);
+int hz_kernel_family_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H */

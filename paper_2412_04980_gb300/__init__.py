@@ -1,0 +1,349 @@
+"""GB300 matrix-free multilevel deflation Helmholtz solver: Python binding.
+
+Thin ctypes layer over the C ABI in ``include/hz.h`` (``libhz.so``, built in-tree by
+``paper_2412_04980_gb300.build``).  Functions keep the C names (``hz_setup``,
+``hz_apply``, ``hz_precond``, ``hz_solve`` ...); :class:`Helmholtz` wraps a handle for
+torch CUDA tensors.  Every numerical step runs in the library's CUDA kernels; this module
+only marshals pointers, sizes and streams.  There is no CPU fallback: if the library is
+missing, importing the symbols raises.
+
+Vectors are complex tensors on the GPU, shaped (nrhs, ny, nx) or (ny, nx), C-contiguous
+(x fastest), dtype complex128 or complex64 as each call states.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+__all__ = [
+    "HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ENOTCONV", "HZ_EBREAKDOWN", "HZ_ETIMEOUT", "HZ_ECUDA",
+    "HZ_ENOTSUP", "HZ_PENDING", "HZ_BC_SOMMERFELD", "HZ_BC_DIRICHLET", "HZ_PREC_FP64", "HZ_PREC_MIXED",
+    "HZ_C128", "HZ_C64", "HZ_OP_A", "HZ_OP_M", "HzGrid", "HzConfig", "HzStats", "HzError", "lib",
+    "library_path", "Helmholtz",
+]
+
+HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ENOTCONV, HZ_EBREAKDOWN, HZ_ETIMEOUT, HZ_ECUDA, HZ_ENOTSUP, HZ_PENDING = range(9)
+HZ_BC_SOMMERFELD, HZ_BC_DIRICHLET = 0, 1
+HZ_PREC_FP64, HZ_PREC_MIXED = 0, 1
+HZ_C128, HZ_C64 = 0, 1
+HZ_OP_A, HZ_OP_M = 0, 1
+HZ_MAX_LEVELS = 10
+HZ_SOLVE_INITIAL_GUESS = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libhz.so")
+
+
+class HzGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("h", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
+class HzConfig(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int), ("precision", ctypes.c_int), ("beta1", ctypes.c_double),
+        ("beta2", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
+        ("l2_tol", ctypes.c_double), ("l2_maxit", ctypes.c_int), ("cslp_tol", ctypes.c_double),
+        ("c_it", ctypes.c_double), ("coarsest_tol", ctypes.c_double), ("negdef_from_level", ctypes.c_int),
+        ("mg_max_level", ctypes.c_int), ("mg_omega", ctypes.c_double), ("mg_nu1", ctypes.c_int),
+        ("mg_nu2", ctypes.c_int), ("mg_coarsest_side", ctypes.c_int), ("max_rhs", ctypes.c_int),
+        ("timeout_s", ctypes.c_double),
+    ]
+
+
+class HzStats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+        ("level_iterations", ctypes.c_int * HZ_MAX_LEVELS), ("level_calls", ctypes.c_int * HZ_MAX_LEVELS),
+        ("cslp_gmres_iterations", ctypes.c_int * HZ_MAX_LEVELS), ("true_relres", ctypes.c_double),
+        ("est_relres", ctypes.c_double), ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {
+            "status": self.status, "outer_iterations": self.outer_iterations,
+            "level_iterations": list(self.level_iterations), "level_calls": list(self.level_calls),
+            "cslp_gmres_iterations": list(self.cslp_gmres_iterations), "true_relres": self.true_relres,
+            "est_relres": self.est_relres, "ms": self.ms,
+        }
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+_P, _I, _D, _U = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
+_SIGS = {
+    "hz_config_init": (_I, [ctypes.POINTER(HzConfig)]),
+    "hz_setup": (_I, [ctypes.POINTER(HzGrid), _P, ctypes.POINTER(HzConfig), _P, ctypes.POINTER(_P)]),
+    "hz_destroy": (_I, [_P]),
+    "hz_memory_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "hz_apply": (_I, [_P, _P, _P, _I]),
+    "hz_precond": (_I, [_P, _P, _P, _I]),
+    "hz_solve": (_I, [_P, _P, _P, _I, _D, _U, ctypes.POINTER(HzStats)]),
+    "hz_solve_host": (_I, [_P, _P, _P, _I, _D, _U, ctypes.POINTER(HzStats)]),
+    "hz_level_size": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "hz_level_apply": (_I, [_P, _I, _I, _I, _P, _P, _I]),
+    "hz_level_jacobi": (_I, [_P, _I, _I, _P, _P, _P, _I]),
+    "hz_defl_restrict": (_I, [_P, _I, _I, _P, _P, _I]),
+    "hz_defl_prolong": (_I, [_P, _I, _I, _P, _P, _I]),
+    "hz_defl_prolong_residual": (_I, [_P, _I, _I, _P, _P, _P, _P, _I]),
+    "hz_mg_vcycle": (_I, [_P, _I, _I, _P, _P, _I]),
+    "hz_mg_size": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "hz_cslp_gmres": (_I, [_P, _I, _I, _P, _P, _I, ctypes.POINTER(_I)]),
+    "hz_strerror": (ctypes.c_char_p, [_I]),
+    "hz_last_error": (ctypes.c_char_p, []),
+    "hz_profile_enable": (_I, [_P, _I, _I]),
+    "hz_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                             ctypes.POINTER(_D)]),
+    "hz_kernel_family_name": (ctypes.c_char_p, [_I]),
+    "hz_kernel_family_count": (_I, []),
+}
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libhz.so`` (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, where: str):
+    if status != HZ_OK:
+        L = lib()
+        raise HzError(status, where, f"{L.hz_strerror(status).decode()}; {L.hz_last_error().decode()}")
+
+
+def __getattr__(name):
+    # hz_* names resolve to the C functions of the loaded library
+    if name.startswith("hz_") and name in _SIGS:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def config(**kw) -> HzConfig:
+    """An HzConfig with the paper's defaults (hz_config_init) updated by keyword fields."""
+    c = HzConfig()
+    _check(lib().hz_config_init(ctypes.byref(c)), "hz_config_init")
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+@dataclass
+class SolveResult:
+    stats: list
+
+
+class Helmholtz:
+    """One Helmholtz instance (grid, wavenumber field, configuration) on the current device.
+
+    ``k`` is a real float64 CUDA tensor of shape (ny, nx).  Keyword arguments set
+    :class:`HzConfig` fields (``levels``, ``precision`` ('fp64' / 'mixed'), ``max_rhs`` ...).
+    """
+
+    def __init__(self, k, h: float, bc: str = "sommerfeld", stream=None, **cfg):
+        import torch
+        if not (k.is_cuda and k.dtype == torch.float64 and k.dim() == 2 and k.is_contiguous()):
+            raise ValueError("k must be a contiguous 2-D float64 CUDA tensor")
+        self.ny, self.nx = int(k.shape[0]), int(k.shape[1])
+        prec = cfg.pop("precision", "fp64")
+        cfg["precision"] = {"fp64": HZ_PREC_FP64, "mixed": HZ_PREC_MIXED}.get(prec, prec)
+        self.cfg = config(**cfg)
+        self.grid = HzGrid(self.nx, self.ny, float(h), HZ_BC_SOMMERFELD if bc == "sommerfeld" else HZ_BC_DIRICHLET)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(k.device)
+        self._h = ctypes.c_void_p()
+        _check(lib().hz_setup(ctypes.byref(self.grid), _ptr(k), ctypes.byref(self.cfg),
+                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)), "hz_setup")
+        self.device = k.device
+
+    def close(self):
+        if self._h:
+            lib().hz_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ---------------------------------------------------------------------
+    @staticmethod
+    def _nrhs(t, ny, nx):
+        if not t.is_contiguous():
+            raise ValueError("vectors must be contiguous")
+        if t.dim() == 2:
+            n = 1
+        elif t.dim() == 3:
+            n = int(t.shape[0])
+        else:
+            raise ValueError("vectors must be (ny, nx) or (nrhs, ny, nx)")
+        if tuple(t.shape[-2:]) != (ny, nx):
+            raise ValueError(f"vector shape {tuple(t.shape)} does not match grid ({ny}, {nx})")
+        return n
+
+    def level_size(self, level: int):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        _check(lib().hz_level_size(self._h, level, ctypes.byref(nx), ctypes.byref(ny)), "hz_level_size")
+        return ny.value, nx.value
+
+    def mg_size(self, level: int, mg_level: int):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        _check(lib().hz_mg_size(self._h, level, mg_level, ctypes.byref(nx), ctypes.byref(ny)), "hz_mg_size")
+        return ny.value, nx.value
+
+    def memory_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().hz_memory_bytes(self._h, ctypes.byref(b)), "hz_memory_bytes")
+        return b.value
+
+    @staticmethod
+    def _dt(t):
+        import torch
+        if t.dtype == torch.complex128:
+            return HZ_C128
+        if t.dtype == torch.complex64:
+            return HZ_C64
+        raise ValueError("complex128 or complex64 expected")
+
+    # -- the hot-path calls ------------------------------------------------------------
+    def apply(self, x, y=None):
+        """y = A_h x (complex128)."""
+        import torch
+        n = self._nrhs(x, self.ny, self.nx)
+        y = torch.empty_like(x) if y is None else y
+        _check(lib().hz_apply(self._h, _ptr(x), _ptr(y), n), "hz_apply")
+        return y
+
+    def precond(self, v, x=None):
+        """x = P v, the A-DEF1 multilevel preconditioner (complex128)."""
+        import torch
+        n = self._nrhs(v, self.ny, self.nx)
+        x = torch.empty_like(v) if x is None else x
+        _check(lib().hz_precond(self._h, _ptr(v), _ptr(x), n), "hz_precond")
+        return x
+
+    def solve(self, b, u=None, tol: float = 1e-6, initial_guess: bool = False, check: bool = True):
+        """Solve A_h u = b (complex128); returns (u, [stats dict per rhs])."""
+        import torch
+        n = self._nrhs(b, self.ny, self.nx)
+        u = torch.empty_like(b) if u is None else u
+        stats = (HzStats * n)()
+        st = lib().hz_solve(self._h, _ptr(b), _ptr(u), n, float(tol),
+                            HZ_SOLVE_INITIAL_GUESS if initial_guess else 0, stats)
+        if check and st not in (HZ_OK,):
+            _check(st, "hz_solve")
+        return u, [s.as_dict() for s in stats]
+
+    def solve_host(self, b_np, tol: float = 1e-6):
+        """hz_solve_host on numpy complex128 arrays; returns (u_np, stats)."""
+        import numpy as np
+        b = np.ascontiguousarray(b_np, dtype=np.complex128)
+        n = 1 if b.ndim == 2 else b.shape[0]
+        u = np.empty_like(b)
+        stats = (HzStats * n)()
+        _check(lib().hz_solve_host(self._h, b.ctypes.data, u.ctypes.data, n, float(tol), 0, stats), "hz_solve_host")
+        return u, [s.as_dict() for s in stats]
+
+    # -- building blocks -----------------------------------------------------------------
+    def level_apply(self, level: int, x, op: str = "A", y=None):
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(x, ny, nx)
+        y = torch.empty_like(x) if y is None else y
+        _check(lib().hz_level_apply(self._h, level, HZ_OP_A if op == "A" else HZ_OP_M, self._dt(x), _ptr(x),
+                                    _ptr(y), n), "hz_level_apply")
+        return y
+
+    def level_jacobi(self, level: int, u, f, out=None):
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(u, ny, nx)
+        out = torch.empty_like(u) if out is None else out
+        _check(lib().hz_level_jacobi(self._h, level, self._dt(u), _ptr(u), _ptr(f), _ptr(out), n),
+               "hz_level_jacobi")
+        return out
+
+    def defl_restrict(self, level: int, v):
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(v, ny, nx)
+        cy, cx = (ny + 1) // 2, (nx + 1) // 2
+        out = torch.empty((n, cy, cx) if v.dim() == 3 else (cy, cx), dtype=v.dtype, device=v.device)
+        _check(lib().hz_defl_restrict(self._h, level, self._dt(v), _ptr(v), _ptr(out), n), "hz_defl_restrict")
+        return out
+
+    def defl_prolong(self, level: int, w):
+        import torch
+        ny, nx = self.level_size(level)
+        cy, cx = (ny + 1) // 2, (nx + 1) // 2
+        n = self._nrhs(w, cy, cx)
+        out = torch.empty((n, ny, nx) if w.dim() == 3 else (ny, nx), dtype=w.dtype, device=w.device)
+        _check(lib().hz_defl_prolong(self._h, level, self._dt(w), _ptr(w), _ptr(out), n), "hz_defl_prolong")
+        return out
+
+    def defl_prolong_residual(self, level: int, vtil, v):
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(v, ny, nx)
+        t = torch.empty_like(v)
+        r = torch.empty_like(v)
+        _check(lib().hz_defl_prolong_residual(self._h, level, self._dt(v), _ptr(vtil), _ptr(v), _ptr(t), _ptr(r),
+                                              n), "hz_defl_prolong_residual")
+        return t, r
+
+    def mg_vcycle(self, level: int, f):
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(f, ny, nx)
+        u = torch.empty_like(f)
+        _check(lib().hz_mg_vcycle(self._h, level, self._dt(f), _ptr(f), _ptr(u), n), "hz_mg_vcycle")
+        return u
+
+    def cslp_gmres(self, level: int, b):
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(b, ny, nx)
+        x = torch.empty_like(b)
+        its = (ctypes.c_int * n)()
+        _check(lib().hz_cslp_gmres(self._h, level, self._dt(b), _ptr(b), _ptr(x), n, its), "hz_cslp_gmres")
+        return x, list(its)
+
+    # -- per-kernel timing ----------------------------------------------------------------
+    @staticmethod
+    def kernel_families():
+        L = lib()
+        return [L.hz_kernel_family_name(i).decode() for i in range(L.hz_kernel_family_count())]
+
+    def profile_enable(self, family: int, on: bool = True):
+        _check(lib().hz_profile_enable(self._h, family, 1 if on else 0), "hz_profile_enable")
+
+    def profile_read(self, family: int):
+        n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().hz_profile_read(self._h, family, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
+               "hz_profile_read")
+        return n.value, ms.value, by.value

@@ -1,0 +1,821 @@
+// Host runtime of the library: hierarchy set-up, workspace, and the solver drivers of
+// Algorithm 1 (recursive deflated FGMRES with the MADP schedule of Section 4.4).
+//
+// Every vector operation runs in the CUDA kernels of kern_stencil.cu / kern_vec.cu.  The
+// host holds only scalars: the Hessenberg matrices of the Krylov cycles, their Givens
+// rotations and least-squares solutions (Algorithm 1 line 22), and the stopping tests.
+// A batch of nb right-hand sides advances in lockstep; each right-hand side keeps its own
+// Hessenberg matrix, stopping iteration and solution, so its result does not depend on
+// the rest of the batch.
+#include "hz_core.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <thread>
+
+namespace hz {
+
+// ---------------------------------------------------------------------------------- errors
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+const char* last_error_message() { return g_err.c_str(); }
+
+int status_of(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return HZ_OK;
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? HZ_ENOMEM : HZ_ECUDA;
+}
+
+#define CK(expr)                                          \
+  do {                                                    \
+    int s_ = ::hz::status_of((expr), #expr);              \
+    if (s_) return s_;                                    \
+  } while (0)
+#define CS(expr)          \
+  do {                    \
+    int s_ = (expr);      \
+    if (s_) return s_;    \
+  } while (0)
+
+static const char* kFamilies[F_COUNT] = {"level_op",  "mg_down", "mg_up",  "defl_restrict", "defl_prolong",
+                                         "multidot",  "axpy",    "reduce", "dense",         "misc"};
+const char* family_name(int f) { return (f >= 0 && f < F_COUNT) ? kFamilies[f] : "?"; }
+
+// ---------------------------------------------------------------------------------- profiler
+cudaEvent_t Prof::get() {
+  if (pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = pool.back();
+  pool.pop_back();
+  return e;
+}
+void Prof::drain(int fam) {
+  for (auto& r : pending[fam]) {
+    float ms_ = 0;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms_, r.a, r.b) == cudaSuccess) {
+      ms[fam] += ms_;
+      launches[fam] += 1;
+      bytes[fam] += r.bytes;
+    }
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  pending[fam].clear();
+}
+Prof::~Prof() {
+  for (int f = 0; f < F_COUNT; ++f)
+    for (auto& r : pending[f]) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+ProfScope::ProfScope(Ctx& c_, int fam_, double bytes_) : c(c_), fam(fam_), bytes(bytes_) {
+  if (c.prof && c.prof->on[fam]) {
+    a = c.prof->get();
+    if (a) cudaEventRecord(a, c.s);
+  }
+}
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEvent_t b = c.prof->get();
+  if (!b) return;
+  cudaEventRecord(b, c.s);
+  c.prof->pending[fam].push_back({a, b, bytes});
+  if (c.prof->pending[fam].size() > 8192) c.prof->drain(fam);
+}
+
+// ---------------------------------------------------------------------------------- helpers
+int dalloc(Handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HZ_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    *p = nullptr;
+    return HZ_ENOMEM;
+  }
+  h->allocs.push_back(*p);
+  h->bytes += bytes;
+  return HZ_OK;
+}
+
+int wait_event(Handle* h, cudaEvent_t ev) {
+  CK(cudaEventRecord(ev, h->ctx.s));
+  auto t0 = std::chrono::steady_clock::now();
+  long spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return HZ_OK;
+    if (e != cudaErrorNotReady) return status_of(e, "cudaEventQuery");
+    if (++spins > 2000) {
+      std::this_thread::yield();
+      double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (s > h->cfg.timeout_s) {
+        set_error("device wait exceeded the configured timeout");
+        return HZ_ETIMEOUT;
+      }
+    }
+  }
+}
+
+static int krylov_cap(double c_it, size_t nodes) { return (int)std::floor(c_it * std::pow((double)nodes, 0.25)); }
+
+OpDesc Level::opA(int dt) const {
+  OpDesc d;
+  d.nx = nx;
+  d.ny = ny;
+  d.R = R;
+  d.bc = 0;
+  d.H = H;
+  d.ks = ks;
+  d.c = ks / (H * H);  // = 1 / h^2 on every level (Galerkin scale 4^(l-1) over H_l^2)
+  d.sr = 1;
+  d.si = 0;
+  for (int i = 0; i < 7; ++i) {
+    d.m[i] = m[i];
+    d.l[i] = L[i];
+  }
+  d.k_d = k_d;
+  d.k_f = k_f;
+  (void)dt;
+  return d;
+}
+OpDesc Level::opM(int dt, double b1, double b2) const {
+  OpDesc d = opA(dt);
+  d.sr = b1;
+  d.si = b2;
+  return d;
+}
+
+static int alloc_scalars(Handle* h, Scalars& s, int cap, int nb) {
+  s.hA = 0;
+  size_t per = (size_t)nb * 2 * (cap + 1);
+  s.hB = per;
+  s.nrm = 2 * per;
+  s.csc = s.nrm + nb;
+  s.ccomb = s.csc + 2 * (size_t)nb;
+  s.total = s.ccomb + (size_t)nb * 2 * (cap + 1);
+  void* p;
+  CS(dalloc(h, &p, s.total * sizeof(double)));
+  s.dev = reinterpret_cast<double*>(p);
+  CK(cudaMallocHost((void**)&s.host, s.total * sizeof(double)));
+  CK(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+  return HZ_OK;
+}
+
+static void free_scalars(Scalars& s) {
+  if (s.host) cudaFreeHost(s.host);
+  if (s.ev) cudaEventDestroy(s.ev);
+  s.host = nullptr;
+  s.ev = nullptr;
+}
+
+// Gauss-Jordan inverse with partial pivoting (row-major n x n, in place).
+static bool invert(std::vector<cd>& A, int n) {
+  std::vector<cd> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = std::abs(A[(size_t)c * n + c]);
+    for (int r = c + 1; r < n; ++r)
+      if (std::abs(A[(size_t)r * n + c]) > best) {
+        best = std::abs(A[(size_t)r * n + c]);
+        p = r;
+      }
+    if (!(best > 0)) return false;
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)p * n + k], A[(size_t)c * n + k]);
+        std::swap(I[(size_t)p * n + k], I[(size_t)c * n + k]);
+      }
+    cd piv = 1.0 / A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] *= piv;
+      I[(size_t)c * n + k] *= piv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      cd f = A[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+        I[(size_t)r * n + k] -= f * I[(size_t)c * n + k];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// Dense inverse of a grid operator: columns from the FP64 level kernel applied to unit vectors.
+static int dense_inverse(Handle* h, const OpDesc& op, double** inv_out) {
+  const int N = (int)op.n();
+  if (N > 2048) {
+    set_error("multigrid coarsest grid has " + std::to_string(N) + " unknowns (limit 2048)");
+    return HZ_ENOTSUP;
+  }
+  size_t bytes = (size_t)N * N * 16;
+  void *E = nullptr, *Y = nullptr;
+  CK(cudaMalloc(&E, bytes));
+  if (cudaMalloc(&Y, bytes) != cudaSuccess) {
+    cudaFree(E);
+    return status_of(cudaErrorMemoryAllocation, "dense_inverse");
+  }
+  std::vector<cd> hostE((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i) hostE[(size_t)i * N + i] = 1.0;
+  int st = HZ_OK;
+  cudaError_t e = cudaMemcpyAsync(E, hostE.data(), bytes, cudaMemcpyHostToDevice, h->ctx.s);
+  if (e == cudaSuccess) e = launch_level_op(h->ctx, op, 0, C128, C128, C128, E, nullptr, Y, 0.0, N);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hostE.data(), Y, bytes, cudaMemcpyDeviceToHost, h->ctx.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->ctx.s);
+  cudaFree(E);
+  cudaFree(Y);
+  if (e != cudaSuccess) return status_of(e, "dense_inverse");
+  std::vector<cd> A((size_t)N * N);
+  for (int c = 0; c < N; ++c)
+    for (int r = 0; r < N; ++r) A[(size_t)r * N + c] = hostE[(size_t)c * N + r];
+  if (!invert(A, N)) {
+    set_error("singular multigrid coarsest operator");
+    return HZ_EBREAKDOWN;
+  }
+  void* p;
+  CS(dalloc(h, &p, bytes));
+  CK(cudaMemcpyAsync(p, A.data(), bytes, cudaMemcpyHostToDevice, h->ctx.s));
+  CK(cudaStreamSynchronize(h->ctx.s));
+  *inv_out = reinterpret_cast<double*>(p);
+  (void)st;
+  return HZ_OK;
+}
+
+static int upload_k(Handle* h, const std::vector<double>& k, double** kd, float** kf) {
+  void* p;
+  CS(dalloc(h, &p, k.size() * 8));
+  *kd = reinterpret_cast<double*>(p);
+  CK(cudaMemcpyAsync(p, k.data(), k.size() * 8, cudaMemcpyHostToDevice, h->ctx.s));
+  std::vector<float> kf32(k.size());
+  for (size_t i = 0; i < k.size(); ++i) kf32[i] = (float)k[i];
+  CS(dalloc(h, &p, k.size() * 4));
+  *kf = reinterpret_cast<float*>(p);
+  CK(cudaMemcpyAsync(p, kf32.data(), k.size() * 4, cudaMemcpyHostToDevice, h->ctx.s));
+  CK(cudaStreamSynchronize(h->ctx.s));
+  return HZ_OK;
+}
+
+static std::vector<double> inject(const std::vector<double>& k, int nx, int ny) {
+  int cx = (nx + 1) / 2, cy = (ny + 1) / 2;
+  std::vector<double> out((size_t)cx * cy);
+  for (int j = 0; j < cy; ++j)
+    for (int i = 0; i < cx; ++i) out[(size_t)j * cx + i] = k[(size_t)(2 * j) * nx + 2 * i];
+  return out;
+}
+
+// ---------------------------------------------------------------------------------- set-up
+int setup(Handle* h, const double* k_dev) {
+  const hz_grid& g = h->g;
+  hz_config& cfg = h->cfg;
+  const int ml = cfg.levels;
+  h->nbmax = cfg.max_rhs;
+  const int nb = h->nbmax;
+  const bool mixed = cfg.precision == HZ_PREC_MIXED;
+  // host copy of k, validated
+  std::vector<double> k((size_t)g.nx * g.ny);
+  CK(cudaMemcpy(k.data(), k_dev, k.size() * 8, cudaMemcpyDeviceToHost));
+  for (double v : k)
+    if (!(std::isfinite(v) && v > 0)) {
+      set_error("wavenumber field must be finite and positive");
+      return HZ_EINVAL;
+    }
+  h->lv.resize(ml);
+  int nx = g.nx, ny = g.ny;
+  std::vector<double> kl = k;
+  for (int l = 1; l <= ml; ++l) {
+    Level& L = h->lv[l - 1];
+    L.l = l;
+    L.nx = nx;
+    L.ny = ny;
+    L.n = (size_t)nx * ny;
+    L.H = std::ldexp(g.h, l - 1);
+    L.ks = std::ldexp(1.0, 2 * (l - 1));
+    galerkin_masks(l, &L.R, L.m, L.L);
+    CS(upload_k(h, kl, &L.k_d, &L.k_f));
+    if (l == 1) {
+      L.dvec = C128;
+      L.dpre = mixed ? C64 : C128;
+      L.dx = L.dpre;
+    } else {
+      L.dvec = L.dpre = L.dx = mixed ? C64 : C128;
+    }
+    if (l < ml) {
+      kl = inject(kl, nx, ny);
+      nx = (nx + 1) / 2;
+      ny = (ny + 1) / 2;
+    }
+  }
+  // per-level workspace
+  size_t maxnv = 2;
+  for (int l = 1; l <= ml; ++l) {
+    Level& L = h->lv[l - 1];
+    const size_t eb = elem_bytes(L.dvec), ep = elem_bytes(L.dpre), ex = elem_bytes(L.dx);
+    const size_t bn = (size_t)nb * L.n;
+    if (l == 1) {
+      L.cap = cfg.restart;
+    } else if (l == ml) {
+      bool negdef = cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level;
+      L.cap = negdef ? 1 : krylov_cap(cfg.c_it, L.n);
+    } else {
+      L.cap = (l == 2) ? cfg.l2_maxit : 1;
+    }
+    if (L.cap < 1) L.cap = 1;
+    maxnv = std::max(maxnv, (size_t)L.cap + 1);
+    CS(dalloc(h, &L.V, (L.cap + 1) * bn * eb));
+    CS(dalloc(h, &L.X, L.cap * bn * ex));
+    CS(dalloc(h, &L.w, bn * eb));
+    CS(dalloc(h, &L.t, bn * ep));
+    CS(dalloc(h, &L.rt, bn * ep));
+    CS(dalloc(h, &L.r, bn * ep));
+    if (l >= 2) {
+      CS(dalloc(h, &L.b, bn * eb));
+      CS(dalloc(h, &L.x, bn * eb));
+    }
+    CS(alloc_scalars(h, L.sc, L.cap, nb));
+    if (l <= cfg.mg_max_level) {
+      // multigrid CSLP hierarchy (level 0 = this deflation level)
+      MGLevel m0;
+      m0.op = L.opM(L.dpre, cfg.beta1, cfg.beta2);
+      L.mg.push_back(m0);
+      std::vector<double> km = kl;  // placeholder, recomputed below
+      // wavenumber of this level on the host again (inject from fine k)
+      km = k;
+      {
+        int fx = g.nx, fy = g.ny;
+        for (int q = 1; q < l; ++q) {
+          km = inject(km, fx, fy);
+          fx = (fx + 1) / 2;
+          fy = (fy + 1) / 2;
+        }
+      }
+      int mx = L.nx, my = L.ny;
+      double Hm = L.H;
+      const bool general = !(cfg.mg_nu1 == 1 && cfg.mg_nu2 == 1);
+      for (;;) {
+        if (std::min(mx, my) <= cfg.mg_coarsest_side || (mx - 1) % 2 || (my - 1) % 2 || std::min(mx, my) < 5) break;
+        km = inject(km, mx, my);
+        mx = (mx + 1) / 2;
+        my = (my + 1) / 2;
+        Hm *= 2.0;
+        MGLevel q;
+        q.op.nx = mx;
+        q.op.ny = my;
+        q.op.R = 1;
+        q.op.bc = 0;
+        q.op.c = L.ks / (Hm * Hm);
+        q.op.H = Hm;
+        q.op.ks = L.ks;
+        q.op.sr = cfg.beta1;
+        q.op.si = cfg.beta2;
+        double* kd;
+        float* kf;
+        CS(upload_k(h, km, &kd, &kf));
+        q.op.k_d = kd;
+        q.op.k_f = kf;
+        CS(dalloc(h, &q.f, (size_t)nb * mx * my * ep));
+        CS(dalloc(h, &q.e, (size_t)nb * mx * my * ep));
+        L.mg.push_back(q);
+      }
+      if (general)
+        for (auto& q : L.mg) {
+          CS(dalloc(h, &q.tmp, (size_t)nb * q.op.n() * ep));
+          CS(dalloc(h, &q.tmp2, (size_t)nb * q.op.n() * ep));
+        }
+      OpDesc last = L.mg.back().op;
+      L.ninv = (int)last.n();
+      CS(dense_inverse(h, last, &L.inv));
+    } else {
+      L.capg = std::max(1, krylov_cap(cfg.c_it, L.n));
+      maxnv = std::max(maxnv, (size_t)L.capg + 1);
+      CS(dalloc(h, &L.Vg, (L.capg + 1) * bn * ep));
+      CS(dalloc(h, &L.wg, bn * ep));
+      CS(alloc_scalars(h, L.scg, L.capg, nb));
+    }
+  }
+  h->ws_bytes = dot_ws_bytes((int)maxnv, nb);
+  CS(dalloc(h, &h->ws, h->ws_bytes));
+  CS(alloc_scalars(h, h->outer_sc, 1, nb));
+  CS(dalloc(h, &h->rres, (size_t)nb * h->lv[0].n * 16));
+  h->st.assign(nb, RhsStats());
+  CK(cudaStreamSynchronize(h->ctx.s));
+  return HZ_OK;
+}
+
+void destroy(Handle* h) {
+  cudaStreamSynchronize(h->ctx.s);
+  for (auto& L : h->lv) {
+    free_scalars(L.sc);
+    free_scalars(L.scg);
+  }
+  free_scalars(h->outer_sc);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+// ---------------------------------------------------------------------------------- V-cycle
+// One V(nu1, nu2) cycle approximating M_l^-1 f (zero initial guess); out = cycle [+ add].
+int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, int nb) {
+  Level& L = h->lv[l - 1];
+  Ctx& c = h->ctx;
+  const double om = h->cfg.mg_omega;
+  const int nm = (int)L.mg.size();
+  if (dt != L.dpre) {
+    set_error("multigrid dtype differs from the handle's preconditioner dtype");
+    return HZ_EINVAL;
+  }
+  const size_t eb = elem_bytes(dt);
+  if (nm == 1) {  // the level itself is the coarsest: exact dense solve
+    if (add) {
+      CK(launch_dense(c, L.inv, L.ninv, dt, f, L.r, nb));
+      CK(launch_add(c, dt, L.r, dt, add, dt, out, (size_t)nb * L.n));
+    } else {
+      CK(launch_dense(c, L.inv, L.ninv, dt, f, out, nb));
+    }
+    return HZ_OK;
+  }
+  if (h->cfg.mg_nu1 == 1 && h->cfg.mg_nu2 == 1) {
+    const void* fm = f;
+    for (int m = 0; m + 1 < nm; ++m) {
+      CK(launch_mg_down(c, L.mg[m].op, dt, fm, L.mg[m + 1].f, om, nb));
+      fm = L.mg[m + 1].f;
+    }
+    CK(launch_dense(c, L.inv, L.ninv, dt, L.mg[nm - 1].f, L.mg[nm - 1].e, nb));
+    for (int m = nm - 2; m >= 0; --m) {
+      const void* fmm = (m == 0) ? f : L.mg[m].f;
+      void* y = (m == 0) ? out : L.mg[m].e;
+      CK(launch_mg_up(c, L.mg[m].op, dt, fmm, L.mg[m + 1].e, y, om, m == 0 ? add : nullptr, dt, nullptr, dt, nb));
+    }
+    return HZ_OK;
+  }
+  // general V(nu1, nu2): explicit sweeps with ping-pong buffers
+  std::function<int(int, const void*, void*)> rec = [&](int m, const void* fm, void* um) -> int {
+    MGLevel& q = L.mg[m];
+    const size_t nn = (size_t)nb * q.op.n();
+    if (m == nm - 1) {
+      CK(launch_dense(c, L.inv, L.ninv, dt, fm, um, nb));
+      return HZ_OK;
+    }
+    void* a = um;
+    void* b = q.tmp2;
+    if (h->cfg.mg_nu1 >= 1) {
+      CK(launch_jacobi_zero(c, q.op, dt, fm, a, om, nb));
+      for (int s = 1; s < h->cfg.mg_nu1; ++s) {
+        CK(launch_level_op(c, q.op, 2, dt, dt, dt, a, fm, b, om, nb));
+        std::swap(a, b);
+      }
+    } else {
+      CK(cudaMemsetAsync(a, 0, nn * eb, c.s));
+    }
+    CK(launch_level_op(c, q.op, 1, dt, dt, dt, a, fm, q.tmp, 0.0, nb));
+    CK(launch_fw(c, dt, q.op.nx, q.op.ny, q.tmp, L.mg[m + 1].f, nb));
+    CS(rec(m + 1, L.mg[m + 1].f, L.mg[m + 1].e));
+    CK(launch_prolong_add(c, dt, q.op.nx, q.op.ny, L.mg[m + 1].e, a, nb));
+    for (int s = 0; s < h->cfg.mg_nu2; ++s) {
+      CK(launch_level_op(c, q.op, 2, dt, dt, dt, a, fm, b, om, nb));
+      std::swap(a, b);
+    }
+    if (a != um) CK(cudaMemcpyAsync(um, a, nn * eb, cudaMemcpyDeviceToDevice, c.s));
+    return HZ_OK;
+  };
+  void* target = add ? L.r : out;
+  CS(rec(0, f, target));
+  if (add) CK(launch_add(c, dt, L.r, dt, add, dt, out, (size_t)nb * L.n));
+  return HZ_OK;
+}
+
+// ---------------------------------------------------------------------------------- Krylov
+struct CycleOut {
+  std::vector<int> its;
+  std::vector<double> est;
+  int status = HZ_OK;
+};
+
+// One (F)GMRES cycle of at most m iterations on nb right-hand sides (Algorithm 1 lines 2-23).
+//  r0 (dvec): initial residuals; u (du): solutions, incremented by X y.
+//  X == nullptr: plain GMRES (x_j = v_j, the basis is combined directly).
+//  tol_abs_b = tol * (ref ? ref[b] : beta_b); active (optional) masks right-hand sides.
+static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, void* V, void* X, void* w, int m,
+                 const void* r0, void* u, int du, double tol, const std::vector<double>* ref,
+                 const std::vector<char>* active_in, const std::function<int(const void*, void*)>& prec,
+                 const std::function<int(const void*, void*)>& op, CycleOut& out) {
+  Ctx& c = h->ctx;
+  const size_t ev = elem_bytes(dvec), ex = elem_bytes(X ? dx : dvec);
+  const size_t bn = (size_t)nb * n;
+  out.its.assign(nb, 0);
+  out.est.assign(nb, 0.0);
+  // beta = ||r0||
+  CK(launch_multidot(c, dvec, r0, 0, 1, r0, n, nb, sc.dev, h->ws));
+  CK(cudaMemcpyAsync(sc.host, sc.dev, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c.s));
+  CS(wait_event(h, sc.ev));
+  std::vector<double> beta(nb), tolabs(nb);
+  std::vector<char> act(nb, 0);
+  int nact = 0;
+  for (int b = 0; b < nb; ++b) {
+    double s = sc.host[2 * b];
+    beta[b] = s > 0 ? std::sqrt(s) : 0.0;
+    if (!std::isfinite(beta[b])) {
+      set_error("non-finite residual norm");
+      out.status = HZ_EBREAKDOWN;
+      return HZ_EBREAKDOWN;
+    }
+    act[b] = (beta[b] > 0) && (!active_in || (*active_in)[b]);
+    tolabs[b] = tol * (ref ? (*ref)[b] : beta[b]);
+    out.est[b] = beta[b];
+    nact += act[b];
+  }
+  if (!nact) return HZ_OK;
+  double* cs_h = sc.host + sc.csc;
+  for (int b = 0; b < nb; ++b) {
+    cs_h[2 * b] = act[b] ? 1.0 / beta[b] : 0.0;
+    cs_h[2 * b + 1] = 0.0;
+  }
+  CK(cudaMemcpyAsync(sc.dev + sc.csc, cs_h, sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, c.s));
+  CK(launch_scale_dev(c, dvec, r0, V, sc.dev + sc.csc, 0, n, nb));
+  // host Hessenberg state per rhs
+  std::vector<std::vector<cd>> H(nb, std::vector<cd>((size_t)(m + 1) * m, 0.0));
+  std::vector<std::vector<double>> gc(nb, std::vector<double>(m, 0.0));
+  std::vector<std::vector<cd>> gs(nb, std::vector<cd>(m, 0.0)), gg(nb, std::vector<cd>(m + 1, 0.0));
+  for (int b = 0; b < nb; ++b) gg[b][0] = beta[b];
+  std::vector<int> jstop(nb, 0);
+  int j = 0;
+  for (; j < m; ++j) {
+    void* Vj = (char*)V + (size_t)j * bn * ev;
+    void* Xj = X ? (char*)X + (size_t)j * bn * ex : Vj;
+    if (X) CS(prec(Vj, Xj));
+    CS(op(Xj, w));
+    const int nv = j + 1;
+    double* hA = sc.dev + sc.hA;
+    double* hB = hA + (size_t)nb * 2 * nv;
+    double* nr = hB + (size_t)nb * 2 * nv;
+    CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hA, h->ws));
+    CK(launch_update(c, dvec, V, bn, nv, hA, dvec, w, n, nb, nullptr, h->ws));
+    CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hB, h->ws));
+    CK(launch_update(c, dvec, V, bn, nv, hB, dvec, w, n, nb, nr, h->ws));
+    const size_t cnt = (size_t)nb * 4 * nv + nb;
+    CK(cudaMemcpyAsync(sc.host, hA, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.s));
+    CS(wait_event(h, sc.ev));
+    const double* hAh = sc.host;
+    const double* hBh = hAh + (size_t)nb * 2 * nv;
+    const double* nrh = hBh + (size_t)nb * 2 * nv;
+    nact = 0;
+    for (int b = 0; b < nb; ++b) {
+      if (!act[b]) continue;
+      std::vector<cd>& Hb = H[b];
+      auto at = [&](int r, int col) -> cd& { return Hb[(size_t)col * (m + 1) + r]; };
+      for (int i = 0; i <= j; ++i)
+        at(i, j) = cd(hAh[(size_t)b * 2 * nv + 2 * i] + hBh[(size_t)b * 2 * nv + 2 * i],
+                      hAh[(size_t)b * 2 * nv + 2 * i + 1] + hBh[(size_t)b * 2 * nv + 2 * i + 1]);
+      double hn = nrh[b] > 0 ? std::sqrt(nrh[b]) : 0.0;
+      at(j + 1, j) = hn;
+      // apply previous rotations
+      for (int i = 0; i < j; ++i) {
+        cd a = at(i, j), bb = at(i + 1, j);
+        at(i, j) = gc[b][i] * a + gs[b][i] * bb;
+        at(i + 1, j) = -std::conj(gs[b][i]) * a + gc[b][i] * bb;
+      }
+      cd a = at(j, j);
+      double bb = hn;
+      double t = std::sqrt(std::norm(a) + bb * bb);
+      if (t == 0) {
+        gc[b][j] = 1.0;
+        gs[b][j] = 0.0;
+      } else if (std::abs(a) == 0) {
+        gc[b][j] = 0.0;
+        gs[b][j] = 1.0;
+      } else {
+        gc[b][j] = std::abs(a) / t;
+        gs[b][j] = (a / std::abs(a)) * bb / t;
+      }
+      at(j, j) = gc[b][j] * a + gs[b][j] * bb;
+      at(j + 1, j) = 0.0;
+      gg[b][j + 1] = -std::conj(gs[b][j]) * gg[b][j];
+      gg[b][j] = gc[b][j] * gg[b][j];
+      double est = std::abs(gg[b][j + 1]);
+      out.est[b] = est;
+      if (!std::isfinite(est) || !std::isfinite(hn)) {
+        set_error("non-finite value in the Arnoldi process");
+        out.status = HZ_EBREAKDOWN;
+        return HZ_EBREAKDOWN;
+      }
+      if (est <= tolabs[b] || hn == 0.0 || j + 1 == m) {
+        act[b] = 0;
+        jstop[b] = j + 1;
+      } else {
+        ++nact;
+      }
+    }
+    if (!nact) {
+      ++j;
+      break;
+    }
+    for (int b = 0; b < nb; ++b) {
+      double hn = std::abs(H[b][(size_t)j * (m + 1) + j + 1]);  // zeroed by rotation; use norm instead
+      (void)hn;
+      double nrm = nrh[b] > 0 ? std::sqrt(nrh[b]) : 0.0;
+      cs_h[2 * b] = act[b] && nrm > 0 ? 1.0 / nrm : 0.0;
+      cs_h[2 * b + 1] = 0.0;
+    }
+    CK(cudaMemcpyAsync(sc.dev + sc.csc, cs_h, sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, c.s));
+    CK(launch_scale_dev(c, dvec, w, (char*)V + (size_t)(j + 1) * bn * ev, sc.dev + sc.csc, 0, n, nb));
+  }
+  // least squares by back substitution on the rotated Hessenberg (Algorithm 1 line 22)
+  int J = 0;
+  for (int b = 0; b < nb; ++b) J = std::max(J, jstop[b]);
+  if (J == 0) return HZ_OK;
+  double* cc = sc.host + sc.ccomb;
+  std::memset(cc, 0, sizeof(double) * 2 * (size_t)nb * J);
+  for (int b = 0; b < nb; ++b) {
+    int k = jstop[b];
+    out.its[b] = k;
+    std::vector<cd> y(k);
+    auto at = [&](int r, int col) -> cd { return H[b][(size_t)col * (m + 1) + r]; };
+    for (int i = k - 1; i >= 0; --i) {
+      cd s = gg[b][i];
+      for (int q = i + 1; q < k; ++q) s -= at(i, q) * y[q];
+      y[i] = s / at(i, i);
+    }
+    for (int i = 0; i < k; ++i) {
+      cc[(size_t)b * 2 * J + 2 * i] = y[i].real();
+      cc[(size_t)b * 2 * J + 2 * i + 1] = y[i].imag();
+    }
+  }
+  CK(cudaMemcpyAsync(sc.dev + sc.ccomb, cc, sizeof(double) * 2 * (size_t)nb * J, cudaMemcpyHostToDevice, c.s));
+  CK(launch_combine(c, X ? dx : dvec, X ? X : V, bn, J, sc.dev + sc.ccomb, du, u, n, nb));
+  return HZ_OK;
+}
+
+// CSLP inverse by unpreconditioned GMRES on M_l (levels > mg_max_level): x += GMRES(b).
+int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
+  Level& L = h->lv[l - 1];
+  const int dt = L.dpre;
+  OpDesc M = L.opM(dt, h->cfg.beta1, h->cfg.beta2);
+  auto op = [&](const void* xin, void* wout) -> int {
+    CK(launch_level_op(h->ctx, M, 0, dt, dt, dt, xin, nullptr, wout, 0.0, nb));
+    return HZ_OK;
+  };
+  std::function<int(const void*, void*)> noprec;
+  CycleOut co;
+  CS(cycle(h, L.scg, dt, dt, L.n, nb, L.Vg, nullptr, L.wg, L.capg, b, x, dt, h->cfg.cslp_tol, nullptr, nullptr,
+           noprec, op, co));
+  for (int q = 0; q < nb; ++q) {
+    h->st[q].cslp_it[l - 1] += co.its[q];
+    if (its_out) its_out[q] = co.its[q];
+  }
+  return HZ_OK;
+}
+
+// out = M_l^-1 rtil [+ add]  (Algorithm 1 line 14; with add = t also line 15)
+int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add, int nb) {
+  Level& L = h->lv[l - 1];
+  if (l <= h->cfg.mg_max_level) return vcycle(h, l, L.dpre, rtil, out, add, nb);
+  const size_t bytes = (size_t)nb * L.n * elem_bytes(L.dpre);
+  if (add) CK(cudaMemcpyAsync(out, add, bytes, cudaMemcpyDeviceToDevice, h->ctx.s));
+  else CK(cudaMemsetAsync(out, 0, bytes, h->ctx.s));
+  return cslp_gmres(h, l, rtil, out, nb, nullptr);
+}
+
+// x = P v at level l (Algorithm 1 lines 5-15).  v has dtype dv; x has dtype lv[l-1].dx.
+int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
+  Level& L = h->lv[l - 1];
+  Ctx& c = h->ctx;
+  const int ml = h->cfg.levels;
+  if (l == ml) {  // coarsest (or single level): CSLP only
+    const void* src = v;
+    if (dv != L.dpre) {
+      CK(launch_convert(c, dv, L.dpre, v, L.rt, (size_t)nb * L.n));
+      src = L.rt;
+    }
+    return cslp_inverse(h, l, src, xout, nullptr, nb);
+  }
+  Level& C = h->lv[l];
+  CK(launch_defl_restrict(c, dv, C.dvec, L.nx, L.ny, v, C.b, nb));                 // line 5
+  CS(coarse_solve(h, l + 1, nb));                                                  // lines 6-10
+  CK(launch_defl_prolong_resid(c, L.opA(L.dpre), L.dpre, dv, C.x, C.nx, C.ny, v, L.t, L.rt, nb));  // 11-13
+  return cslp_inverse(h, l, L.rt, xout, L.t, nb);                                  // lines 14-15
+}
+
+// v_til ~ A_l^-1 b on level l >= 2 with the MADP schedule; reads lv[l-1].b, writes .x
+int coarse_solve(Handle* h, int l, int nb) {
+  Level& L = h->lv[l - 1];
+  const hz_config& cfg = h->cfg;
+  const int ml = cfg.levels;
+  double tol;
+  if (l == ml) {
+    bool negdef = cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level;
+    tol = negdef ? 0.0 : cfg.coarsest_tol;
+  } else {
+    tol = (l == 2) ? cfg.l2_tol : 0.0;
+  }
+  CK(cudaMemsetAsync(L.x, 0, (size_t)nb * L.n * elem_bytes(L.dvec), h->ctx.s));
+  OpDesc A = L.opA(L.dvec);
+  auto op = [&](const void* xin, void* wout) -> int {
+    CK(launch_level_op(h->ctx, A, 0, L.dvec, L.dx, L.dvec, xin, nullptr, wout, 0.0, nb));
+    return HZ_OK;
+  };
+  auto prec = [&](const void* vj, void* xj) -> int { return precond(h, l, vj, L.dvec, xj, nb); };
+  CycleOut co;
+  CS(cycle(h, L.sc, L.dvec, L.dx, L.n, nb, L.V, L.X, L.w, L.cap, L.b, L.x, L.dvec, tol, nullptr, nullptr, prec, op,
+           co));
+  for (int q = 0; q < nb; ++q)
+    if (co.its[q] > 0) {
+      h->st[q].lev_it[l - 1] += co.its[q];
+      h->st[q].lev_calls[l - 1] += 1;
+    }
+  return HZ_OK;
+}
+
+// ---------------------------------------------------------------------------------- solve
+int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags) {
+  Level& L = h->lv[0];
+  Ctx& c = h->ctx;
+  const hz_config& cfg = h->cfg;
+  const size_t n = L.n;
+  for (int q = 0; q < nb; ++q) h->st[q] = RhsStats();
+  Scalars& sc = h->outer_sc;
+  auto norms = [&](const void* x, std::vector<double>& out) -> int {
+    CK(launch_multidot(c, C128, x, 0, 1, x, n, nb, sc.dev, h->ws));
+    CK(cudaMemcpyAsync(sc.host, sc.dev, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c.s));
+    CS(wait_event(h, sc.ev));
+    out.resize(nb);
+    for (int q = 0; q < nb; ++q) out[q] = sc.host[2 * q] > 0 ? std::sqrt(sc.host[2 * q]) : 0.0;
+    return HZ_OK;
+  };
+  OpDesc A = L.opA(C128);
+  std::vector<double> bnorm, rel(nb, 0.0);
+  CS(norms(b, bnorm));
+  if (flags & HZ_SOLVE_INITIAL_GUESS) {
+    CK(launch_level_op(c, A, 1, C128, C128, C128, u, b, h->rres, 0.0, nb));
+  } else {
+    CK(cudaMemsetAsync(u, 0, (size_t)nb * n * 16, c.s));
+    CK(cudaMemcpyAsync(h->rres, b, (size_t)nb * n * 16, cudaMemcpyDeviceToDevice, c.s));
+  }
+  std::vector<double> rn;
+  CS(norms(h->rres, rn));
+  std::vector<char> act(nb, 0);
+  std::vector<int> total(nb, 0);
+  int nact = 0;
+  for (int q = 0; q < nb; ++q) {
+    rel[q] = bnorm[q] > 0 ? rn[q] / bnorm[q] : 0.0;
+    act[q] = bnorm[q] > 0 && rel[q] > tol;
+    nact += act[q];
+  }
+  auto op = [&](const void* xin, void* wout) -> int {
+    CK(launch_level_op(c, A, 0, C128, L.dx, C128, xin, nullptr, wout, 0.0, nb));
+    return HZ_OK;
+  };
+  auto prec = [&](const void* vj, void* xj) -> int { return precond(h, 1, vj, C128, xj, nb); };
+  while (nact) {
+    int mint = cfg.max_outer;
+    for (int q = 0; q < nb; ++q)
+      if (act[q]) mint = std::min(mint, total[q]);
+    int m = std::min(cfg.restart, cfg.max_outer - mint);
+    if (m <= 0) break;
+    CycleOut co;
+    CS(cycle(h, L.sc, C128, L.dx, n, nb, L.V, L.X, L.w, m, h->rres, u, C128, tol, &bnorm, &act, prec, op, co));
+    CK(launch_level_op(c, A, 1, C128, C128, C128, u, b, h->rres, 0.0, nb));   // true residual (FP64)
+    CS(norms(h->rres, rn));
+    nact = 0;
+    for (int q = 0; q < nb; ++q) {
+      if (!act[q]) continue;
+      total[q] += co.its[q];
+      h->st[q].est = bnorm[q] > 0 ? co.est[q] / bnorm[q] : 0.0;
+      rel[q] = rn[q] / bnorm[q];
+      if (!std::isfinite(rel[q])) {
+        act[q] = 0;
+        h->st[q].status = HZ_EBREAKDOWN;
+      } else if (rel[q] <= tol) {
+        act[q] = 0;
+      } else if (total[q] >= cfg.max_outer || co.its[q] == 0) {
+        act[q] = 0;
+        h->st[q].status = HZ_ENOTCONV;
+      } else {
+        ++nact;
+      }
+    }
+  }
+  int first = HZ_OK;
+  for (int q = 0; q < nb; ++q) {
+    h->st[q].outer = total[q];
+    h->st[q].true_rel = rel[q];
+    if (h->st[q].status == HZ_OK && rel[q] > tol) h->st[q].status = HZ_ENOTCONV;
+    if (!first && h->st[q].status) first = h->st[q].status;
+  }
+  return first;
+}
+
+}  // namespace hz

@@ -1,0 +1,101 @@
+// Library state behind the C ABI: level hierarchy, workspace, solver drivers.
+#pragma once
+#include <complex>
+#include <vector>
+
+#include "../../include/hz.h"
+#include "hz_internal.h"
+
+namespace hz {
+
+typedef std::complex<double> cd;
+
+struct MGLevel {
+  OpDesc op;              // M on this multigrid level (level 0: the deflation level's own M_l)
+  void* f = nullptr;      // right-hand side of this MG level (levels >= 1)
+  void* e = nullptr;      // correction of this MG level (levels >= 1)
+  void* tmp = nullptr;    // scratch for the general (nu != 1) cycle
+  void* tmp2 = nullptr;
+};
+
+// Pinned host + device scalar areas of one Krylov driver (one per level and purpose).
+struct Scalars {
+  double* dev = nullptr;  // [hA | hB | nrm2 | coef_scale | coef_comb]
+  double* host = nullptr;
+  size_t hA = 0, hB = 0, nrm = 0, csc = 0, ccomb = 0, total = 0;
+  cudaEvent_t ev = nullptr;
+};
+
+struct Level {
+  int l = 1, nx = 0, ny = 0;
+  size_t n = 0;
+  int R = 1;
+  double H = 0, ks = 1;
+  double m[7] = {}, L[7] = {};
+  double* k_d = nullptr;
+  float* k_f = nullptr;
+  int dvec = C128, dpre = C128, dx = C128;   // basis, preconditioner temporaries, stored x_j
+  // multigrid CSLP (l <= mg_max_level)
+  std::vector<MGLevel> mg;
+  double* inv = nullptr;                     // dense FP64 inverse of the coarsest MG operator
+  int ninv = 0;
+  // deflated / CSLP FGMRES of this level
+  int cap = 0;                               // iteration cap per cycle
+  void* V = nullptr;                         // (cap + 1) batches, dvec
+  void* X = nullptr;                         // cap batches, dx
+  void* w = nullptr;                         // dvec
+  void* b = nullptr;                         // right-hand side on this level (l >= 2), dvec
+  void* x = nullptr;                         // solution on this level (l >= 2), dvec
+  void* t = nullptr;                         // Z v_til, dpre
+  void* rt = nullptr;                        // r_til, dpre
+  void* r = nullptr;                         // general-path scratch, dpre
+  Scalars sc;
+  // GMRES CSLP inverse (l > mg_max_level)
+  int capg = 0;
+  void* Vg = nullptr;                        // (capg + 1) batches, dpre
+  void* wg = nullptr;
+  Scalars scg;
+  OpDesc opA(int dt) const;
+  OpDesc opM(int dt, double b1, double b2) const;
+};
+
+struct RhsStats {
+  int outer = 0;
+  int lev_it[HZ_MAX_LEVELS] = {}, lev_calls[HZ_MAX_LEVELS] = {}, cslp_it[HZ_MAX_LEVELS] = {};
+  double est = 0, true_rel = 0;
+  int status = HZ_OK;
+};
+
+struct Handle {
+  hz_grid g{};
+  hz_config cfg{};
+  Ctx ctx;
+  Prof prof;
+  std::vector<Level> lv;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  void* ws = nullptr;                        // reduction workspace
+  size_t ws_bytes = 0;
+  int nbmax = 1;
+  std::vector<RhsStats> st;                  // per-rhs statistics of the running call
+  Scalars outer_sc;                          // true-residual norms
+  void* rres = nullptr;                      // level-1 true residual buffer (C128)
+};
+
+// allocation helpers (track for hz_destroy)
+int dalloc(Handle* h, void** p, size_t bytes);
+int status_of(cudaError_t e, const char* where);
+
+int setup(Handle* h, const double* k_dev);
+void destroy(Handle* h);
+
+// drivers (all on nb right-hand sides in lockstep)
+int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, int nb);
+int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add, int nb);
+int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out);
+int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb);
+int coarse_solve(Handle* h, int l, int nb);
+int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags);
+int wait_event(Handle* h, cudaEvent_t ev);
+
+}  // namespace hz

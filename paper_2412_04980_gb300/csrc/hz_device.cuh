@@ -1,0 +1,254 @@
+// Device-side building blocks shared by the stencil kernels.
+//
+// Layout: one level vector is ny rows of nx interleaved complex values (x fastest);
+// a batch of nrhs vectors is contiguous with stride nx*ny.  blockIdx.z selects the rhs.
+//
+// Tile engine.  A CTA owns an output window of the grid.  It stages the input field,
+// extended by the stencil radius R, in shared memory, fills the Sommerfeld ghost layer
+// (u_ghost = u_inner + 2 H i k_boundary u_boundary, Section 2.1), and evaluates the
+// level operator at each output node:
+//   R = 1 : the 5-point rows of Section 2.1 (ghosts already substituted in the tile);
+//   R >= 2: the separable Galerkin stencil of Section 3.3 at interior nodes,
+//           Lap = c (L_y M_x + M_y L_x) u,  K = M_y M_x (k^2 u),  out = Lap - sigma K,
+//           computed as three x-passes and two y-passes; physical-boundary nodes use
+//           the 5-point row at the level spacing (Section 3.3, "Boundary").
+// Cells of the extended tile outside the grid are zero except the first ghost layer
+// (one coordinate outside by exactly one); ghost wavenumbers are zero, so the
+// wavenumber part sees zeros outside the grid.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hzd {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> z;
+  z.re = r;
+  z.im = i;
+  return z;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk<T>(s * a.re, s * a.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a / b for complex b
+template <typename T>
+__device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
+  T d = b.re * b.re + b.im * b.im;
+  T inv = T(1) / d;
+  return mk<T>((a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv);
+}
+template <typename TO, typename TI>
+__device__ __forceinline__ cx<TO> cvt(cx<TI> a) {
+  return mk<TO>(TO(a.re), TO(a.im));
+}
+
+// Operator of one grid (a deflation level or a multigrid level).
+//   R == 1 : out = c (4 u - sum of 4 neighbours) - sigma * ks * k^2 u
+//   R >= 2 : interior out = c (L (x) M + M (x) L) u - sigma (M (x) M)(k^2 u), boundary as R == 1
+// sigma = 1 for A, beta1 + i beta2 for the CSLP M.  ks = 4^(l-1) (Galerkin scale).
+template <typename T>
+struct OpP {
+  int nx, ny;
+  int R;            // stencil radius (also a template parameter of the kernels)
+  int bc;           // 0 Sommerfeld, 1 Dirichlet
+  T c;              // Laplacian scale
+  T H;              // ghost spacing (2 H i k)
+  T ks;             // wavenumber-stencil sum
+  T sr, si;         // sigma
+  T m[7], l[7];     // 1-D masks, index d + R (R >= 2)
+  const T* k;       // wavenumber, nx*ny
+};
+
+template <typename T>
+__device__ __forceinline__ int bsides(const OpP<T>& P, int gx, int gy) {
+  return (gx == 0) + (gx == P.nx - 1) + (gy == 0) + (gy == P.ny - 1);
+}
+
+// Exact diagonal of the operator at an in-grid node (matches the ghost substitution).
+template <typename T, int R>
+__device__ __forceinline__ cx<T> op_diag(const OpP<T>& P, int gx, int gy) {
+  T k = P.k[(size_t)gy * P.nx + gx];
+  T k2 = k * k;
+  int g = bsides(P, gx, gy);
+  if (R == 1 || g > 0) {
+    T dre = T(4) * P.c - P.sr * P.ks * k2;
+    T dim = -P.si * P.ks * k2;
+    if (P.bc == 0) dim -= P.c * T(2) * P.H * k * T(g);
+    return mk<T>(dre, dim);
+  } else {
+    T lap = P.c * T(2) * P.l[R] * P.m[R];
+    T extra = P.c * (P.l[R] * P.m[R + 2] + P.m[R] * P.l[R + 2]);
+    int near = (gx == 1) + (gx == P.nx - 2) + (gy == 1) + (gy == P.ny - 2);
+    lap += extra * T(near);
+    T kc = P.m[R] * P.m[R] * k2;
+    return mk<T>(lap - P.sr * kc, -P.si * kc);
+  }
+}
+
+// Shared-memory tile: output window OX x OY at grid origin (ox0, oy0), extended by R.
+template <typename T, int R>
+struct TileView {
+  cx<T>* U;      // (OY + 2R) x (OX + 2R): field with ghost layer
+  cx<T>* W;      // same shape: k^2 * field inside the grid, 0 outside (R >= 2 only)
+  cx<T>* XA;     // (OY + 2R) x OX : L_x U      (R >= 2 only)
+  cx<T>* XB;     //                  M_x U
+  cx<T>* XC;     //                  M_x W
+  int OX, OY, ox0, oy0;
+  __device__ __forceinline__ int WX() const { return OX + 2 * R; }
+  __device__ __forceinline__ int WY() const { return OY + 2 * R; }
+  __device__ __forceinline__ cx<T>& u(int cx_, int cy_) const { return U[cy_ * WX() + cx_]; }
+};
+
+template <typename T, int R>
+__host__ __device__ constexpr size_t tile_smem_bytes(int OX, int OY) {
+  return sizeof(cx<T>) * ((size_t)(OY + 2 * R) * (OX + 2 * R) * (R >= 2 ? 2 : 1) +
+                          (R >= 2 ? (size_t)3 * (OY + 2 * R) * OX : 0));
+}
+
+template <typename T, int R>
+__device__ __forceinline__ TileView<T, R> make_tile(void* smem, int OX, int OY, int ox0, int oy0) {
+  TileView<T, R> t;
+  t.OX = OX;
+  t.OY = OY;
+  t.ox0 = ox0;
+  t.oy0 = oy0;
+  cx<T>* p = reinterpret_cast<cx<T>*>(smem);
+  size_t wsz = (size_t)(OY + 2 * R) * (OX + 2 * R);
+  t.U = p;
+  p += wsz;
+  if (R >= 2) {
+    t.W = p;
+    p += wsz;
+    t.XA = p;
+    p += (size_t)(OY + 2 * R) * OX;
+    t.XB = p;
+    p += (size_t)(OY + 2 * R) * OX;
+    t.XC = p;
+  } else {
+    t.W = t.XA = t.XB = t.XC = nullptr;
+  }
+  return t;
+}
+
+// Stage 1: fill in-grid cells from src(gx, gy) (out-of-grid cells = 0) and W = k^2 u.
+// Stage 2: Sommerfeld ghost layer.  Stage 3 (R >= 2): x-passes.  Ends synchronised.
+template <typename T, int R, class Src>
+__device__ __forceinline__ void tile_fill(const TileView<T, R>& t, const OpP<T>& P, const Src& src) {
+  const int WX = t.WX(), WY = t.WY();
+  const int nthr = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int gx0 = t.ox0 - R, gy0 = t.oy0 - R;
+  for (int idx = tid; idx < WX * WY; idx += nthr) {
+    int cy = idx / WX, cxx = idx - cy * WX;
+    int gx = gx0 + cxx, gy = gy0 + cy;
+    cx<T> v = mk<T>(T(0), T(0));
+    cx<T> w = v;
+    if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) {
+      v = src(gx, gy);
+      if (R >= 2) {
+        T k = P.k[(size_t)gy * P.nx + gx];
+        w = (k * k) * v;
+      }
+    }
+    t.U[idx] = v;
+    if (R >= 2) t.W[idx] = w;
+  }
+  __syncthreads();
+  if (P.bc == 0) {
+    const T two_h = T(2) * P.H;
+    // left (gx = -1) and right (gx = nx) ghost columns, rows inside the grid
+    const int cl = -1 - gx0, cr = P.nx - gx0;
+    for (int cy = tid; cy < WY; cy += nthr) {
+      int gy = gy0 + cy;
+      if (gy < 0 || gy >= P.ny) continue;
+      if (cl >= 0 && cl < WX) {
+        T k = P.k[(size_t)gy * P.nx + 0];
+        cx<T> ub = t.U[cy * WX + cl + 1], ui = t.U[cy * WX + cl + 2];
+        t.U[cy * WX + cl] = mk<T>(ui.re - two_h * k * ub.im, ui.im + two_h * k * ub.re);
+      }
+      if (cr >= 0 && cr < WX) {
+        T k = P.k[(size_t)gy * P.nx + P.nx - 1];
+        cx<T> ub = t.U[cy * WX + cr - 1], ui = t.U[cy * WX + cr - 2];
+        t.U[cy * WX + cr] = mk<T>(ui.re - two_h * k * ub.im, ui.im + two_h * k * ub.re);
+      }
+    }
+    const int rb = -1 - gy0, rt = P.ny - gy0;
+    for (int cxx = tid; cxx < WX; cxx += nthr) {
+      int gx = gx0 + cxx;
+      if (gx < 0 || gx >= P.nx) continue;
+      if (rb >= 0 && rb < WY) {
+        T k = P.k[gx];
+        cx<T> ub = t.U[(rb + 1) * WX + cxx], ui = t.U[(rb + 2) * WX + cxx];
+        t.U[rb * WX + cxx] = mk<T>(ui.re - two_h * k * ub.im, ui.im + two_h * k * ub.re);
+      }
+      if (rt >= 0 && rt < WY) {
+        T k = P.k[(size_t)(P.ny - 1) * P.nx + gx];
+        cx<T> ub = t.U[(rt - 1) * WX + cxx], ui = t.U[(rt - 2) * WX + cxx];
+        t.U[rt * WX + cxx] = mk<T>(ui.re - two_h * k * ub.im, ui.im + two_h * k * ub.re);
+      }
+    }
+    __syncthreads();
+  }
+  if (R >= 2) {
+    const int OX = t.OX;
+    for (int idx = tid; idx < WY * OX; idx += nthr) {
+      int cy = idx / OX, ox = idx - cy * OX;
+      const cx<T>* ur = t.U + cy * WX + ox;   // cell (ox + R + d) at ur[R + d]
+      const cx<T>* wr = t.W + cy * WX + ox;
+      cx<T> a = mk<T>(T(0), T(0)), b = a, c = a;
+#pragma unroll
+      for (int d = 0; d <= 2 * R; ++d) {
+        a = a + P.l[d] * ur[d];
+        b = b + P.m[d] * ur[d];
+        c = c + P.m[d] * wr[d];
+      }
+      t.XA[idx] = a;
+      t.XB[idx] = b;
+      t.XC[idx] = c;
+    }
+    __syncthreads();
+  }
+}
+
+// Operator value at output cell (ox, oy) of the tile (grid node ox0 + ox, oy0 + oy).
+template <typename T, int R>
+__device__ __forceinline__ cx<T> tile_op(const TileView<T, R>& t, const OpP<T>& P, int ox, int oy) {
+  const int WX = t.WX();
+  const int gx = t.ox0 + ox, gy = t.oy0 + oy;
+  const cx<T>* uc = t.U + (oy + R) * WX + (ox + R);
+  if (R == 1 || bsides(P, gx, gy) > 0) {
+    cx<T> s = (uc[1] + uc[-1]) + (uc[WX] + uc[-WX]);
+    T k = P.k[(size_t)gy * P.nx + gx];
+    T k2 = P.ks * k * k;
+    cx<T> lap = mk<T>(T(4) * uc->re - s.re, T(4) * uc->im - s.im);
+    // c * lap - sigma * ks * k^2 * u
+    T ar = k2 * P.sr, ai = k2 * P.si;
+    return mk<T>(P.c * lap.re - (ar * uc->re - ai * uc->im), P.c * lap.im - (ar * uc->im + ai * uc->re));
+  } else {
+    const int OX = t.OX;
+    cx<T> lap = mk<T>(T(0), T(0)), kk = lap;
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) {
+      int row = (oy + d) * OX + ox;
+      lap = lap + P.m[d] * t.XA[row];
+      lap = lap + P.l[d] * t.XB[row];
+      kk = kk + P.m[d] * t.XC[row];
+    }
+    return mk<T>(P.c * lap.re - (P.sr * kk.re - P.si * kk.im), P.c * lap.im - (P.sr * kk.im + P.si * kk.re));
+  }
+}
+
+}  // namespace hzd

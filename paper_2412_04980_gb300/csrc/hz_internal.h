@@ -1,0 +1,126 @@
+// Host-side internal interface of the library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace hz {
+
+enum Dtype { C128 = 0, C64 = 1 };
+
+inline size_t elem_bytes(int dt) { return dt == C128 ? 16 : 8; }
+
+// Kernel families for the per-launch event timer.
+enum Family {
+  F_LEVEL_OP = 0,   // level operator apply / residual / Jacobi
+  F_MG_DOWN,        // fused pre-smooth + residual + full weighting
+  F_MG_UP,          // fused bilinear correction + post-smooth
+  F_DEFL_RESTRICT,  // Z^T
+  F_DEFL_PROLONG,   // Z, and Z + A + subtract
+  F_DOT,            // multi-dot products
+  F_AXPY,           // basis updates / combinations / scaling
+  F_REDUCE,         // second-stage reductions
+  F_DENSE,          // dense coarsest multigrid solve
+  F_MISC,           // conversions, copies
+  F_COUNT
+};
+const char* family_name(int f);
+
+struct Prof {
+  struct Rec { cudaEvent_t a, b; double bytes; };
+  bool on[F_COUNT] = {};
+  std::vector<Rec> pending[F_COUNT];
+  long long launches[F_COUNT] = {};
+  double ms[F_COUNT] = {};
+  double bytes[F_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void drain(int fam);   // synchronous: folds pending records into the totals
+  ~Prof();
+};
+
+struct Ctx {
+  cudaStream_t s = 0;
+  Prof* prof = nullptr;
+};
+
+// RAII-free launch timer: begin() returns an index, end() closes it.
+struct ProfScope {
+  Ctx& c;
+  int fam;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(Ctx& c_, int fam_, double bytes_);
+  ~ProfScope();
+};
+
+// Host description of one grid operator (see hzd::OpP).
+struct OpDesc {
+  int nx = 0, ny = 0, R = 1, bc = 0;
+  double c = 0, H = 0, ks = 1, sr = 1, si = 0;
+  double m[7] = {}, l[7] = {};
+  const double* k_d = nullptr;
+  const float* k_f = nullptr;
+  size_t n() const { return (size_t)nx * ny; }
+};
+
+// ---- stencil launchers (kern_stencil.cu) --------------------------------------------
+// mode: 0 y = Op x; 1 y = f - Op x; 2 y = x + omega (f - Op x) / D
+// tcomp: arithmetic dtype; tx: dtype of x and f; ty: dtype of y.
+cudaError_t launch_level_op(Ctx& c, const OpDesc& op, int mode, int tcomp, int tx, int ty, const void* x,
+                            const void* f, void* y, double omega, int nrhs);
+// y = omega f / D (Jacobi sweep from a zero initial guess), tcomp == tx == ty
+cudaError_t launch_jacobi_zero(Ctx& c, const OpDesc& op, int dt, const void* f, void* y, double omega, int nrhs);
+// t = Z vtil (coarse vtil, dtype tcomp), rtil = v - A t.  v has dtype tv; t, rtil dtype tcomp.
+cudaError_t launch_defl_prolong_resid(Ctx& c, const OpDesc& op, int tcomp, int tv, const void* vtil,
+                                      int ncx, int ncy, const void* v, void* t, void* rtil, int nrhs);
+// t = Z w (plain prolongation), same dtype.
+cudaError_t launch_defl_prolong(Ctx& c, int dt, int nx, int ny, const void* w, void* t, int nrhs);
+// vhat = Z^T v; v dtype tin, vhat dtype tout (arithmetic in tout).
+cudaError_t launch_defl_restrict(Ctx& c, int tin, int tout, int nx, int ny, const void* v, void* vhat,
+                                 int nrhs);
+// Fused multigrid kernels, V(1,1) with zero initial guess.
+// down: fc = FW(f - Op(omega f / D)) on the next coarser grid (ncx x ncy)
+cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void* fc, double omega, int nrhs);
+// up: u = omega f / D + P ec; y = u + omega (f - Op u) / D (+ add if add != null, add dtype tadd)
+cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const void* ec, void* y,
+                         double omega, const void* add, int tadd, void* yout2, int tout2, int nrhs);
+// General multigrid pieces: fc = FW(r); u += P ec.
+cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs);
+cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs);
+
+// ---- vector launchers (kern_vec.cu) -------------------------------------------------
+// Dense FP64 complex matvec y = A x with dtype conversions (coarsest multigrid solve).
+cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, void* y, int nrhs);
+// Convert between dtypes: y (ty) = x (tx), n complex elements.
+cudaError_t launch_convert(Ctx& c, int tx, int ty, const void* x, void* y, size_t n);
+// y (ty) = x (tx) + z (tz)  (all n elements)
+cudaError_t launch_add(Ctx& c, int tx, const void* x, int tz, const void* z, int ty, void* y, size_t n);
+
+// Batched Krylov kernels.  nb right-hand sides; vector i of rhs b lives at base + i*ldv + b*n
+// (elements), so a batch of one vector index is nb*n contiguous elements.
+// Multi-dot: out[b*2nv + 2i + {0,1}] = sum_e conj(V_i^b[e]) w^b[e] (double), ws: dot_ws_bytes(nv, nb).
+size_t dot_ws_bytes(int nv, int nb);
+cudaError_t launch_multidot(Ctx& c, int dt, const void* V, size_t ldv, int nv, const void* w, size_t n, int nb,
+                            double* out, void* ws);
+// w^b (dtw) -= sum_i coef[b*2nv + 2i..] V_i^b (dtv); optionally ||w^b||^2 into nrm2[b] (device doubles).
+cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, const double* coef, int dtw, void* w,
+                          size_t n, int nb, double* nrm2, void* ws);
+// u^b (dtu) += sum_i coef[b*2nv + 2i..] X_i^b (dtx)
+cudaError_t launch_combine(Ctx& c, int dtx, const void* X, size_t ldx, int nv, const double* coef, int dtu, void* u,
+                           size_t n, int nb);
+// y^b = alpha_b x^b: alpha complex (2 doubles per rhs) or, with recip, 1/sqrt(alpha_b) (1 double per rhs).
+cudaError_t launch_scale_dev(Ctx& c, int dt, const void* x, void* y, const double* alpha_dev, int recip, size_t n,
+                             int nb);
+
+// ---- exact coarse stencils (stencil_gen.cpp) ----------------------------------------
+// 1-D Galerkin masks of level l (1-based), length 2R+1, as exact rationals rounded once.
+void galerkin_masks(int level, int* R, double m[7], double l[7]);
+
+// ---- thread-local error message -----------------------------------------------------
+void set_error(const std::string& msg);
+
+}  // namespace hz

@@ -1,0 +1,598 @@
+// Stencil kernels of the hot path: level operators (Section 2.1, Section 3.3), deflation
+// transfers Z / Z^T (Section 3.1, Algorithm 1 lines 5 and 11-13) and the multigrid
+// CSLP pieces (damped Jacobi, full weighting, bilinear prolongation).
+//
+// Every kernel is HBM-bound in FP32 and FP64-ALU-bound in FP64 on this part; inputs are
+// staged once per CTA in shared memory (tile + halo), outputs are written coalesced.
+#include <cstdio>
+
+#include "hz_device.cuh"
+#include "hz_internal.h"
+
+using namespace hzd;
+
+namespace {
+
+constexpr int BX = 32, BY = 8;          // 256 threads per CTA
+constexpr int OXT = 32, OYT = 16;       // output tile of the fine-grid kernels
+
+__host__ __device__ inline int floordiv2(int a) { return (a >= 0) ? (a >> 1) : -((-a + 1) >> 1); }
+
+template <typename T>
+OpP<T> make_op(const hz::OpDesc& d) {
+  OpP<T> p;
+  p.nx = d.nx;
+  p.ny = d.ny;
+  p.R = d.R;
+  p.bc = d.bc;
+  p.c = T(d.c);
+  p.H = T(d.H);
+  p.ks = T(d.ks);
+  p.sr = T(d.sr);
+  p.si = T(d.si);
+  for (int i = 0; i < 7; ++i) {
+    p.m[i] = T(d.m[i]);
+    p.l[i] = T(d.l[i]);
+  }
+  if constexpr (sizeof(T) == 8) p.k = reinterpret_cast<const T*>(d.k_d);
+  else p.k = reinterpret_cast<const T*>(d.k_f);
+  return p;
+}
+
+template <typename T>
+__device__ __forceinline__ T pw(int d) {  // deflation weights p = [1,4,6,4,1]/8
+  return d == 0 ? T(0.75) : ((d == 1 || d == -1) ? T(0.5) : ((d == 2 || d == -2) ? T(0.125) : T(0)));
+}
+
+template <typename T, typename TI>
+struct GlobalSrc {
+  const cx<TI>* x;
+  int nx;
+  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const { return cvt<T>(x[(size_t)gy * nx + gx]); }
+};
+
+// omega * f / D : one Jacobi sweep from a zero initial guess
+template <typename T, int R>
+struct JacZeroSrc {
+  const cx<T>* f;
+  OpP<T> P;
+  T omega;
+  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const {
+    return omega * cdiv(f[(size_t)gy * P.nx + gx], op_diag<T, R>(P, gx, gy));
+  }
+};
+
+// Z vtil from a coarse tile held in shared memory
+template <typename T>
+struct ZSrc {
+  const cx<T>* Cs;
+  int CW, Imin, Jmin;
+  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const {
+    int I0 = floordiv2(gx - 1), I1 = floordiv2(gx + 2);
+    int J0 = floordiv2(gy - 1), J1 = floordiv2(gy + 2);
+    cx<T> acc = mk<T>(T(0), T(0));
+    for (int J = J0; J <= J1; ++J) {
+      T wy = pw<T>(gy - 2 * J);
+      cx<T> row = mk<T>(T(0), T(0));
+      for (int I = I0; I <= I1; ++I) row = row + pw<T>(gx - 2 * I) * Cs[(J - Jmin) * CW + (I - Imin)];
+      acc = acc + wy * row;
+    }
+    return acc;
+  }
+};
+
+// omega f / D + bilinear(ec) from a coarse tile in shared memory
+template <typename T, int R>
+struct UpSrc {
+  const cx<T>* f;
+  OpP<T> P;
+  T omega;
+  const cx<T>* Es;
+  int EW, Imin, Jmin;
+  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const {
+    cx<T> u = omega * cdiv(f[(size_t)gy * P.nx + gx], op_diag<T, R>(P, gx, gy));
+    int I = floordiv2(gx), J = floordiv2(gy);
+    int ex = gx - 2 * I, ey = gy - 2 * J;
+    const cx<T>* e = Es + (J - Jmin) * EW + (I - Imin);
+    cx<T> a = e[0];
+    if (ex) a = T(0.5) * (a + e[1]);
+    if (ey) {
+      cx<T> b = e[EW];
+      if (ex) b = T(0.5) * (b + e[EW + 1]);
+      a = T(0.5) * (a + b);
+    }
+    return u + a;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+template <typename T, typename TI, typename TO, int R, int MODE>
+__global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __restrict__ x,
+                                                       const cx<TI>* __restrict__ f, cx<TO>* __restrict__ y,
+                                                       T omega) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t off = (size_t)blockIdx.z * P.nx * P.ny;
+  x += off;
+  y += off;
+  if (MODE != 0) f += off;
+  const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
+  TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
+  tile_fill<T, R>(t, P, GlobalSrc<T, TI>{x, P.nx});
+#pragma unroll
+  for (int p = 0; p < OYT / BY; ++p) {
+    const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+    const int gx = ox0 + ox, gy = oy0 + oy;
+    if (gx >= P.nx || gy >= P.ny) continue;
+    cx<T> v = tile_op<T, R>(t, P, ox, oy);
+    const size_t i = (size_t)gy * P.nx + gx;
+    cx<T> out;
+    if (MODE == 0) {
+      out = v;
+    } else {
+      cx<T> r = cvt<T>(f[i]) - v;
+      if (MODE == 1) out = r;
+      else out = t.u(ox + R, oy + R) + omega * cdiv(r, op_diag<T, R>(P, gx, gy));
+    }
+    y[i] = cvt<TO>(out);
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_jacobi_zero(OpP<T> P, const cx<T>* __restrict__ f, cx<T>* __restrict__ y,
+                                                     T omega) {
+  const size_t n = (size_t)P.nx * P.ny;
+  const size_t off = (size_t)blockIdx.y * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    int gy = (int)(i / P.nx), gx = (int)(i - (size_t)gy * P.nx);
+    y[off + i] = omega * cdiv(f[off + i], op_diag<T, R>(P, gx, gy));
+  }
+}
+
+// t = Z vtil ; rtil = v - A t  (Algorithm 1, lines 11-13)
+template <typename T, typename TV, int R>
+__global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const cx<T>* __restrict__ vtil, int ncx,
+                                                                 int ncy, const cx<TV>* __restrict__ v,
+                                                                 cx<T>* __restrict__ tout, cx<T>* __restrict__ rtil) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t off = (size_t)blockIdx.z * P.nx * P.ny;
+  const size_t offc = (size_t)blockIdx.z * ncx * ncy;
+  const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
+  const int Imin = floordiv2(ox0 - R - 1), Imax = floordiv2(ox0 + OXT + R + 1);
+  const int Jmin = floordiv2(oy0 - R - 1), Jmax = floordiv2(oy0 + OYT + R + 1);
+  const int CW = Imax - Imin + 1, CH = Jmax - Jmin + 1;
+  TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
+  cx<T>* Cs = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OXT, OYT));
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int idx = tid; idx < CW * CH; idx += BX * BY) {
+    int cj = idx / CW, ci = idx - cj * CW;
+    int I = Imin + ci, J = Jmin + cj;
+    Cs[idx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? vtil[offc + (size_t)J * ncx + I] : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  tile_fill<T, R>(t, P, ZSrc<T>{Cs, CW, Imin, Jmin});
+#pragma unroll
+  for (int p = 0; p < OYT / BY; ++p) {
+    const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+    const int gx = ox0 + ox, gy = oy0 + oy;
+    if (gx >= P.nx || gy >= P.ny) continue;
+    const size_t i = off + (size_t)gy * P.nx + gx;
+    cx<T> s = tile_op<T, R>(t, P, ox, oy);
+    rtil[i] = cvt<T>(v[i]) - s;
+    if (tout) tout[i] = t.u(ox + R, oy + R);
+  }
+}
+
+// plain t = Z w (Algorithm 1, line 11)
+template <typename T>
+__global__ void __launch_bounds__(256) k_defl_prolong(const cx<T>* __restrict__ w, int ncx, int ncy,
+                                                      cx<T>* __restrict__ t, int nx, int ny) {
+  const size_t n = (size_t)nx * ny;
+  const size_t off = (size_t)blockIdx.y * n, offc = (size_t)blockIdx.y * ncx * ncy;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    int gy = (int)(i / nx), gx = (int)(i - (size_t)gy * nx);
+    int I0 = floordiv2(gx - 1), I1 = floordiv2(gx + 2), J0 = floordiv2(gy - 1), J1 = floordiv2(gy + 2);
+    cx<T> acc = mk<T>(T(0), T(0));
+    for (int J = J0; J <= J1; ++J) {
+      if (J < 0 || J >= ncy) continue;
+      cx<T> row = mk<T>(T(0), T(0));
+      for (int I = I0; I <= I1; ++I) {
+        if (I < 0 || I >= ncx) continue;
+        row = row + pw<T>(gx - 2 * I) * w[offc + (size_t)J * ncx + I];
+      }
+      acc = acc + pw<T>(gy - 2 * J) * row;
+    }
+    t[off + i] = acc;
+  }
+}
+
+// vhat = Z^T v (Algorithm 1, line 5): separable 5-tap filters at stride 2
+constexpr int RXC = 32, RYC = 16;
+template <typename TI, typename T>
+__global__ void __launch_bounds__(BX* BY) k_defl_restrict(const cx<TI>* __restrict__ v, int nx, int ny,
+                                                            cx<T>* __restrict__ vhat, int ncx, int ncy) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int FW = 2 * RXC + 3, FH = 2 * RYC + 3;
+  cx<T>* F = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* XR = F + FW * FH;
+  const size_t off = (size_t)blockIdx.z * nx * ny, offc = (size_t)blockIdx.z * ncx * ncy;
+  const int x0c = blockIdx.x * RXC, y0c = blockIdx.y * RYC;
+  const int fx0 = 2 * x0c - 2, fy0 = 2 * y0c - 2;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int idx = tid; idx < FW * FH; idx += BX * BY) {
+    int fy = idx / FW, fx = idx - fy * FW;
+    int gx = fx0 + fx, gy = fy0 + fy;
+    F[idx] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? cvt<T>(v[off + (size_t)gy * nx + gx]) : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  for (int idx = tid; idx < FH * RXC; idx += BX * BY) {
+    int fy = idx / RXC, ox = idx - fy * RXC;
+    const cx<T>* r = F + fy * FW + 2 * ox;   // fine cell 2*ox + 2 + a at r[2 + a]
+    XR[idx] = (T(0.125) * (r[0] + r[4]) + T(0.5) * (r[1] + r[3])) + T(0.75) * r[2];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < RYC / BY; ++p) {
+    int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+    int I = x0c + ox, J = y0c + oy;
+    if (I >= ncx || J >= ncy) continue;
+    const cx<T>* c = XR + (2 * oy) * RXC + ox;   // fine row 2*oy + 2 + b at c[(2 + b) * RXC]
+    vhat[offc + (size_t)J * ncx + I] =
+        (T(0.125) * (c[0] + c[4 * RXC]) + T(0.5) * (c[RXC] + c[3 * RXC])) + T(0.75) * c[2 * RXC];
+  }
+}
+
+// fc = FW(f - Op(omega f / D)) : pre-smoothing from zero, residual, full weighting
+constexpr int DXC = 32, DYC = 8;
+template <typename T, int R>
+__global__ void __launch_bounds__(BX* BY) k_mg_down(OpP<T> P, const cx<T>* __restrict__ f, cx<T>* __restrict__ fc,
+                                                      int ncx, int ncy, T omega) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int OX = 2 * DXC + 1, OY = 2 * DYC + 1;
+  const size_t off = (size_t)blockIdx.z * P.nx * P.ny, offc = (size_t)blockIdx.z * ncx * ncy;
+  f += off;
+  const int x0c = blockIdx.x * DXC, y0c = blockIdx.y * DYC;
+  const int ox0 = 2 * x0c - 1, oy0 = 2 * y0c - 1;
+  TileView<T, R> t = make_tile<T, R>(smem, OX, OY, ox0, oy0);
+  cx<T>* RS = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OX, OY));
+  tile_fill<T, R>(t, P, JacZeroSrc<T, R>{f, P, omega});
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int idx = tid; idx < OX * OY; idx += BX * BY) {
+    int oy = idx / OX, ox = idx - oy * OX;
+    int gx = ox0 + ox, gy = oy0 + oy;
+    cx<T> r = mk<T>(T(0), T(0));
+    if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) r = f[(size_t)gy * P.nx + gx] - tile_op<T, R>(t, P, ox, oy);
+    RS[idx] = r;
+  }
+  __syncthreads();
+  const int ox = threadIdx.x, oy = threadIdx.y;
+  const int I = x0c + ox, J = y0c + oy;
+  if (I < ncx && J < ncy) {
+    const cx<T>* c = RS + (2 * oy + 1) * OX + (2 * ox + 1);
+    cx<T> s = (T(4) * c[0] + T(2) * ((c[1] + c[-1]) + (c[OX] + c[-OX]))) +
+              ((c[OX + 1] + c[OX - 1]) + (c[-OX + 1] + c[-OX - 1]));
+    fc[offc + (size_t)J * ncx + I] = T(0.0625) * s;
+  }
+}
+
+// u = omega f / D + P ec ; y = u + omega (f - Op u) / D [+ add]
+template <typename T, int R>
+__global__ void __launch_bounds__(BX* BY) k_mg_up(OpP<T> P, const cx<T>* __restrict__ f, const cx<T>* __restrict__ ec,
+                                                    int ncx, int ncy, cx<T>* __restrict__ y, T omega,
+                                                    const cx<T>* __restrict__ add) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t off = (size_t)blockIdx.z * P.nx * P.ny, offc = (size_t)blockIdx.z * ncx * ncy;
+  f += off;
+  const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
+  const int Imin = floordiv2(ox0 - R), Imax = floordiv2(ox0 + OXT + R - 1) + 1;
+  const int Jmin = floordiv2(oy0 - R), Jmax = floordiv2(oy0 + OYT + R - 1) + 1;
+  const int EW = Imax - Imin + 1, EH = Jmax - Jmin + 1;
+  TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
+  cx<T>* Es = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OXT, OYT));
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int idx = tid; idx < EW * EH; idx += BX * BY) {
+    int cj = idx / EW, ci = idx - cj * EW;
+    int I = Imin + ci, J = Jmin + cj;
+    Es[idx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[offc + (size_t)J * ncx + I] : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  tile_fill<T, R>(t, P, UpSrc<T, R>{f, P, omega, Es, EW, Imin, Jmin});
+#pragma unroll
+  for (int p = 0; p < OYT / BY; ++p) {
+    const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+    const int gx = ox0 + ox, gy = oy0 + oy;
+    if (gx >= P.nx || gy >= P.ny) continue;
+    const size_t i = (size_t)gy * P.nx + gx;
+    cx<T> r = f[i] - tile_op<T, R>(t, P, ox, oy);
+    cx<T> out = t.u(ox + R, oy + R) + omega * cdiv(r, op_diag<T, R>(P, gx, gy));
+    if (add) out = out + add[off + i];
+    y[off + i] = out;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fw(const cx<T>* __restrict__ r, int nx, int ny, cx<T>* __restrict__ rc,
+                                            int ncx, int ncy) {
+  const size_t nc = (size_t)ncx * ncy;
+  const size_t off = (size_t)blockIdx.y * nx * ny, offc = (size_t)blockIdx.y * nc;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nc; i += (size_t)gridDim.x * blockDim.x) {
+    int J = (int)(i / ncx), I = (int)(i - (size_t)J * ncx);
+    cx<T> s = mk<T>(T(0), T(0));
+    for (int b = -1; b <= 1; ++b) {
+      int gy = 2 * J + b;
+      if (gy < 0 || gy >= ny) continue;
+      for (int a = -1; a <= 1; ++a) {
+        int gx = 2 * I + a;
+        if (gx < 0 || gx >= nx) continue;
+        T w = T((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
+        s = s + w * r[off + (size_t)gy * nx + gx];
+      }
+    }
+    rc[offc + i] = T(0.0625) * s;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(const cx<T>* __restrict__ ec, int ncx, int ncy,
+                                                     cx<T>* __restrict__ u, int nx, int ny) {
+  const size_t n = (size_t)nx * ny;
+  const size_t off = (size_t)blockIdx.y * n, offc = (size_t)blockIdx.y * ncx * ncy;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    int gy = (int)(i / nx), gx = (int)(i - (size_t)gy * nx);
+    int I = gx >> 1, J = gy >> 1, ex = gx & 1, ey = gy & 1;
+    const cx<T>* e = ec + offc + (size_t)J * ncx + I;
+    cx<T> a = e[0];
+    if (ex) a = T(0.5) * (a + e[1]);
+    if (ey) {
+      cx<T> b = e[ncx];
+      if (ex) b = T(0.5) * (b + e[ncx + 1]);
+      a = T(0.5) * (a + b);
+    }
+    u[off + i] = u[off + i] + a;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+inline unsigned grid1d(size_t n) {
+  size_t b = (n + 255) / 256;
+  size_t cap = 152 * 16;
+  return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <typename T, typename TI, typename TO, int R>
+cudaError_t level_op_r(hz::Ctx& c, const hz::OpDesc& d, int mode, const void* x, const void* f, void* y,
+                       double omega, int nrhs) {
+  OpP<T> P = make_op<T>(d);
+  dim3 grid((d.nx + OXT - 1) / OXT, (d.ny + OYT - 1) / OYT, nrhs), block(BX, BY);
+  size_t sm = tile_smem_bytes<T, R>(OXT, OYT);
+  auto X = reinterpret_cast<const cx<TI>*>(x);
+  auto F = reinterpret_cast<const cx<TI>*>(f);
+  auto Y = reinterpret_cast<cx<TO>*>(y);
+  cudaError_t e;
+  double bytes = (double)nrhs * d.n() * (sizeof(cx<TI>) * (mode ? 2 : 1) + sizeof(cx<TO>) + sizeof(T));
+  hz::ProfScope ps(c, hz::F_LEVEL_OP, bytes);
+  if (mode == 0) {
+    if ((e = set_smem(k_level_op<T, TI, TO, R, 0>, sm)) != cudaSuccess) return e;
+    k_level_op<T, TI, TO, R, 0><<<grid, block, sm, c.s>>>(P, X, F, Y, T(omega));
+  } else if (mode == 1) {
+    if ((e = set_smem(k_level_op<T, TI, TO, R, 1>, sm)) != cudaSuccess) return e;
+    k_level_op<T, TI, TO, R, 1><<<grid, block, sm, c.s>>>(P, X, F, Y, T(omega));
+  } else {
+    if ((e = set_smem(k_level_op<T, TI, TO, R, 2>, sm)) != cudaSuccess) return e;
+    k_level_op<T, TI, TO, R, 2><<<grid, block, sm, c.s>>>(P, X, F, Y, T(omega));
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, typename TI, typename TO>
+cudaError_t level_op_t(hz::Ctx& c, const hz::OpDesc& d, int mode, const void* x, const void* f, void* y,
+                       double omega, int nrhs) {
+  switch (d.R) {
+    case 1: return level_op_r<T, TI, TO, 1>(c, d, mode, x, f, y, omega, nrhs);
+    case 2: return level_op_r<T, TI, TO, 2>(c, d, mode, x, f, y, omega, nrhs);
+    case 3: return level_op_r<T, TI, TO, 3>(c, d, mode, x, f, y, omega, nrhs);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+namespace hz {
+
+cudaError_t launch_level_op(Ctx& c, const OpDesc& op, int mode, int tcomp, int tx, int ty, const void* x,
+                            const void* f, void* y, double omega, int nrhs) {
+  if (tcomp == C128 && tx == C128 && ty == C128) return level_op_t<double, double, double>(c, op, mode, x, f, y, omega, nrhs);
+  if (tcomp == C64 && tx == C64 && ty == C64) return level_op_t<float, float, float>(c, op, mode, x, f, y, omega, nrhs);
+  if (tcomp == C128 && tx == C64 && ty == C128) return level_op_t<double, float, double>(c, op, mode, x, f, y, omega, nrhs);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int R>
+static cudaError_t jz_r(Ctx& c, const OpDesc& d, const void* f, void* y, double omega, int nrhs) {
+  ProfScope ps(c, F_MG_DOWN, (double)nrhs * d.n() * (2 * sizeof(cx<T>) + sizeof(T)));
+  k_jacobi_zero<T, R><<<dim3(grid1d(d.n()), nrhs), 256, 0, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f),
+                                                                   reinterpret_cast<cx<T>*>(y), T(omega));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_zero(Ctx& c, const OpDesc& op, int dt, const void* f, void* y, double omega, int nrhs) {
+  if (dt == C128) {
+    switch (op.R) {
+      case 1: return jz_r<double, 1>(c, op, f, y, omega, nrhs);
+      case 2: return jz_r<double, 2>(c, op, f, y, omega, nrhs);
+      case 3: return jz_r<double, 3>(c, op, f, y, omega, nrhs);
+    }
+  } else {
+    switch (op.R) {
+      case 1: return jz_r<float, 1>(c, op, f, y, omega, nrhs);
+      case 2: return jz_r<float, 2>(c, op, f, y, omega, nrhs);
+      case 3: return jz_r<float, 3>(c, op, f, y, omega, nrhs);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, typename TV, int R>
+static cudaError_t dpr_r(Ctx& c, const OpDesc& d, const void* vtil, int ncx, int ncy, const void* v, void* t,
+                         void* rtil, int nrhs) {
+  OpP<T> P = make_op<T>(d);
+  dim3 grid((d.nx + OXT - 1) / OXT, (d.ny + OYT - 1) / OYT, nrhs), block(BX, BY);
+  const int CW = (OXT + 2 * R + 6) / 2 + 2, CH = (OYT + 2 * R + 6) / 2 + 2;
+  size_t sm = tile_smem_bytes<T, R>(OXT, OYT) + sizeof(cx<T>) * CW * CH;
+  cudaError_t e = set_smem(k_defl_prolong_resid<T, TV, R>, sm);
+  if (e != cudaSuccess) return e;
+  double bytes = (double)nrhs * d.n() * (sizeof(cx<TV>) + sizeof(cx<T>) * (t ? 2 : 1) + sizeof(T) + sizeof(cx<T>) / 4.0);
+  ProfScope ps(c, F_DEFL_PROLONG, bytes);
+  k_defl_prolong_resid<T, TV, R><<<grid, block, sm, c.s>>>(P, reinterpret_cast<const cx<T>*>(vtil), ncx, ncy,
+                                                           reinterpret_cast<const cx<TV>*>(v),
+                                                           reinterpret_cast<cx<T>*>(t), reinterpret_cast<cx<T>*>(rtil));
+  return cudaGetLastError();
+}
+
+template <typename T, typename TV>
+static cudaError_t dpr_t(Ctx& c, const OpDesc& d, const void* vtil, int ncx, int ncy, const void* v, void* t,
+                         void* rtil, int nrhs) {
+  switch (d.R) {
+    case 1: return dpr_r<T, TV, 1>(c, d, vtil, ncx, ncy, v, t, rtil, nrhs);
+    case 2: return dpr_r<T, TV, 2>(c, d, vtil, ncx, ncy, v, t, rtil, nrhs);
+    case 3: return dpr_r<T, TV, 3>(c, d, vtil, ncx, ncy, v, t, rtil, nrhs);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_defl_prolong_resid(Ctx& c, const OpDesc& op, int tcomp, int tv, const void* vtil, int ncx,
+                                      int ncy, const void* v, void* t, void* rtil, int nrhs) {
+  if (tcomp == C128 && tv == C128) return dpr_t<double, double>(c, op, vtil, ncx, ncy, v, t, rtil, nrhs);
+  if (tcomp == C64 && tv == C64) return dpr_t<float, float>(c, op, vtil, ncx, ncy, v, t, rtil, nrhs);
+  if (tcomp == C64 && tv == C128) return dpr_t<float, double>(c, op, vtil, ncx, ncy, v, t, rtil, nrhs);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_defl_prolong(Ctx& c, int dt, int nx, int ny, const void* w, void* t, int nrhs) {
+  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+  size_t n = (size_t)nx * ny;
+  ProfScope ps(c, F_DEFL_PROLONG, (double)nrhs * n * elem_bytes(dt) * 1.25);
+  if (dt == C128)
+    k_defl_prolong<double><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(w), ncx, ncy,
+                                                                    reinterpret_cast<cx<double>*>(t), nx, ny);
+  else
+    k_defl_prolong<float><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<float>*>(w), ncx, ncy,
+                                                                   reinterpret_cast<cx<float>*>(t), nx, ny);
+  return cudaGetLastError();
+}
+
+template <typename TI, typename T>
+static cudaError_t dr_t(Ctx& c, int nx, int ny, const void* v, void* vhat, int nrhs) {
+  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+  constexpr int FW = 2 * RXC + 3, FH = 2 * RYC + 3;
+  size_t sm = sizeof(cx<T>) * (FW * FH + FH * RXC);
+  cudaError_t e = set_smem(k_defl_restrict<TI, T>, sm);
+  if (e != cudaSuccess) return e;
+  ProfScope ps(c, F_DEFL_RESTRICT, (double)nrhs * ((double)nx * ny * sizeof(cx<TI>) + (double)ncx * ncy * sizeof(cx<T>)));
+  dim3 grid((ncx + RXC - 1) / RXC, (ncy + RYC - 1) / RYC, nrhs);
+  k_defl_restrict<TI, T><<<grid, dim3(BX, BY), sm, c.s>>>(reinterpret_cast<const cx<TI>*>(v), nx, ny,
+                                                          reinterpret_cast<cx<T>*>(vhat), ncx, ncy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defl_restrict(Ctx& c, int tin, int tout, int nx, int ny, const void* v, void* vhat, int nrhs) {
+  if (tin == C128 && tout == C128) return dr_t<double, double>(c, nx, ny, v, vhat, nrhs);
+  if (tin == C64 && tout == C64) return dr_t<float, float>(c, nx, ny, v, vhat, nrhs);
+  if (tin == C128 && tout == C64) return dr_t<double, float>(c, nx, ny, v, vhat, nrhs);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int R>
+static cudaError_t down_r(Ctx& c, const OpDesc& d, const void* f, void* fc, double omega, int nrhs) {
+  int ncx = (d.nx + 1) / 2, ncy = (d.ny + 1) / 2;
+  constexpr int OX = 2 * DXC + 1, OY = 2 * DYC + 1;
+  size_t sm = tile_smem_bytes<T, R>(OX, OY) + sizeof(cx<T>) * OX * OY;
+  cudaError_t e = set_smem(k_mg_down<T, R>, sm);
+  if (e != cudaSuccess) return e;
+  ProfScope ps(c, F_MG_DOWN, (double)nrhs * ((double)d.n() * (sizeof(cx<T>) + sizeof(T)) + (double)ncx * ncy * sizeof(cx<T>)));
+  dim3 grid((ncx + DXC - 1) / DXC, (ncy + DYC - 1) / DYC, nrhs);
+  k_mg_down<T, R><<<grid, dim3(BX, BY), sm, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f),
+                                                   reinterpret_cast<cx<T>*>(fc), ncx, ncy, T(omega));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void* fc, double omega, int nrhs) {
+  if (dt == C128) {
+    if (op.R == 1) return down_r<double, 1>(c, op, f, fc, omega, nrhs);
+    if (op.R == 2) return down_r<double, 2>(c, op, f, fc, omega, nrhs);
+    if (op.R == 3) return down_r<double, 3>(c, op, f, fc, omega, nrhs);
+  } else {
+    if (op.R == 1) return down_r<float, 1>(c, op, f, fc, omega, nrhs);
+    if (op.R == 2) return down_r<float, 2>(c, op, f, fc, omega, nrhs);
+    if (op.R == 3) return down_r<float, 3>(c, op, f, fc, omega, nrhs);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int R>
+static cudaError_t up_r(Ctx& c, const OpDesc& d, const void* f, const void* ec, void* y, double omega,
+                        const void* add, int nrhs) {
+  int ncx = (d.nx + 1) / 2, ncy = (d.ny + 1) / 2;
+  const int EW = (OXT + 2 * R) / 2 + 3, EH = (OYT + 2 * R) / 2 + 3;
+  size_t sm = tile_smem_bytes<T, R>(OXT, OYT) + sizeof(cx<T>) * EW * EH;
+  cudaError_t e = set_smem(k_mg_up<T, R>, sm);
+  if (e != cudaSuccess) return e;
+  double bytes = (double)nrhs * ((double)d.n() * (sizeof(cx<T>) * (add ? 3 : 2) + sizeof(T)) + (double)ncx * ncy * sizeof(cx<T>));
+  ProfScope ps(c, F_MG_UP, bytes);
+  dim3 grid((d.nx + OXT - 1) / OXT, (d.ny + OYT - 1) / OYT, nrhs);
+  k_mg_up<T, R><<<grid, dim3(BX, BY), sm, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f),
+                                                 reinterpret_cast<const cx<T>*>(ec), ncx, ncy,
+                                                 reinterpret_cast<cx<T>*>(y), T(omega),
+                                                 reinterpret_cast<const cx<T>*>(add));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const void* ec, void* y, double omega,
+                         const void* add, int tadd, void* yout2, int tout2, int nrhs) {
+  (void)tadd;
+  (void)yout2;
+  (void)tout2;
+  if (dt == C128) {
+    if (op.R == 1) return up_r<double, 1>(c, op, f, ec, y, omega, add, nrhs);
+    if (op.R == 2) return up_r<double, 2>(c, op, f, ec, y, omega, add, nrhs);
+    if (op.R == 3) return up_r<double, 3>(c, op, f, ec, y, omega, add, nrhs);
+  } else {
+    if (op.R == 1) return up_r<float, 1>(c, op, f, ec, y, omega, add, nrhs);
+    if (op.R == 2) return up_r<float, 2>(c, op, f, ec, y, omega, add, nrhs);
+    if (op.R == 3) return up_r<float, 3>(c, op, f, ec, y, omega, add, nrhs);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs) {
+  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+  size_t nc = (size_t)ncx * ncy;
+  ProfScope ps(c, F_MISC, (double)nrhs * ((double)nx * ny + nc) * elem_bytes(dt));
+  if (dt == C128)
+    k_fw<double><<<dim3(grid1d(nc), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(r), nx, ny,
+                                                           reinterpret_cast<cx<double>*>(rc), ncx, ncy);
+  else
+    k_fw<float><<<dim3(grid1d(nc), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<float>*>(r), nx, ny,
+                                                          reinterpret_cast<cx<float>*>(rc), ncx, ncy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs) {
+  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+  size_t n = (size_t)nx * ny;
+  ProfScope ps(c, F_MISC, (double)nrhs * (2.0 * n + (double)ncx * ncy) * elem_bytes(dt));
+  if (dt == C128)
+    k_prolong_add<double><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(ec), ncx, ncy,
+                                                                   reinterpret_cast<cx<double>*>(u), nx, ny);
+  else
+    k_prolong_add<float><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<float>*>(ec), ncx, ncy,
+                                                                  reinterpret_cast<cx<float>*>(u), nx, ny);
+  return cudaGetLastError();
+}
+
+}  // namespace hz

@@ -1,0 +1,364 @@
+// Krylov vector kernels (Algorithm 1 lines 16-23: inner products, Gram-Schmidt updates,
+// norms, the final combination u = u0 + X y) and the dense multigrid coarsest solve.
+//
+// Reductions are deterministic: each CTA writes one partial per coefficient, a second
+// kernel sums the partials in a fixed order.  FP32 vectors accumulate per thread in FP32
+// and reduce across threads in FP64; FP64 vectors use FP64 throughout.
+#include <type_traits>
+
+#include "hz_device.cuh"
+#include "hz_internal.h"
+
+using namespace hzd;
+
+namespace {
+
+constexpr int NT = 256;        // threads per CTA
+constexpr int CV = 8;          // vectors per multi-dot CTA
+constexpr int MAXP = 1216;     // element CTAs (8 per SM)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of `cnt` doubles per thread held in vals[]; result valid in thread 0.
+template <int CNT>
+__device__ __forceinline__ void block_sum(double (&vals)[CNT], double* sm /* 8 * CNT */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < CNT; ++i) {
+    double v = warp_sum(vals[i]);
+    if (lane == 0) sm[wid * CNT + i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      double s = 0;
+      for (int w = 0; w < NT / 32; ++w) s += sm[w * CNT + i];
+      vals[i] = s;
+    }
+  }
+}
+
+inline int nparts(size_t n) {
+  size_t b = (n + NT * 4 - 1) / (NT * 4);
+  if (b > MAXP) b = MAXP;
+  return (int)(b > 0 ? b : 1);
+}
+
+// partial[by * ldp + 2*i + {0,1}] for vectors i of chunk blockIdx.x
+template <typename T>
+__global__ void __launch_bounds__(NT) k_multidot(const cx<T>* __restrict__ V, size_t ldv, int nv,
+                                                 const cx<T>* __restrict__ w, size_t n, double* __restrict__ part,
+                                                 int ldp) {
+  __shared__ double sm[8 * 2 * CV];
+  const int c0 = blockIdx.x * CV;
+  V += (size_t)blockIdx.z * n;
+  w += (size_t)blockIdx.z * n;
+  part += (size_t)blockIdx.z * gridDim.y * ldp;
+  const int cnt = min(CV, nv - c0);
+  T ar[CV], ai[CV];
+#pragma unroll
+  for (int i = 0; i < CV; ++i) ar[i] = ai[i] = T(0);
+  for (size_t e = blockIdx.y * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.y * NT) {
+    cx<T> we = w[e];
+#pragma unroll
+    for (int i = 0; i < CV; ++i) {
+      if (i < cnt) {
+        cx<T> v = V[(size_t)(c0 + i) * ldv + e];
+        ar[i] += v.re * we.re + v.im * we.im;
+        ai[i] += v.re * we.im - v.im * we.re;
+      }
+    }
+  }
+  double vals[2 * CV];
+#pragma unroll
+  for (int i = 0; i < CV; ++i) {
+    vals[2 * i] = double(ar[i]);
+    vals[2 * i + 1] = double(ai[i]);
+  }
+  block_sum<2 * CV>(vals, sm);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < cnt; ++i) {
+      part[(size_t)blockIdx.y * ldp + 2 * (c0 + i)] = vals[2 * i];
+      part[(size_t)blockIdx.y * ldp + 2 * (c0 + i) + 1] = vals[2 * i + 1];
+    }
+  }
+}
+
+// out[j] = sum_b part[b * ldp + j], j < m (fixed order)
+__global__ void __launch_bounds__(NT) k_reduce(const double* __restrict__ part, int nb, int ldp, int m,
+                                               double* __restrict__ out) {
+  __shared__ double sm[8];
+  const int j = blockIdx.x;
+  part += (size_t)blockIdx.y * nb * ldp;
+  out += (size_t)blockIdx.y * m;
+  if (j >= m) return;
+  double s = 0;
+  for (int b = threadIdx.x; b < nb; b += NT) s += part[(size_t)b * ldp + j];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < NT / 32; ++w) t += sm[w];
+    out[j] = t;
+  }
+}
+
+// w -= sum_i coef_i V_i ; optional partial norms of the new w
+template <typename TV, typename TW>
+__global__ void __launch_bounds__(NT) k_update(const cx<TV>* __restrict__ V, size_t ldv, int nv,
+                                               const double* __restrict__ coef, cx<TW>* __restrict__ w, size_t n,
+                                               double* __restrict__ part) {
+  extern __shared__ double scoef[];  // 2 * nv
+  __shared__ double sm[8];
+  V += (size_t)blockIdx.y * n;
+  w += (size_t)blockIdx.y * n;
+  coef += (size_t)blockIdx.y * 2 * nv;
+  if (part) part += (size_t)blockIdx.y * gridDim.x;
+  for (int i = threadIdx.x; i < 2 * nv; i += NT) scoef[i] = coef[i];
+  __syncthreads();
+  using T = typename std::conditional<(sizeof(TW) > sizeof(TV)), TW, TV>::type;
+  T acc = T(0);
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+    cx<T> x = cvt<T>(w[e]);
+    for (int i = 0; i < nv; ++i) {
+      cx<T> v = cvt<T>(V[(size_t)i * ldv + e]);
+      T cr = T(scoef[2 * i]), ci = T(scoef[2 * i + 1]);
+      x.re -= cr * v.re - ci * v.im;
+      x.im -= cr * v.im + ci * v.re;
+    }
+    w[e] = cvt<TW>(x);
+    if (part) acc += x.re * x.re + x.im * x.im;
+  }
+  if (part) {
+    double s = warp_sum(double(acc));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int q = 0; q < NT / 32; ++q) t += sm[q];
+      part[blockIdx.x] = t;
+    }
+  }
+}
+
+// u += sum_i coef_i X_i
+template <typename TX, typename TU>
+__global__ void __launch_bounds__(NT) k_combine(const cx<TX>* __restrict__ X, size_t ldx, int nv,
+                                                const double* __restrict__ coef, cx<TU>* __restrict__ u, size_t n) {
+  extern __shared__ double scoef[];
+  X += (size_t)blockIdx.y * n;
+  u += (size_t)blockIdx.y * n;
+  coef += (size_t)blockIdx.y * 2 * nv;
+  for (int i = threadIdx.x; i < 2 * nv; i += NT) scoef[i] = coef[i];
+  __syncthreads();
+  using T = typename std::conditional<(sizeof(TU) > sizeof(TX)), TU, TX>::type;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+    cx<T> x = cvt<T>(u[e]);
+    for (int i = 0; i < nv; ++i) {
+      cx<T> v = cvt<T>(X[(size_t)i * ldx + e]);
+      T cr = T(scoef[2 * i]), ci = T(scoef[2 * i + 1]);
+      x.re += cr * v.re - ci * v.im;
+      x.im += cr * v.im + ci * v.re;
+    }
+    u[e] = cvt<TU>(x);
+  }
+}
+
+// y = alpha * x, alpha = coef (complex) or 1/sqrt(nrm2) (recip)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_scale(const cx<T>* __restrict__ x, cx<T>* __restrict__ y,
+                                              const double* __restrict__ alpha, int recip, size_t n) {
+  x += (size_t)blockIdx.y * n;
+  y += (size_t)blockIdx.y * n;
+  alpha += (size_t)blockIdx.y * (recip ? 1 : 2);
+  double ar, ai;
+  if (recip) {
+    double s = alpha[0];
+    ar = s > 0 ? 1.0 / sqrt(s) : 0.0;
+    ai = 0;
+  } else {
+    ar = alpha[0];
+    ai = alpha[1];
+  }
+  const T r = T(ar), i_ = T(ai);
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+    cx<T> v = x[e];
+    y[e] = mk<T>(r * v.re - i_ * v.im, r * v.im + i_ * v.re);
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(NT) k_convert(const cx<TX>* __restrict__ x, cx<TY>* __restrict__ y, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) y[e] = cvt<TY>(x[e]);
+}
+
+template <typename TX, typename TZ, typename TY>
+__global__ void __launch_bounds__(NT) k_add(const cx<TX>* __restrict__ x, const cx<TZ>* __restrict__ z,
+                                            cx<TY>* __restrict__ y, size_t n) {
+  using T = typename std::conditional<(sizeof(TX) > sizeof(TZ)), TX, TZ>::type;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT)
+    y[e] = cvt<TY>(cvt<T>(x[e]) + cvt<T>(z[e]));
+}
+
+// y = A x with A dense complex double (row-major n x n); one warp per row; batch in blockIdx.y
+template <typename T>
+__global__ void __launch_bounds__(NT) k_dense(const cx<double>* __restrict__ A, int n, const cx<T>* __restrict__ x,
+                                              cx<T>* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  const size_t off = (size_t)blockIdx.y * n;
+  if (row >= n) return;
+  double sr = 0, si = 0;
+  for (int c = lane; c < n; c += 32) {
+    cx<double> a = A[(size_t)row * n + c];
+    cx<double> v = cvt<double>(x[off + c]);
+    sr += a.re * v.re - a.im * v.im;
+    si += a.re * v.im + a.im * v.re;
+  }
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  if (lane == 0) y[off + row] = cvt<T>(mk<double>(sr, si));
+}
+
+inline unsigned g1(size_t n) {
+  size_t b = (n + NT - 1) / NT;
+  size_t cap = 152 * 8;
+  return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+namespace hz {
+
+size_t dot_ws_bytes(int nv, int nb) {
+  return sizeof(double) * (size_t)MAXP * (2 * (size_t)(nv > 0 ? nv : 1) + 2) * (size_t)(nb > 0 ? nb : 1);
+}
+
+cudaError_t launch_multidot(Ctx& c, int dt, const void* V, size_t ldv, int nv, const void* w, size_t n, int nb,
+                            double* out, void* ws) {
+  if (nv <= 0) return cudaSuccess;
+  int np = nparts(n);
+  int ldp = 2 * nv;
+  double* part = reinterpret_cast<double*>(ws);
+  dim3 grid((nv + CV - 1) / CV, np, nb);
+  {
+    ProfScope ps(c, F_DOT, (double)nb * n * elem_bytes(dt) * (nv + 1));
+    if (dt == C128)
+      k_multidot<double><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv,
+                                               reinterpret_cast<const cx<double>*>(w), n, part, ldp);
+    else
+      k_multidot<float><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv,
+                                              reinterpret_cast<const cx<float>*>(w), n, part, ldp);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ProfScope ps2(c, F_REDUCE, (double)nb * np * ldp * 8);
+  k_reduce<<<dim3(2 * nv, nb), NT, 0, c.s>>>(part, np, ldp, 2 * nv, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, const double* coef, int dtw, void* w,
+                          size_t n, int nb, double* nrm2, void* ws) {
+  unsigned np = (unsigned)nparts(n);
+  double* part = nrm2 ? reinterpret_cast<double*>(ws) : nullptr;
+  size_t sm = sizeof(double) * 2 * (size_t)(nv > 0 ? nv : 1);
+  dim3 grid(np, nb);
+  {
+    ProfScope ps(c, F_AXPY, (double)nb * n * (elem_bytes(dtv) * nv + 2 * elem_bytes(dtw)));
+    if (dtv == C128 && dtw == C128)
+      k_update<double, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv, coef,
+                                                      reinterpret_cast<cx<double>*>(w), n, part);
+    else if (dtv == C64 && dtw == C64)
+      k_update<float, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv, coef,
+                                                    reinterpret_cast<cx<float>*>(w), n, part);
+    else if (dtv == C128 && dtw == C64)
+      k_update<double, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv, coef,
+                                                     reinterpret_cast<cx<float>*>(w), n, part);
+    else
+      k_update<float, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv, coef,
+                                                     reinterpret_cast<cx<double>*>(w), n, part);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !nrm2) return e;
+  ProfScope ps2(c, F_REDUCE, (double)nb * np * 8);
+  k_reduce<<<dim3(1, nb), NT, 0, c.s>>>(part, (int)np, 1, 1, nrm2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(Ctx& c, int dtx, const void* X, size_t ldx, int nv, const double* coef, int dtu, void* u,
+                           size_t n, int nb) {
+  if (nv <= 0) return cudaSuccess;
+  size_t sm = sizeof(double) * 2 * (size_t)nv;
+  ProfScope ps(c, F_AXPY, (double)nb * n * (elem_bytes(dtx) * nv + 2 * elem_bytes(dtu)));
+  dim3 grid(g1(n), nb);
+  if (dtx == C128 && dtu == C128)
+    k_combine<double, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(X), ldx, nv, coef,
+                                                     reinterpret_cast<cx<double>*>(u), n);
+  else if (dtx == C64 && dtu == C64)
+    k_combine<float, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(X), ldx, nv, coef,
+                                                   reinterpret_cast<cx<float>*>(u), n);
+  else if (dtx == C64 && dtu == C128)
+    k_combine<float, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(X), ldx, nv, coef,
+                                                    reinterpret_cast<cx<double>*>(u), n);
+  else
+    k_combine<double, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(X), ldx, nv, coef,
+                                                    reinterpret_cast<cx<float>*>(u), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_dev(Ctx& c, int dt, const void* x, void* y, const double* alpha_dev, int recip, size_t n,
+                             int nb) {
+  ProfScope ps(c, F_AXPY, (double)nb * n * 2 * elem_bytes(dt));
+  dim3 grid(g1(n), nb);
+  if (dt == C128)
+    k_scale<double><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(x), reinterpret_cast<cx<double>*>(y),
+                                          alpha_dev, recip, n);
+  else
+    k_scale<float><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<float>*>(x), reinterpret_cast<cx<float>*>(y),
+                                         alpha_dev, recip, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(Ctx& c, int tx, int ty, const void* x, void* y, size_t n) {
+  ProfScope ps(c, F_MISC, (double)n * (elem_bytes(tx) + elem_bytes(ty)));
+  if (tx == C128 && ty == C64)
+    k_convert<double, float><<<g1(n), NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(x), reinterpret_cast<cx<float>*>(y), n);
+  else if (tx == C64 && ty == C128)
+    k_convert<float, double><<<g1(n), NT, 0, c.s>>>(reinterpret_cast<const cx<float>*>(x), reinterpret_cast<cx<double>*>(y), n);
+  else
+    return cudaMemcpyAsync(y, x, n * elem_bytes(tx), cudaMemcpyDeviceToDevice, c.s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(Ctx& c, int tx, const void* x, int tz, const void* z, int ty, void* y, size_t n) {
+  ProfScope ps(c, F_MISC, (double)n * (elem_bytes(tx) + elem_bytes(tz) + elem_bytes(ty)));
+#define HZ_ADD(A, B, C)                                                                                      \
+  k_add<A, B, C><<<g1(n), NT, 0, c.s>>>(reinterpret_cast<const cx<A>*>(x), reinterpret_cast<const cx<B>*>(z), \
+                                        reinterpret_cast<cx<C>*>(y), n)
+  if (tx == C64 && tz == C64 && ty == C64) HZ_ADD(float, float, float);
+  else if (tx == C128 && tz == C128 && ty == C128) HZ_ADD(double, double, double);
+  else if (tx == C64 && tz == C64 && ty == C128) HZ_ADD(float, float, double);
+  else return cudaErrorInvalidValue;
+#undef HZ_ADD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, void* y, int nrhs) {
+  dim3 grid((n + NT / 32 - 1) / (NT / 32), nrhs);
+  ProfScope ps(c, F_DENSE, (double)n * n * 16.0);
+  if (dt == C128)
+    k_dense<double><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(A), n,
+                                          reinterpret_cast<const cx<double>*>(x), reinterpret_cast<cx<double>*>(y));
+  else
+    k_dense<float><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(A), n,
+                                         reinterpret_cast<const cx<float>*>(x), reinterpret_cast<cx<float>*>(y));
+  return cudaGetLastError();
+}
+
+}  // namespace hz

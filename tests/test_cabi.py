@@ -1,0 +1,76 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and exports every
+function include/hz.h declares; argument validation answers before any device work."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hz.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\*?\s+\*?(hz_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2412_04980_gb300 import build
+    build.build()
+    import paper_2412_04980_gb300 as hz
+    return hz.lib()
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for required in ("hz_setup", "hz_apply", "hz_precond", "hz_solve", "hz_destroy", "hz_strerror"):
+        assert required in names
+    assert len(names) >= 20
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_config_defaults(L):
+    import paper_2412_04980_gb300 as hz
+    c = hz.config()
+    assert (c.beta1, c.beta2, c.restart, c.l2_tol, c.cslp_tol, c.c_it, c.mg_omega) == (1.0, 0.5, 30, 0.3, 0.1, 6.0, 0.8)
+    assert c.mg_max_level == 2 and c.mg_nu1 == 1 and c.mg_nu2 == 1 and c.max_rhs == 1
+
+
+def test_strerror_names_every_status(L):
+    for s in range(9):
+        assert L.hz_strerror(s).decode().startswith("HZ_")
+
+
+def test_setup_rejects_bad_arguments_before_device_work(L):
+    import paper_2412_04980_gb300 as hz
+    h = ctypes.c_void_p()
+    cfg = hz.config(levels=2)
+    bad_grid = hz.HzGrid(2, 9, 0.1, 0)
+    assert L.hz_setup(ctypes.byref(bad_grid), ctypes.c_void_p(1), ctypes.byref(cfg), None, ctypes.byref(h)) == hz.HZ_EINVAL
+    even = hz.HzGrid(10, 9, 0.1, 0)
+    assert L.hz_setup(ctypes.byref(even), ctypes.c_void_p(1), ctypes.byref(cfg), None, ctypes.byref(h)) == hz.HZ_EINVAL
+    neg_h = hz.HzGrid(9, 9, -1.0, 0)
+    assert L.hz_setup(ctypes.byref(neg_h), ctypes.c_void_p(1), ctypes.byref(cfg), None, ctypes.byref(h)) == hz.HZ_EINVAL
+    cfg_bad = hz.config(levels=0)
+    ok = hz.HzGrid(9, 9, 0.1, 0)
+    assert L.hz_setup(ctypes.byref(ok), ctypes.c_void_p(1), ctypes.byref(cfg_bad), None, ctypes.byref(h)) == hz.HZ_EINVAL
+    assert L.hz_setup(None, None, None, None, None) == hz.HZ_EINVAL
+    assert L.hz_apply(None, None, None, 1) == hz.HZ_EINVAL
+    assert "null" in L.hz_last_error().decode()
+
+
+def test_kernel_families(L):
+    n = L.hz_kernel_family_count()
+    names = [L.hz_kernel_family_name(i).decode() for i in range(n)]
+    assert "mg_down" in names and "level_op" in names

@@ -1,0 +1,204 @@
+"""GPU parity of each hot-path building block against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import model_problems as mp
+from gpu_common import (TOL32, TOL32_COMPOSITE, TOL64, TOL64_COMPOSITE, dev, host, hzlib, rel_inf, round32,
+                        round32r, torch)
+from oracle import operators as O
+from oracle import transfers as T
+from oracle.madp import Hierarchy, MADPConfig, krylov_cap
+from oracle.multigrid import CSLPMultigrid
+
+pytestmark = pytest.mark.gpu
+
+SHIFT = 1.0 + 0.5j
+
+
+@pytest.fixture(scope="module")
+def hz():
+    return hzlib()
+
+
+def handle(hz, k, h, **cfg):
+    return hz.Helmholtz(dev(k), h, **cfg)
+
+
+# ---- a1: fine Helmholtz apply ------------------------------------------------------------
+@pytest.mark.parametrize("ny,nx", [(19, 37), (129, 129), (3, 3), (257, 65), (1025, 1025)])
+def test_apply_fp64_sommerfeld(hz, ny, nx):
+    h = 1.0 / (nx - 1)
+    k = mp.random_k(ny, nx, seed=1)
+    u = mp.random_complex((ny, nx), seed=2)
+    H = handle(hz, k, h)
+    y = host(H.apply(dev(u)))
+    assert rel_inf(y, O.apply_helmholtz(u, k, h)) <= TOL64
+
+
+def test_apply_fp64_dirichlet(hz):
+    ny, nx = 31, 45
+    h = 1.0 / (nx + 1)
+    k = mp.random_k(ny, nx, seed=3)
+    u = mp.random_complex((ny, nx), seed=4)
+    H = handle(hz, k, h, bc="dirichlet")
+    assert rel_inf(host(H.apply(dev(u))), O.apply_helmholtz(u, k, h, bc=O.DIRICHLET)) <= TOL64
+
+
+def test_apply_dirichlet_eigenpair(hz):
+    n, kv = 63, 7.0
+    h = 1.0 / (n + 1)
+    x = h * np.arange(1, n + 1)
+    X, Y = np.meshgrid(x, x)
+    phi = (np.sin(3 * np.pi * X) * np.sin(5 * np.pi * Y)).astype(np.complex128)
+    lam = 4 / h ** 2 * (np.sin(3 * np.pi * h / 2) ** 2 + np.sin(5 * np.pi * h / 2) ** 2) - kv ** 2
+    H = handle(hz, np.full((n, n), kv), h, bc="dirichlet")
+    assert rel_inf(host(H.apply(dev(phi))), lam * phi) <= 1e-11
+
+
+def test_apply_batched_equals_single(hz):
+    ny, nx = 33, 65
+    k = mp.random_k(ny, nx, seed=5)
+    u = mp.random_complex((3, ny, nx), seed=6)
+    H = handle(hz, k, 0.1)
+    yb = host(H.apply(dev(u)))
+    for r in range(3):
+        assert np.array_equal(yb[r], host(H.apply(dev(u[r]))))
+
+
+# ---- a1/a2/a8: level operators A_l, M_l ------------------------------------------------------
+@pytest.mark.parametrize("level", [1, 2, 3, 4])
+@pytest.mark.parametrize("op", ["A", "M"])
+def test_level_apply_fp64(hz, level, op):
+    ny, nx = 161, 97                      # levels: 161x97, 81x49, 41x25, 21x13
+    h = 0.01
+    k = mp.random_k(ny, nx, seed=7, kmin=10, kmax=40)
+    H = handle(hz, k, h, levels=4)
+    cy, cx = H.level_size(level)
+    kl = T.inject(k, 2 ** (level - 1))
+    u = mp.random_complex((cy, cx), seed=8 + level)
+    y = host(H.level_apply(level, dev(u), op))
+    ref = O.apply_level(u, kl, level, h, 1.0 if op == "A" else SHIFT)
+    assert rel_inf(y, ref) <= TOL64
+
+
+@pytest.mark.parametrize("level", [1, 2, 3, 4])
+def test_level_apply_fp32(hz, level):
+    ny, nx = 161, 97
+    h = 0.01
+    k = mp.random_k(ny, nx, seed=7, kmin=10, kmax=40)
+    H = handle(hz, k, h, levels=4, precision="mixed")
+    cy, cx = H.level_size(level)
+    kl = round32r(T.inject(k, 2 ** (level - 1)))
+    u = round32(mp.random_complex((cy, cx), seed=8 + level))
+    y = host(H.level_apply(level, dev(u, torch.complex64), "M"))
+    assert rel_inf(y, O.apply_level(u, kl, level, h, SHIFT)) <= TOL32
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_level_jacobi(hz, level):
+    ny, nx = 81, 145
+    h = 0.02
+    k = mp.random_k(ny, nx, seed=9, kmin=5, kmax=25)
+    H = handle(hz, k, h, levels=3)
+    cy, cx = H.level_size(level)
+    kl = T.inject(k, 2 ** (level - 1))
+    u = mp.random_complex((cy, cx), seed=10)
+    f = mp.random_complex((cy, cx), seed=11)
+    y = host(H.level_jacobi(level, dev(u), dev(f)))
+    ref = O.jacobi(u, f, lambda x: O.apply_level(x, kl, level, h, SHIFT), O.diag_level(kl, level, h, SHIFT), 0.8)
+    assert rel_inf(y, ref) <= TOL64
+
+
+# ---- a6/a7: deflation transfers ---------------------------------------------------------------
+@pytest.mark.parametrize("ny,nx", [(19, 37), (129, 257), (1025, 513)])
+def test_defl_restrict_and_prolong(hz, ny, nx):
+    k = mp.random_k(ny, nx, seed=12)
+    H = handle(hz, k, 0.1, levels=2)
+    v = mp.random_complex((ny, nx), seed=13)
+    assert rel_inf(host(H.defl_restrict(1, dev(v))), T.deflation_restrict(v)) <= TOL64
+    w = mp.random_complex(((ny + 1) // 2, (nx + 1) // 2), seed=14)
+    assert rel_inf(host(H.defl_prolong(1, dev(w))), T.deflation_prolong(w, (ny, nx))) <= TOL64
+    v32 = round32(v)
+    assert rel_inf(host(H.defl_restrict(1, dev(v32, torch.complex64))), T.deflation_restrict(v32)) <= TOL32
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_defl_prolong_residual(hz, level):
+    ny, nx = 161, 97
+    h = 0.01
+    k = mp.random_k(ny, nx, seed=15, kmin=10, kmax=40)
+    H = handle(hz, k, h, levels=4)
+    cy, cx = H.level_size(level)
+    kl = T.inject(k, 2 ** (level - 1))
+    vtil = mp.random_complex(((cy + 1) // 2, (cx + 1) // 2), seed=16)
+    v = mp.random_complex((cy, cx), seed=17)
+    t, r = H.defl_prolong_residual(level, dev(vtil), dev(v))
+    t_ref = T.deflation_prolong(vtil, (cy, cx))
+    assert rel_inf(host(t), t_ref) <= TOL64
+    assert rel_inf(host(r), v - O.apply_level(t_ref, kl, level, h, 1.0)) <= TOL64
+
+
+# ---- a2-a5: multigrid CSLP V-cycle ----------------------------------------------------------------
+@pytest.mark.parametrize("level,shape", [(1, (129, 129)), (1, (289, 161)), (2, (257, 257))])
+def test_mg_vcycle_fp64(hz, level, shape):
+    ny, nx = shape
+    h = 1.0 / 128
+    k = mp.random_k(ny, nx, seed=18, kmin=5, kmax=0.3 / h)
+    H = handle(hz, k, h, levels=2)
+    cy, cx = H.level_size(level)
+    kl = T.inject(k, 2 ** (level - 1))
+    f = mp.random_complex((cy, cx), seed=19)
+    mg = CSLPMultigrid(kl, level, h, SHIFT)
+    assert len(mg.levels) == len([1 for m in range(12) if _mg_exists(H, level, m)])
+    y = host(H.mg_vcycle(level, dev(f)))
+    assert rel_inf(y, mg(f)) <= TOL64_COMPOSITE
+
+
+def _mg_exists(H, level, m):
+    try:
+        H.mg_size(level, m)
+        return True
+    except Exception:
+        return False
+
+
+def test_mg_vcycle_fp32(hz):
+    ny = nx = 257
+    h = 1.0 / 256
+    k = round32r(mp.random_k(ny, nx, seed=20, kmin=5, kmax=0.3 / h))
+    H = handle(hz, k, h, levels=2, precision="mixed")
+    f = round32(mp.random_complex((ny, nx), seed=21))
+    mg = CSLPMultigrid(k, 1, h, SHIFT)
+    y = host(H.mg_vcycle(1, dev(f, torch.complex64)))
+    assert rel_inf(y, mg(f)) <= TOL32_COMPOSITE
+
+
+def test_mg_vcycle_general_path_matches(hz):
+    """nu1 = nu2 = 1 through the general (unfused) kernels equals the fused path's oracle;
+    nu1 = 2, nu2 = 1 matches the oracle with the same sweeps."""
+    ny = nx = 129
+    h = 1.0 / 128
+    k = mp.random_k(ny, nx, seed=22, kmin=5, kmax=30)
+    f = mp.random_complex((ny, nx), seed=23)
+    H = handle(hz, k, h, levels=2, mg_nu1=2, mg_nu2=1)
+    mg = CSLPMultigrid(k, 1, h, SHIFT, nu1=2, nu2=1)
+    assert rel_inf(host(H.mg_vcycle(1, dev(f))), mg(f)) <= TOL64_COMPOSITE
+
+
+# ---- a9: CSLP inverse by GMRES (levels >= 3) -------------------------------------------------------
+@pytest.mark.parametrize("level", [3, 4])
+def test_cslp_gmres_fp64(hz, level):
+    ny, nx = 257, 257
+    h = 5.0
+    p = mp.random_field(257, h, seed=3, kh_max=0.3, levels=4)
+    H = handle(hz, p.k, h, levels=4)
+    cy, cx = H.level_size(level)
+    kl = T.inject(p.k, 2 ** (level - 1))
+    b = mp.random_complex((cy, cx), seed=24)
+    hier = Hierarchy(p.k, h, MADPConfig(levels=4))
+    x_ref = hier.cslp_inverse(level, b)
+    its_ref = hier.stats.cslp_gmres_iterations[level]
+    x, its = H.cslp_gmres(level, dev(b))
+    assert its[0] == its_ref
+    assert rel_inf(host(x), x_ref) <= TOL64_COMPOSITE
+    assert its_ref <= krylov_cap(6.0, cy * cx)

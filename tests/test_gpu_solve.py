@@ -1,0 +1,90 @@
+"""GPU parity of the preconditioner and the full solver against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import model_problems as mp
+from gpu_common import TOL64_COMPOSITE, dev, host, hzlib, rel2, rel_inf, torch
+from oracle.madp import Hierarchy, MADPConfig
+from oracle.operators import apply_helmholtz
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hz():
+    return hzlib()
+
+
+def _cfg(p):
+    return MADPConfig(levels=p.levels, negdef_from_level=p.negdef_from_level)
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_precond_fp64(hz, levels):
+    p = mp.random_field(129, 5.0, seed=3, kh_max=0.3, levels=levels, negdef_from_level=4)
+    v = mp.random_complex((129, 129), seed=30)
+    hier = Hierarchy(p.k, p.h, MADPConfig(levels=levels, negdef_from_level=4))
+    ref = hier.precond(1, v)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=levels, negdef_from_level=4)
+    x = host(H.precond(dev(v)))
+    assert rel_inf(x, ref) <= TOL64_COMPOSITE
+
+
+def _solve_case(hz, p, precision):
+    hier = Hierarchy(p.k, p.h, _cfg(p))
+    ref, rst = hier.solve(p.b[0])
+    H = hz.Helmholtz(dev(p.k), p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=precision)
+    u, st = H.solve(dev(p.b[0]), tol=1e-6)
+    u = host(u)
+    r = p.b[0] - apply_helmholtz(u, p.k, p.h)
+    true_rel = np.linalg.norm(r) / np.linalg.norm(p.b[0])
+    return u, st[0], ref, rst, true_rel
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_mp1b_129(hz, precision):
+    """Constant k = 20 on 129^2 nodes, two-level deflation (the smallest benchmark case)."""
+    p = mp.named("mp1b_129")
+    u, st, ref, rst, true_rel = _solve_case(hz, p, precision)
+    assert st["status"] == 0 and true_rel <= 1e-6
+    assert abs(st["true_relres"] - true_rel) <= 1e-9
+    assert rel2(u, ref) <= 1e-5
+    assert abs(st["outer_iterations"] - rst.outer_iterations) <= 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_wedge_289x481(hz, precision):
+    """Synthetic wedge, 289 x 481 nodes, f = 20 Hz, four levels."""
+    p = mp.named("wedge_289x481")
+    u, st, ref, rst, true_rel = _solve_case(hz, p, precision)
+    assert st["status"] == 0 and true_rel <= 1e-6
+    assert rel2(u, ref) <= 1e-5
+    assert abs(st["outer_iterations"] - rst.outer_iterations) <= 1
+
+
+def test_solve_batched_equals_alone(hz):
+    """Three right-hand sides in one lockstep batch give the same result as each alone."""
+    p = mp.random_field(129, 5.0, seed=3, kh_max=0.3, levels=3, negdef_from_level=4, nsrc=3)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=3, negdef_from_level=4, precision="mixed", max_rhs=3)
+    ub, stb = H.solve(dev(p.b), tol=1e-6)
+    ub = host(ub)
+    for r in range(3):
+        u1, st1 = H.solve(dev(p.b[r]), tol=1e-6)
+        assert np.array_equal(host(u1), ub[r])
+        assert st1[0]["outer_iterations"] == stb[r]["outer_iterations"]
+
+
+def test_zero_rhs(hz):
+    p = mp.mp1b(32, 10.0)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=2)
+    u, st = H.solve(torch.zeros((33, 33), dtype=torch.complex128, device="cuda"))
+    assert st[0]["status"] == 0 and st[0]["outer_iterations"] == 0
+    assert not host(u).any()
+
+
+def test_solve_host_matches_device(hz):
+    p = mp.mp1b(64, 12.0)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=2, precision="mixed")
+    ud, _ = H.solve(dev(p.b[0]))
+    uh, st = H.solve_host(p.b[0])
+    assert np.array_equal(host(ud), uh)
