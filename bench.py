@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-1e-6-residual and solves/s of the multilevel deflation solver on GB300.
+
+One step = one full solve (hz_solve) of the workload to a 1e-6 relative residual, the
+right-hand side already resident in device memory.  Default workload: the 4097 x 4097
+seeded random-velocity model (k_max h = 0.3, source at the top centre), 6-level MADP,
+mixed precision (FP32 preconditioner, FP64 outer FGMRES).
+
+Printed JSON line (rank 0):
+  value            solves/s of the whole job (all ranks; replicas, no collective)
+  ms_per_step      mean time-to-solution
+  time_to_solution p50 / p99 over the timed steps
+  fp64_gpu         the plain FP64 GPU solver on the same workload (one solve)
+  e2e              hz_solve_host: host b -> device, solve, device u -> host, per step
+  roofline         the dominant kernel family, algorithmic bytes / event-timed duration
+  cpu_baseline     the FP64 oracle on the host cores, a bounded sample scaled to a solve
+  clocks           nvidia-smi samples taken during the timed region
+
+--impl reference times only the oracle (rank 0), with the same metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "random_4097": "4097x4097 seeded random-velocity model (layered 1500-4500 m/s + Gaussian field, "
+                   "corr. 200 m, sigma 400 m/s, clipped 1500-5500), h = 5 m, k_max h = 0.3, point source at "
+                   "the top centre, 6-level MADP, tol 1e-6",
+    "wedge_289x481": "289x481 synthetic three-layer wedge, f = 20 Hz, kh_max = 0.1745, 4-level MADP, tol 1e-6",
+    "mp1b_129": "129x129 constant k = 20, point source at the centre, 2-level, tol 1e-6",
+    "random_1025": "1025x1025 seeded random-velocity model, k_max h = 0.3, 4-level MADP, tol 1e-6",
+}
+METRIC = "solves/s at a 1e-6 relative residual (time-to-solution = ms_per_step)"
+COUNTS_FILE = os.path.join(ROOT, "profiles", "solve_counts.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="random_4097", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--out", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------- oracle leg
+def oracle_sample(workload: str, counts: dict) -> dict:
+    """Time each oracle primitive once at every level size of the workload (one core) and
+    scale by the per-solve operation counts of the method: the oracle's time-to-solution
+    estimate.  Runs in a fresh single-threaded interpreter."""
+    import numpy as np
+
+    import model_problems as mp
+    from oracle import operators as O
+    from oracle import transfers as T
+    from oracle.madp import MADPConfig
+    from oracle.multigrid import CSLPMultigrid
+
+    p = mp.named(workload)
+    cfg = MADPConfig(levels=p.levels, negdef_from_level=p.negdef_from_level)
+    ml = p.levels
+    shift = complex(cfg.beta1, cfg.beta2)
+    t_total = time.perf_counter()
+    unit = {}
+    u = mp.random_complex((p.ny, p.nx), seed=1)
+    k = p.k
+    for l in range(1, ml + 1):
+        kl = T.inject(k, 2 ** (l - 1))
+        ul = u
+        t = time.perf_counter()
+        O.apply_level(ul, kl, l, p.h, 1.0)
+        unit[f"A{l}"] = time.perf_counter() - t
+        if l <= cfg.mg_max_level:
+            mg = CSLPMultigrid(kl, l, p.h, shift, cfg.mg_omega, cfg.mg_nu1, cfg.mg_nu2, cfg.mg_coarsest_side)
+            t = time.perf_counter()
+            mg(ul)
+            unit[f"V{l}"] = time.perf_counter() - t
+        t = time.perf_counter()
+        hdot = np.vdot(ul, ul)
+        _ = ul - hdot * ul
+        unit[f"G{l}"] = time.perf_counter() - t                  # one MGS step: dot + axpy
+        if l < ml:
+            t = time.perf_counter()
+            v = T.deflation_restrict(ul)
+            unit[f"Zt{l}"] = time.perf_counter() - t
+            t = time.perf_counter()
+            T.deflation_prolong(v, ul.shape)
+            unit[f"Z{l}"] = time.perf_counter() - t
+            u = v
+    sample_s = time.perf_counter() - t_total
+    est = 0.0
+    for l in range(1, ml + 1):
+        its = counts["outer"] if l == 1 else counts["level_iterations"][l - 1]
+        calls = 1 if l == 1 else max(counts["level_calls"][l - 1], 1)
+        per_it = unit[f"A{l}"]
+        if l < ml:
+            per_it += unit[f"Zt{l}"] + unit[f"Z{l}"] + unit[f"A{l}"]
+        if l <= cfg.mg_max_level:
+            per_it += unit[f"V{l}"]
+        kk = its / calls
+        est += its * per_it + calls * kk * (kk + 1) / 2 * unit[f"G{l}"]
+        g = counts["cslp_gmres_iterations"][l - 1]
+        if l > cfg.mg_max_level and its > 0:
+            kg = g / its
+            est += g * unit[f"A{l}"] + its * kg * (kg + 1) / 2 * unit[f"G{l}"]
+    est += unit["A1"]                                            # true residual
+    return {"est_s_per_solve": est, "sample_s": sample_s, "unit_s": unit, "cores": 1}
+
+
+def run_oracle_sample(workload: str, counts: dict) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    with tempfile.TemporaryDirectory() as d:
+        cpath, opath = os.path.join(d, "c.json"), os.path.join(d, "o.json")
+        with open(cpath, "w") as f:
+            json.dump(counts, f)
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, "--out", opath]
+        r = subprocess.run(cmd, env=dict(env, HZ_COUNTS=cpath), capture_output=True, text=True, timeout=900)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr[-2000:])
+        with open(opath) as f:
+            return json.load(f)
+
+
+def load_counts(workload: str):
+    if os.path.exists(COUNTS_FILE):
+        with open(COUNTS_FILE) as f:
+            allc = json.load(f)
+        return allc.get(workload)
+    return None
+
+
+def cpu_line(workload, res, steps_note):
+    est = res["est_s_per_solve"]
+    return {"value": 1.0 / est, "unit": "solves/s", "cores": res["cores"], "kind": "oracle",
+            "sample": f"each oracle primitive (A_l, V-cycle, Z^T, Z, MGS step) timed once at every level size of "
+                      f"{workload} ({res['sample_s']:.1f} s of CPU work), scaled by the solve's per-level "
+                      f"iteration counts to {est:.0f} s per solve{steps_note}",
+            "est_s_per_solve": est}
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- GPU arm
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2412_04980_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        with open(os.environ["HZ_COUNTS"]) as f:
+            counts = json.load(f)
+        res = oracle_sample(args.oracle_sample, counts)
+        with open(args.out, "w") as f:
+            json.dump(res, f)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        counts = load_counts(args.workload)
+        if counts is None:
+            print(json.dumps({"impl": "reference", "unavailable": "no per-solve iteration counts recorded for "
+                                                                   f"{args.workload}"}))
+            return
+        times = []
+        res = None
+        for s in range(args.warmup + args.steps):
+            res = run_oracle_sample(args.workload, counts)
+            if s >= args.warmup:
+                times.append(res["est_s_per_solve"])
+        est = statistics.mean(times)
+        line = {"impl": "reference", "metric": METRIC, "value": 1.0 / est, "unit": "solves/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+                "cpu_baseline": cpu_line(args.workload, dict(res, est_s_per_solve=est), ""),
+                "e2e": {"value": 1.0 / est, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+
+    import model_problems as mp
+    import paper_2412_04980_gb300 as hz
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    p = mp.named(args.workload)
+    k = torch.from_numpy(p.k).to(dev)
+    b = torch.from_numpy(p.b[0]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision)
+    u = torch.empty_like(b)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    mem_gb = H.memory_bytes() / 1e9
+    for _ in range(args.warmup):
+        _, st = H.solve(b, u, tol=1e-6)
+    # which kernel family dominates (one profiled solve, not timed)
+    fams = H.kernel_families()
+    for f in range(len(fams)):
+        H.profile_enable(f, True)
+    H.solve(b, u, tol=1e-6)
+    fam_ms = {}
+    for f in range(len(fams)):
+        n, ms, by = H.profile_read(f)
+        fam_ms[fams[f]] = (ms, n, by)
+        H.profile_enable(f, False)
+    dom = max(fam_ms, key=lambda x: fam_ms[x][0])
+    dom_id = fams.index(dom)
+    H.profile_enable(dom_id, True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = H.launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stats = []
+    ev[0].record(stream)
+    for s in range(args.steps):
+        _, st = H.solve(b, u, tol=1e-6)
+        ev[s + 1].record(stream)
+        stats.append(st[0])
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = H.launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    n_dom, ms_dom, by_dom = H.profile_read(dom_id)
+    H.profile_enable(dom_id, False)
+    assert all(s["status"] == 0 and s["true_relres"] <= 1e-6 for s in stats), stats
+
+    # end to end through the host-buffer entry point
+    b_host = torch.from_numpy(p.b[0]).pin_memory().numpy()
+    e2e_t = []
+    for s in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        uh, st_h = H.solve_host(b_host, tol=1e-6)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t[1:]) if len(e2e_t) > 1 else e2e_t[0]
+    nbytes = p.nx * p.ny * 16
+
+    fp64 = None
+    if not args.no_fp64 and rank == 0 and args.precision != "fp64":
+        H.close()
+        torch.cuda.empty_cache()
+        H64 = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="fp64")
+        H64.solve(b, u, tol=1e-6)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st64 = H64.solve(b, u, tol=1e-6)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64 = {"s_per_solve": e0.elapsed_time(e1) / 1e3, "outer_iterations": st64[0]["outer_iterations"],
+                "true_relres": st64[0]["true_relres"]}
+        H64.close()
+
+    counts = {"outer": stats[-1]["outer_iterations"], "level_iterations": stats[-1]["level_iterations"],
+              "level_calls": stats[-1]["level_calls"],
+              "cslp_gmres_iterations": stats[-1]["cslp_gmres_iterations"]}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            cpu = cpu_line(args.workload, run_oracle_sample(args.workload, counts), "")
+        except Exception as e:  # report, do not hide
+            cpu = {"error": str(e)[-300:]}
+
+    if rank != 0:
+        return
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
+        try:
+            peaks = json.load(f)
+        except Exception:
+            peaks = {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = (by_dom / 1e9) / (ms_dom / 1e3) if ms_dom > 0 else None
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        ent = tr.get(dom)
+        if ent and ent.get("kernel_hash") == kernel_source_hash() and ent.get("workload") == args.workload:
+            traffic = ent.get("bytes_per_launch")
+    t_sorted = sorted(step_ms)
+    value = world * args.steps / total_s
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (FP32 preconditioner, FP64 outer FGMRES)" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
+                   "levels": p.levels, "nrhs": 1, "precision": args.precision,
+                   "l2": f"inputs larger than L2: b is {nbytes / 1e6:.0f} MB and the solver touches "
+                         f"{mem_gb:.1f} GB of workspace per solve",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_solution_s": {"p50": statistics.median(step_ms) / 1e3,
+                               "p99": t_sorted[min(len(t_sorted) - 1, math.ceil(0.99 * len(t_sorted)) - 1)] / 1e3},
+        "iterations": {"outer": counts["outer"], "level2": counts["level_iterations"][1],
+                       "true_relres": stats[-1]["true_relres"]},
+        "fp64_gpu": fp64,
+        "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                     "launches": n_dom, "avg_launch_us": ms_dom * 1e3 / max(n_dom, 1),
+                     "share_of_step": ms_dom / max(sum(step_ms), 1e-9),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "kernel_ms_per_solve": {f: round(v[0], 3) for f, v in fam_ms.items()},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -212,6 +212,10 @@ int hz_profile_read(hz_handle h, int family, long long* launches, double* ms, do
 const char* hz_kernel_family_name(int family);
 int hz_kernel_family_count(void);
 
+/* Number of CUDA kernels this handle has launched since hz_setup (every launch of the
+ * library's own kernels on the handle's stream, including the set-up launches). */
+int hz_launch_count(hz_handle h, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,7 @@ _SIGS = {
                              ctypes.POINTER(_D)]),
     "hz_kernel_family_name": (ctypes.c_char_p, [_I]),
     "hz_kernel_family_count": (_I, []),
+    "hz_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _LIB = None
@@ -332,6 +333,11 @@ class Helmholtz:
         its = (ctypes.c_int * n)()
         _check(lib().hz_cslp_gmres(self._h, level, self._dt(b), _ptr(b), _ptr(x), n, its), "hz_cslp_gmres")
         return x, list(its)
+
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        _check(lib().hz_launch_count(self._h, ctypes.byref(n)), "hz_launch_count")
+        return n.value
 
     # -- per-kernel timing ----------------------------------------------------------------
     @staticmethod

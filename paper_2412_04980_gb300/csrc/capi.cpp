@@ -378,6 +378,13 @@ int hz_profile_read(hz_handle hp, int family, long long* launches, double* ms, d
   return HZ_OK;
 }
 
+int hz_launch_count(hz_handle hp, long long* launches) {
+  GUARD_HANDLE(hp);
+  if (!launches) return bad("null argument");
+  *launches = H_->prof.total_launches;
+  return HZ_OK;
+}
+
 const char* hz_kernel_family_name(int family) { return family_name(family); }
 int hz_kernel_family_count(void) { return F_COUNT; }
 

@@ -78,6 +78,7 @@ Prof::~Prof() {
   for (auto e : pool) cudaEventDestroy(e);
 }
 ProfScope::ProfScope(Ctx& c_, int fam_, double bytes_) : c(c_), fam(fam_), bytes(bytes_) {
+  if (c.prof) c.prof->total_launches += 1;
   if (c.prof && c.prof->on[fam]) {
     a = c.prof->get();
     if (a) cudaEventRecord(a, c.s);

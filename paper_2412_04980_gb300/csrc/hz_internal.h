@@ -36,6 +36,7 @@ struct Prof {
   long long launches[F_COUNT] = {};
   double ms[F_COUNT] = {};
   double bytes[F_COUNT] = {};
+  long long total_launches = 0;   // every kernel launch through a launcher, profiled or not
   std::vector<cudaEvent_t> pool;
   cudaEvent_t get();
   void drain(int fam);   // synchronous: folds pending records into the totals
