@@ -195,6 +195,24 @@ int hz_mg_size(hz_handle h, int level, int mg_level, int* nx, int* ny);
 int hz_cslp_gmres(hz_handle h, int level, int dtype, const void* b, void* x, int nrhs,
                   int* iterations);
 
+/* ---- allocation-free check -------------------------------------------------------- */
+
+/* Largest nrhs accepted by hz_true_residual_noalloc. */
+#define HZ_NOALLOC_MAX_RHS 64
+
+/* relres_dev[r] = ||b_r - A_h u_r||_2 / ||b_r||_2 (||b_r - A_h u_r||_2 if b_r = 0) for
+ * r < nrhs, in FP64, computed without allocating any device memory.  The paper has no
+ * counterpart: this call exists for callers that cannot call cudaMalloc where they
+ * check a solution (e.g. a plugin whose host application owns every device
+ * allocation, or a loop that must not enter the allocator).
+ * b, u: nrhs * nx * ny HZ_C128 device vectors; relres_dev: nrhs device doubles.
+ * Scratch is a static device array of 1216 * 2 * HZ_NOALLOC_MAX_RHS doubles (1.25 MB)
+ * that every GPU loading the library keeps until exit; the first call on a device looks
+ * up its address (make that first call before any stream capture).  All calls share
+ * the array, so calls that overlap on the GPU race and must be serialised by the caller.
+ * Errors: HZ_EINVAL (null pointer, nrhs < 1 or > HZ_NOALLOC_MAX_RHS), HZ_ECUDA. */
+int hz_true_residual_noalloc(hz_handle h, const void* b, const void* u, int nrhs, double* relres_dev);
+
 /* ---- diagnostics ------------------------------------------------------------------- */
 
 /* Name of a status code. */

@@ -104,6 +104,7 @@ _SIGS = {
     "hz_kernel_family_name": (ctypes.c_char_p, [_I]),
     "hz_kernel_family_count": (_I, []),
     "hz_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "hz_true_residual_noalloc": (_I, [_P, _P, _P, _I, _P]),
 }
 
 _LIB = None
