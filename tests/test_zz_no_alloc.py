@@ -33,12 +33,14 @@ def test_noalloc_residual_matches_solver_report():
     assert np.all(want <= 1e-6) and np.all(want > 0)
     first = _noalloc(hz, H, b, u, 3)
     second = _noalloc(hz, H, b, u, 3)                      # two calls in a row share the array
+    # both values are ||b - A u|| / ||b||; the residual b - A u carries rounding relative to
+    # ||b|| (not to the small residual), so they agree to TOL64 in units of ||b||
     for got in (first, second):
-        assert np.all(np.abs(got - want) <= TOL64 * want + 1e-300), (got, want)
+        assert np.all(np.abs(got - want) <= TOL64), (got, want)
     # a different input through the same static array, then the first input again
     z = torch.zeros_like(u)
     np.testing.assert_allclose(_noalloc(hz, H, b, z, 3), 1.0, rtol=TOL64)
-    assert np.all(np.abs(_noalloc(hz, H, b, u, 3) - want) <= TOL64 * want)
+    assert np.all(np.abs(_noalloc(hz, H, b, u, 3) - want) <= TOL64)
 
 
 def test_noalloc_rejects_oversized_batch():
