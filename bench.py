@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply"],
+                    help="time one building block on the workload's finest grid instead of a solve")
+    ap.add_argument("--repeat", type=int, default=20)
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--out", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -222,6 +225,51 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def micro(args):
+    """One building block on the workload's finest grid, repeated; per-family event timing.
+    gmres: the CSLP inverse by GMRES (forced on level 1 with mg_max_level = 0);
+    vcycle: one multigrid V-cycle; apply: the level-1 operator."""
+    import torch
+
+    import model_problems as mp
+    import paper_2412_04980_gb300 as hz
+
+    p = mp.named(args.workload)
+    dev = torch.device("cuda", 0)
+    k = torch.from_numpy(p.k).to(dev)
+    prec = args.precision
+    cdt = torch.complex64 if prec == "mixed" else torch.complex128
+    extra = {"mg_max_level": 0} if args.micro == "gmres" else {}
+    H = hz.Helmholtz(k, p.h, levels=1, precision=prec, **extra)
+    f = torch.from_numpy(mp.random_complex((p.ny, p.nx), seed=7)).to(dev)
+    if args.micro != "apply":
+        f = f.to(cdt)
+    fams = H.kernel_families()
+    run = {"gmres": lambda: H.cslp_gmres(1, f), "vcycle": lambda: H.mg_vcycle(1, f),
+           "apply": lambda: H.apply(f)}[args.micro]
+    for _ in range(args.warmup):
+        out = run()
+    torch.cuda.synchronize()
+    for i in range(len(fams)):
+        H.profile_enable(i, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.repeat):
+        out = run()
+    e1.record()
+    torch.cuda.synchronize()
+    res = {"micro": args.micro, "workload": args.workload, "precision": prec, "repeat": args.repeat,
+           "ms_per_call": e0.elapsed_time(e1) / args.repeat}
+    if args.micro == "gmres":
+        res["iterations"] = out[1]
+    for i in range(len(fams)):
+        n, ms, by = H.profile_read(i)
+        if n:
+            res[fams[i]] = {"launches": n, "ms": round(ms, 3), "avg_us": round(1e3 * ms / n, 2),
+                            "GB/s": round(by / ms / 1e6, 1)}
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -231,6 +279,9 @@ def main():
         with open(args.out, "w") as f:
             json.dump(res, f)
         return
+
+    if args.micro:
+        return micro(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,10 +342,14 @@ def main():
     for f in range(len(fams)):
         H.profile_enable(f, True)
     H.solve(b, u, tol=1e-6)
-    fam_ms = {}
+    fam_ms, lev_ms = {}, {}
     for f in range(len(fams)):
         n, ms, by = H.profile_read(f)
         fam_ms[fams[f]] = (ms, n, by)
+        for lv in range(1, p.levels + 1):
+            nl, msl, byl = H.profile_read(f + 256 * lv)
+            if nl:
+                lev_ms.setdefault(str(lv), {})[fams[f]] = [round(msl, 3), nl, round(byl / max(msl, 1e-9) / 1e6, 1)]
         H.profile_enable(f, False)
     dom = max(fam_ms, key=lambda x: fam_ms[x][0])
     dom_id = fams.index(dom)
@@ -406,6 +461,8 @@ def main():
                      "share_of_step": ms_dom / max(sum(step_ms), 1e-9),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "kernel_ms_per_solve": {f: round(v[0], 3) for f, v in fam_ms.items()},
+        "kernel_ms_launches_gbs_by_level": lev_ms,
+        "counts": counts,
         "cpu_baseline": cpu,
         "clocks": clk,
     }

@@ -224,7 +224,8 @@ const char* hz_last_error(void);
 /* Per-kernel timing with CUDA events on the handle's stream: enable records an event
  * pair around every launch of the kernel family `family` (see hz_kernel_family_name);
  * read returns the number of launches, their summed milliseconds and their summed
- * algorithmic bytes since enable.  Reading synchronises the stream. */
+ * algorithmic bytes since enable; hz_profile_read also accepts family + 256 * l to read
+ * only the launches made for deflation level l (1-based).  Reading synchronises the stream. */
 int hz_profile_enable(hz_handle h, int family, int enable);
 int hz_profile_read(hz_handle h, int family, long long* launches, double* ms, double* bytes);
 const char* hz_kernel_family_name(int family);

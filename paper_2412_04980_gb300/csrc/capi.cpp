@@ -362,19 +362,26 @@ int hz_profile_enable(hz_handle hp, int family, int enable) {
     H_->prof.launches[family] = 0;
     H_->prof.ms[family] = 0;
     H_->prof.bytes[family] = 0;
+    for (int l = 0; l < kProfLevels; ++l) {
+      H_->prof.launches_lv[family][l] = 0;
+      H_->prof.ms_lv[family][l] = 0;
+      H_->prof.bytes_lv[family][l] = 0;
+    }
   }
   return HZ_OK;
 }
 
 int hz_profile_read(hz_handle hp, int family, long long* launches, double* ms, double* bytes) {
   GUARD_HANDLE(hp);
-  if (family < 0 || family >= F_COUNT) return bad("unknown kernel family");
+  const int fam = family & 0xff, lev = family >> 8;
+  if (fam < 0 || fam >= F_COUNT || lev < 0 || lev >= kProfLevels) return bad("unknown kernel family or level");
   int st = status_of(cudaStreamSynchronize(H_->ctx.s), "hz_profile_read");
   if (st) return st;
-  H_->prof.drain(family);
-  if (launches) *launches = H_->prof.launches[family];
-  if (ms) *ms = H_->prof.ms[family];
-  if (bytes) *bytes = H_->prof.bytes[family];
+  H_->prof.drain(fam);
+  const Prof& P = H_->prof;
+  if (launches) *launches = lev ? P.launches_lv[fam][lev] : P.launches[fam];
+  if (ms) *ms = lev ? P.ms_lv[fam][lev] : P.ms[fam];
+  if (bytes) *bytes = lev ? P.bytes_lv[fam][lev] : P.bytes[fam];
   return HZ_OK;
 }
 

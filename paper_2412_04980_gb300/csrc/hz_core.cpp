@@ -63,6 +63,10 @@ void Prof::drain(int fam) {
       ms[fam] += ms_;
       launches[fam] += 1;
       bytes[fam] += r.bytes;
+      int lv = (r.level >= 0 && r.level < kProfLevels) ? r.level : 0;
+      ms_lv[fam][lv] += ms_;
+      launches_lv[fam][lv] += 1;
+      bytes_lv[fam][lv] += r.bytes;
     }
     pool.push_back(r.a);
     pool.push_back(r.b);
@@ -77,7 +81,7 @@ Prof::~Prof() {
     }
   for (auto e : pool) cudaEventDestroy(e);
 }
-ProfScope::ProfScope(Ctx& c_, int fam_, double bytes_) : c(c_), fam(fam_), bytes(bytes_) {
+ProfScope::ProfScope(Ctx& c_, int fam_, double bytes_) : c(c_), fam(fam_), bytes(bytes_), level(c_.level) {
   if (c.prof) c.prof->total_launches += 1;
   if (c.prof && c.prof->on[fam]) {
     a = c.prof->get();
@@ -89,7 +93,7 @@ ProfScope::~ProfScope() {
   cudaEvent_t b = c.prof->get();
   if (!b) return;
   cudaEventRecord(b, c.s);
-  c.prof->pending[fam].push_back({a, b, bytes});
+  c.prof->pending[fam].push_back({a, b, bytes, level});
   if (c.prof->pending[fam].size() > 8192) c.prof->drain(fam);
 }
 
@@ -431,6 +435,7 @@ void destroy(Handle* h) {
 // ---------------------------------------------------------------------------------- V-cycle
 // One V(nu1, nu2) cycle approximating M_l^-1 f (zero initial guess); out = cycle [+ add].
 int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, int nb) {
+  LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
   Ctx& c = h->ctx;
   const double om = h->cfg.mg_omega;
@@ -560,27 +565,39 @@ static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, voi
     if (X) CS(prec(Vj, Xj));
     CS(op(Xj, w));
     const int nv = j + 1;
+    // Gram-Schmidt with selective reorthogonalisation ("twice is enough", eta = 1/sqrt(2)):
+    // pass 1 returns h = V^H w and ||w||^2; a second classical pass runs only for the
+    // right-hand sides whose norm dropped below eta ||w|| (decided on the device).
+    const int ldA = 2 * nv + 1;
     double* hA = sc.dev + sc.hA;
-    double* hB = hA + (size_t)nb * 2 * nv;
-    double* nr = hB + (size_t)nb * 2 * nv;
-    CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hA, h->ws));
-    CK(launch_update(c, dvec, V, bn, nv, hA, dvec, w, n, nb, nullptr, h->ws));
-    CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hB, h->ws));
-    CK(launch_update(c, dvec, V, bn, nv, hB, dvec, w, n, nb, nr, h->ws));
-    const size_t cnt = (size_t)nb * 4 * nv + nb;
+    double* hB = hA + (size_t)nb * ldA;
+    double* n1 = hB + (size_t)nb * 2 * nv;
+    double* n2 = n1 + nb;
+    double* flag = n2 + nb;
+    CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hA, h->ws, 1));
+    CK(launch_update(c, dvec, V, bn, nv, hA, ldA, dvec, w, n, nb, n1, h->ws));
+    CK(launch_dgks_flag(c, hA + 2 * nv, ldA, n1, flag, nb, 0.5));
+    CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hB, h->ws, 0, flag));
+    CK(launch_update(c, dvec, V, bn, nv, hB, 2 * nv, dvec, w, n, nb, n2, h->ws, flag));
+    const size_t cnt = (size_t)nb * (ldA + 2 * nv + 3);
     CK(cudaMemcpyAsync(sc.host, hA, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.s));
     CS(wait_event(h, sc.ev));
     const double* hAh = sc.host;
-    const double* hBh = hAh + (size_t)nb * 2 * nv;
-    const double* nrh = hBh + (size_t)nb * 2 * nv;
+    const double* hBh = hAh + (size_t)nb * ldA;
+    const double* n1h = hBh + (size_t)nb * 2 * nv;
+    const double* n2h = n1h + nb;
+    const double* flh = n2h + nb;
+    std::vector<double> nrh(nb);
+    for (int b = 0; b < nb; ++b) nrh[b] = flh[b] != 0.0 ? n1h[b] : n2h[b];
     nact = 0;
     for (int b = 0; b < nb; ++b) {
       if (!act[b]) continue;
       std::vector<cd>& Hb = H[b];
       auto at = [&](int r, int col) -> cd& { return Hb[(size_t)col * (m + 1) + r]; };
+      const bool second = flh[b] == 0.0;
       for (int i = 0; i <= j; ++i)
-        at(i, j) = cd(hAh[(size_t)b * 2 * nv + 2 * i] + hBh[(size_t)b * 2 * nv + 2 * i],
-                      hAh[(size_t)b * 2 * nv + 2 * i + 1] + hBh[(size_t)b * 2 * nv + 2 * i + 1]);
+        at(i, j) = cd(hAh[(size_t)b * ldA + 2 * i] + (second ? hBh[(size_t)b * 2 * nv + 2 * i] : 0.0),
+                      hAh[(size_t)b * ldA + 2 * i + 1] + (second ? hBh[(size_t)b * 2 * nv + 2 * i + 1] : 0.0));
       double hn = nrh[b] > 0 ? std::sqrt(nrh[b]) : 0.0;
       at(j + 1, j) = hn;
       // apply previous rotations
@@ -662,6 +679,7 @@ static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, voi
 
 // CSLP inverse by unpreconditioned GMRES on M_l (levels > mg_max_level): x += GMRES(b).
 int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
+  LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
   const int dt = L.dpre;
   OpDesc M = L.opM(dt, h->cfg.beta1, h->cfg.beta2);
@@ -692,6 +710,7 @@ int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add,
 
 // x = P v at level l (Algorithm 1 lines 5-15).  v has dtype dv; x has dtype lv[l-1].dx.
 int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
+  LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
   Ctx& c = h->ctx;
   const int ml = h->cfg.levels;
@@ -712,6 +731,7 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
 
 // v_til ~ A_l^-1 b on level l >= 2 with the MADP schedule; reads lv[l-1].b, writes .x
 int coarse_solve(Handle* h, int l, int nb) {
+  LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
   const hz_config& cfg = h->cfg;
   const int ml = cfg.levels;
@@ -742,6 +762,7 @@ int coarse_solve(Handle* h, int l, int nb) {
 
 // ---------------------------------------------------------------------------------- solve
 int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags) {
+  LevelTag tag(h->ctx, 1);
   Level& L = h->lv[0];
   Ctx& c = h->ctx;
   const hz_config& cfg = h->cfg;

@@ -68,6 +68,7 @@ struct OpP {
   T H;              // ghost spacing (2 H i k)
   T ks;             // wavenumber-stencil sum
   T sr, si;         // sigma
+  T ksr, ksi;       // ks * sigma
   T m[7], l[7];     // 1-D masks, index d + R (R >= 2)
   const T* k;       // wavenumber, nx*ny
 };
@@ -230,13 +231,14 @@ __device__ __forceinline__ cx<T> tile_op(const TileView<T, R>& t, const OpP<T>& 
   const int gx = t.ox0 + ox, gy = t.oy0 + oy;
   const cx<T>* uc = t.U + (oy + R) * WX + (ox + R);
   if (R == 1 || bsides(P, gx, gy) > 0) {
-    cx<T> s = (uc[1] + uc[-1]) + (uc[WX] + uc[-WX]);
-    T k = P.k[(size_t)gy * P.nx + gx];
-    T k2 = P.ks * k * k;
-    cx<T> lap = mk<T>(T(4) * uc->re - s.re, T(4) * uc->im - s.im);
-    // c * lap - sigma * ks * k^2 * u
-    T ar = k2 * P.sr, ai = k2 * P.si;
-    return mk<T>(P.c * lap.re - (ar * uc->re - ai * uc->im), P.c * lap.im - (ar * uc->im + ai * uc->re));
+    // c (4 u - s) - sigma ks k^2 u = (4c - sr ks k^2) u - i si ks k^2 u - c s
+    const cx<T> s = (uc[1] + uc[-1]) + (uc[WX] + uc[-WX]);
+    const T k = P.k[(size_t)gy * P.nx + gx];
+    const T k2 = k * k;
+    const T dr = fma(-P.ksr, k2, T(4) * P.c);
+    const T di = P.ksi * k2;
+    const cx<T> u = *uc;
+    return mk<T>(fma(dr, u.re, fma(di, u.im, -P.c * s.re)), fma(dr, u.im, fma(-di, u.re, -P.c * s.im)));
   } else {
     const int OX = t.OX;
     cx<T> lap = mk<T>(T(0), T(0)), kk = lap;

@@ -29,13 +29,17 @@ enum Family {
 };
 const char* family_name(int f);
 
+constexpr int kProfLevels = 11;  // index 0: not inside a level; 1..10: deflation level
 struct Prof {
-  struct Rec { cudaEvent_t a, b; double bytes; };
+  struct Rec { cudaEvent_t a, b; double bytes; int level; };
   bool on[F_COUNT] = {};
   std::vector<Rec> pending[F_COUNT];
   long long launches[F_COUNT] = {};
   double ms[F_COUNT] = {};
   double bytes[F_COUNT] = {};
+  long long launches_lv[F_COUNT][kProfLevels] = {};
+  double ms_lv[F_COUNT][kProfLevels] = {};
+  double bytes_lv[F_COUNT][kProfLevels] = {};
   long long total_launches = 0;   // every kernel launch through a launcher, profiled or not
   std::vector<cudaEvent_t> pool;
   cudaEvent_t get();
@@ -46,6 +50,15 @@ struct Prof {
 struct Ctx {
   cudaStream_t s = 0;
   Prof* prof = nullptr;
+  int level = 0;  // deflation level whose work is being launched (profiling attribution)
+};
+
+// Sets Ctx::level for the lifetime of the object and restores the previous value.
+struct LevelTag {
+  Ctx& c;
+  int prev;
+  LevelTag(Ctx& c_, int l) : c(c_), prev(c_.level) { c.level = l; }
+  ~LevelTag() { c.level = prev; }
 };
 
 // RAII-free launch timer: begin() returns an index, end() closes it.
@@ -53,6 +66,7 @@ struct ProfScope {
   Ctx& c;
   int fam;
   double bytes;
+  int level;
   cudaEvent_t a = nullptr;
   ProfScope(Ctx& c_, int fam_, double bytes_);
   ~ProfScope();
@@ -105,11 +119,15 @@ cudaError_t launch_add(Ctx& c, int tx, const void* x, int tz, const void* z, int
 // (elements), so a batch of one vector index is nb*n contiguous elements.
 // Multi-dot: out[b*2nv + 2i + {0,1}] = sum_e conj(V_i^b[e]) w^b[e] (double), ws: dot_ws_bytes(nv, nb).
 size_t dot_ws_bytes(int nv, int nb);
+// with_norm: also out[b*(2nv+1) + 2nv] = ||w^b||^2 (the per-rhs stride becomes 2nv+1).
+// skip (optional, per rhs): a non-zero entry makes the kernel return without work.
 cudaError_t launch_multidot(Ctx& c, int dt, const void* V, size_t ldv, int nv, const void* w, size_t n, int nb,
-                            double* out, void* ws);
-// w^b (dtw) -= sum_i coef[b*2nv + 2i..] V_i^b (dtv); optionally ||w^b||^2 into nrm2[b] (device doubles).
-cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, const double* coef, int dtw, void* w,
-                          size_t n, int nb, double* nrm2, void* ws);
+                            double* out, void* ws, int with_norm = 0, const double* skip = nullptr);
+// w^b (dtw) -= sum_i coef[b*ldc + 2i..] V_i^b (dtv); optionally ||w^b||^2 into nrm2[b] (device doubles).
+cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, const double* coef, int ldc, int dtw,
+                          void* w, size_t n, int nb, double* nrm2, void* ws, const double* skip = nullptr);
+// flag[b] = 1.0 when n1[b] >= eta2 * wn[b*ldw] (second Gram-Schmidt pass not needed), else 0.0
+cudaError_t launch_dgks_flag(Ctx& c, const double* wn, int ldw, const double* n1, double* flag, int nb, double eta2);
 // u^b (dtu) += sum_i coef[b*2nv + 2i..] X_i^b (dtx)
 cudaError_t launch_combine(Ctx& c, int dtx, const void* X, size_t ldx, int nv, const double* coef, int dtu, void* u,
                            size_t n, int nb);

@@ -30,6 +30,8 @@ OpP<T> make_op(const hz::OpDesc& d) {
   p.ks = T(d.ks);
   p.sr = T(d.sr);
   p.si = T(d.si);
+  p.ksr = T(d.ks * d.sr);
+  p.ksi = T(d.ks * d.si);
   for (int i = 0; i < 7; ++i) {
     p.m[i] = T(d.m[i]);
     p.l[i] = T(d.l[i]);

@@ -23,24 +23,38 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-wide sum of `cnt` doubles per thread held in vals[]; result valid in thread 0.
-template <int CNT>
-__device__ __forceinline__ void block_sum(double (&vals)[CNT], double* sm /* 8 * CNT */) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Warp transpose-reduction of CNT values held by every lane (CNT a power of two <= 32):
+// after it, lane l (l < CNT) holds the warp sum of value (l % CNT).  Each halving step
+// exchanges half of the remaining values, so a lane performs CNT - 1 + log2(32/CNT) adds
+// instead of 5 * CNT for independent butterfly sums.
+template <typename T, int CNT>
+__device__ __forceinline__ T warp_transpose_sum(T (&v)[CNT]) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int i = 0; i < CNT; ++i) {
-    double v = warp_sum(vals[i]);
-    if (lane == 0) sm[wid * CNT + i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  for (int half = CNT / 2; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) != 0;
 #pragma unroll
-    for (int i = 0; i < CNT; ++i) {
-      double s = 0;
-      for (int w = 0; w < NT / 32; ++w) s += sm[w * CNT + i];
-      vals[i] = s;
+    for (int i = 0; i < half; ++i) {
+      T send = upper ? v[i] : v[i + half];
+      T keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
     }
   }
+  T x = v[0];
+#pragma unroll
+  for (int o = CNT; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;  // lane l holds the sum of value index (l & (CNT-1)) -- after the transposition
+}
+
+// Which original value index ends up in lane slot q after warp_transpose_sum<CNT>.
+template <int CNT>
+__device__ __forceinline__ int slot_value(int q) {
+  // at each halving step with width `half`, lanes with (lane & half) keep the upper half;
+  // the kept index is v[i + half] for those lanes, so bit `half` of the lane selects it.
+  int idx = 0;
+  for (int half = CNT / 2; half >= 1; half >>= 1)
+    if (q & half) idx += half;
+  return idx;
 }
 
 inline int nparts(size_t n) {
@@ -53,18 +67,23 @@ inline int nparts(size_t n) {
 template <typename T>
 __global__ void __launch_bounds__(NT) k_multidot(const cx<T>* __restrict__ V, size_t ldv, int nv,
                                                  const cx<T>* __restrict__ w, size_t n, double* __restrict__ part,
-                                                 int ldp) {
+                                                 int ldp, int with_norm, const double* __restrict__ skip) {
   __shared__ double sm[8 * 2 * CV];
+  __shared__ double snorm[NT / 32];
+  if (skip && skip[blockIdx.z] != 0.0) return;
   const int c0 = blockIdx.x * CV;
+  const bool do_norm = with_norm && blockIdx.x == 0;
   V += (size_t)blockIdx.z * n;
   w += (size_t)blockIdx.z * n;
   part += (size_t)blockIdx.z * gridDim.y * ldp;
   const int cnt = min(CV, nv - c0);
   T ar[CV], ai[CV];
+  T wn = T(0);
 #pragma unroll
   for (int i = 0; i < CV; ++i) ar[i] = ai[i] = T(0);
   for (size_t e = blockIdx.y * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.y * NT) {
     cx<T> we = w[e];
+    if (do_norm) wn += we.re * we.re + we.im * we.im;
 #pragma unroll
     for (int i = 0; i < CV; ++i) {
       if (i < cnt) {
@@ -74,18 +93,33 @@ __global__ void __launch_bounds__(NT) k_multidot(const cx<T>* __restrict__ V, si
       }
     }
   }
-  double vals[2 * CV];
+  T vals[2 * CV];
 #pragma unroll
   for (int i = 0; i < CV; ++i) {
-    vals[2 * i] = double(ar[i]);
-    vals[2 * i + 1] = double(ai[i]);
+    vals[2 * i] = ar[i];
+    vals[2 * i + 1] = ai[i];
   }
-  block_sum<2 * CV>(vals, sm);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < cnt; ++i) {
-      part[(size_t)blockIdx.y * ldp + 2 * (c0 + i)] = vals[2 * i];
-      part[(size_t)blockIdx.y * ldp + 2 * (c0 + i) + 1] = vals[2 * i + 1];
-    }
+  // value index held by this lane after the transposition: bit-reversed halving order
+  const T ws = warp_transpose_sum<T, 2 * CV>(vals);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane < 2 * CV) sm[wid * 2 * CV + lane] = double(ws);
+  if (do_norm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+    if (lane == 0) snorm[wid] = double(wn);
+  }
+  __syncthreads();
+  if (do_norm && threadIdx.x == 0) {
+    double t = 0;
+    for (int w2 = 0; w2 < NT / 32; ++w2) t += snorm[w2];
+    part[(size_t)blockIdx.y * ldp + 2 * nv] = t;
+  }
+  if (threadIdx.x < 2 * CV) {
+    const int q = threadIdx.x;          // slot; its value index is slot_value(q)
+    double t = 0;
+    for (int w = 0; w < NT / 32; ++w) t += sm[w * 2 * CV + q];
+    const int vi = slot_value<2 * CV>(q);
+    if ((vi >> 1) < cnt) part[(size_t)blockIdx.y * ldp + 2 * c0 + vi] = t;
   }
 }
 
@@ -112,23 +146,25 @@ __global__ void __launch_bounds__(NT) k_reduce(const double* __restrict__ part, 
 // w -= sum_i coef_i V_i ; optional partial norms of the new w
 template <typename TV, typename TW>
 __global__ void __launch_bounds__(NT) k_update(const cx<TV>* __restrict__ V, size_t ldv, int nv,
-                                               const double* __restrict__ coef, cx<TW>* __restrict__ w, size_t n,
-                                               double* __restrict__ part) {
+                                               const double* __restrict__ coef, int ldc, cx<TW>* __restrict__ w,
+                                               size_t n, double* __restrict__ part, const double* __restrict__ skip) {
   extern __shared__ double scoef[];  // 2 * nv
   __shared__ double sm[8];
+  if (skip && skip[blockIdx.y] != 0.0) return;
   V += (size_t)blockIdx.y * n;
   w += (size_t)blockIdx.y * n;
-  coef += (size_t)blockIdx.y * 2 * nv;
+  coef += (size_t)blockIdx.y * ldc;
   if (part) part += (size_t)blockIdx.y * gridDim.x;
-  for (int i = threadIdx.x; i < 2 * nv; i += NT) scoef[i] = coef[i];
-  __syncthreads();
   using T = typename std::conditional<(sizeof(TW) > sizeof(TV)), TW, TV>::type;
+  T* sc = reinterpret_cast<T*>(scoef);  // coefficients converted once to the arithmetic type
+  for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(coef[i]);
+  __syncthreads();
   T acc = T(0);
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
     cx<T> x = cvt<T>(w[e]);
     for (int i = 0; i < nv; ++i) {
       cx<T> v = cvt<T>(V[(size_t)i * ldv + e]);
-      T cr = T(scoef[2 * i]), ci = T(scoef[2 * i + 1]);
+      T cr = sc[2 * i], ci = sc[2 * i + 1];
       x.re -= cr * v.re - ci * v.im;
       x.im -= cr * v.im + ci * v.re;
     }
@@ -136,7 +172,9 @@ __global__ void __launch_bounds__(NT) k_update(const cx<TV>* __restrict__ V, siz
     if (part) acc += x.re * x.re + x.im * x.im;
   }
   if (part) {
-    double s = warp_sum(double(acc));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    double s = double(acc);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -147,6 +185,13 @@ __global__ void __launch_bounds__(NT) k_update(const cx<TV>* __restrict__ V, siz
   }
 }
 
+// flag[b] = 1 (skip the second Gram-Schmidt pass) when ||w'||^2 >= eta2 ||w||^2
+__global__ void k_dgks(const double* __restrict__ wn, int ldw, const double* __restrict__ n1, double* __restrict__ flag,
+                       int nb, double eta2) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nb) flag[b] = (n1[b] >= eta2 * wn[(size_t)b * ldw]) ? 1.0 : 0.0;
+}
+
 // u += sum_i coef_i X_i
 template <typename TX, typename TU>
 __global__ void __launch_bounds__(NT) k_combine(const cx<TX>* __restrict__ X, size_t ldx, int nv,
@@ -155,14 +200,15 @@ __global__ void __launch_bounds__(NT) k_combine(const cx<TX>* __restrict__ X, si
   X += (size_t)blockIdx.y * n;
   u += (size_t)blockIdx.y * n;
   coef += (size_t)blockIdx.y * 2 * nv;
-  for (int i = threadIdx.x; i < 2 * nv; i += NT) scoef[i] = coef[i];
-  __syncthreads();
   using T = typename std::conditional<(sizeof(TU) > sizeof(TX)), TU, TX>::type;
+  T* sc = reinterpret_cast<T*>(scoef);
+  for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(coef[i]);
+  __syncthreads();
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
     cx<T> x = cvt<T>(u[e]);
     for (int i = 0; i < nv; ++i) {
       cx<T> v = cvt<T>(X[(size_t)i * ldx + e]);
-      T cr = T(scoef[2 * i]), ci = T(scoef[2 * i + 1]);
+      T cr = sc[2 * i], ci = sc[2 * i + 1];
       x.re += cr * v.re - ci * v.im;
       x.im += cr * v.im + ci * v.re;
     }
@@ -241,30 +287,30 @@ size_t dot_ws_bytes(int nv, int nb) {
 }
 
 cudaError_t launch_multidot(Ctx& c, int dt, const void* V, size_t ldv, int nv, const void* w, size_t n, int nb,
-                            double* out, void* ws) {
+                            double* out, void* ws, int with_norm, const double* skip) {
   if (nv <= 0) return cudaSuccess;
   int np = nparts(n);
-  int ldp = 2 * nv;
+  int ldp = 2 * nv + (with_norm ? 1 : 0);
   double* part = reinterpret_cast<double*>(ws);
   dim3 grid((nv + CV - 1) / CV, np, nb);
   {
     ProfScope ps(c, F_DOT, (double)nb * n * elem_bytes(dt) * (nv + 1));
     if (dt == C128)
       k_multidot<double><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv,
-                                               reinterpret_cast<const cx<double>*>(w), n, part, ldp);
+                                               reinterpret_cast<const cx<double>*>(w), n, part, ldp, with_norm, skip);
     else
       k_multidot<float><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv,
-                                              reinterpret_cast<const cx<float>*>(w), n, part, ldp);
+                                              reinterpret_cast<const cx<float>*>(w), n, part, ldp, with_norm, skip);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ProfScope ps2(c, F_REDUCE, (double)nb * np * ldp * 8);
-  k_reduce<<<dim3(2 * nv, nb), NT, 0, c.s>>>(part, np, ldp, 2 * nv, out);
+  k_reduce<<<dim3(ldp, nb), NT, 0, c.s>>>(part, np, ldp, ldp, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, const double* coef, int dtw, void* w,
-                          size_t n, int nb, double* nrm2, void* ws) {
+cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, const double* coef, int ldc, int dtw,
+                          void* w, size_t n, int nb, double* nrm2, void* ws, const double* skip) {
   unsigned np = (unsigned)nparts(n);
   double* part = nrm2 ? reinterpret_cast<double*>(ws) : nullptr;
   size_t sm = sizeof(double) * 2 * (size_t)(nv > 0 ? nv : 1);
@@ -272,22 +318,28 @@ cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, co
   {
     ProfScope ps(c, F_AXPY, (double)nb * n * (elem_bytes(dtv) * nv + 2 * elem_bytes(dtw)));
     if (dtv == C128 && dtw == C128)
-      k_update<double, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv, coef,
-                                                      reinterpret_cast<cx<double>*>(w), n, part);
+      k_update<double, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv, coef, ldc,
+                                                      reinterpret_cast<cx<double>*>(w), n, part, skip);
     else if (dtv == C64 && dtw == C64)
-      k_update<float, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv, coef,
-                                                    reinterpret_cast<cx<float>*>(w), n, part);
+      k_update<float, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv, coef, ldc,
+                                                    reinterpret_cast<cx<float>*>(w), n, part, skip);
     else if (dtv == C128 && dtw == C64)
-      k_update<double, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv, coef,
-                                                     reinterpret_cast<cx<float>*>(w), n, part);
+      k_update<double, float><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<double>*>(V), ldv, nv, coef, ldc,
+                                                     reinterpret_cast<cx<float>*>(w), n, part, skip);
     else
-      k_update<float, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv, coef,
-                                                     reinterpret_cast<cx<double>*>(w), n, part);
+      k_update<float, double><<<grid, NT, sm, c.s>>>(reinterpret_cast<const cx<float>*>(V), ldv, nv, coef, ldc,
+                                                     reinterpret_cast<cx<double>*>(w), n, part, skip);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !nrm2) return e;
   ProfScope ps2(c, F_REDUCE, (double)nb * np * 8);
   k_reduce<<<dim3(1, nb), NT, 0, c.s>>>(part, (int)np, 1, 1, nrm2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dgks_flag(Ctx& c, const double* wn, int ldw, const double* n1, double* flag, int nb, double eta2) {
+  ProfScope ps(c, F_REDUCE, (double)nb * 24);
+  k_dgks<<<(nb + 127) / 128, 128, 0, c.s>>>(wn, ldw, n1, flag, nb, eta2);
   return cudaGetLastError();
 }
 
