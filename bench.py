@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--reorth-eta", type=float, default=None,
+                    help="Gram-Schmidt reorthogonalisation threshold (library default if omitted)")
     ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply"],
                     help="time one building block on the workload's finest grid instead of a solve")
     ap.add_argument("--repeat", type=int, default=20)
@@ -327,7 +329,9 @@ def main():
     k = torch.from_numpy(p.k).to(dev)
     b = torch.from_numpy(p.b[0]).to(dev)
     stream = torch.cuda.current_stream(dev)
-    H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision)
+    extra = {} if args.reorth_eta is None else {"reorth_eta": args.reorth_eta}
+    H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision,
+                     **extra)
     u = torch.empty_like(b)
 
     def barrier():
@@ -396,7 +400,8 @@ def main():
     if not args.no_fp64 and rank == 0 and args.precision != "fp64":
         H.close()
         torch.cuda.empty_cache()
-        H64 = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="fp64")
+        H64 = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="fp64",
+                           **extra)
         H64.solve(b, u, tol=1e-6)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -444,7 +449,7 @@ def main():
         "dtype": "f32+f64 (FP32 preconditioner, FP64 outer FGMRES)" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
-                   "levels": p.levels, "nrhs": 1, "precision": args.precision,
+                   "levels": p.levels, "nrhs": 1, "precision": args.precision, "reorth_eta": H.cfg.reorth_eta,
                    "l2": f"inputs larger than L2: b is {nbytes / 1e6:.0f} MB and the solver touches "
                          f"{mem_gb:.1f} GB of workspace per solve",
                    "parallelism": f"replicas x{world}"},

@@ -62,6 +62,8 @@ int hz_config_init(hz_config* c) {
   c->mg_coarsest_side = 20;
   c->max_rhs = 1;
   c->timeout_s = 600.0;
+  c->device_gmres = 1;
+  c->reorth_eta = 0.1;
   return HZ_OK;
 }
 
@@ -80,6 +82,7 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
     return bad("invalid multigrid or Krylov-cap parameter");
   if (c.mg_max_level < 0 || c.mg_coarsest_side < 3) return bad("invalid multigrid level settings");
   if (!(c.timeout_s > 0)) return bad("timeout_s must be positive");
+  if (!(c.reorth_eta >= 0 && c.reorth_eta <= 1)) return bad("reorth_eta must be in [0, 1]");
   if (g.bc == HZ_BC_DIRICHLET && c.levels != 1) return bad("Dirichlet grids support the level-1 operator only");
   int nx = g.nx, ny = g.ny;
   for (int l = 1; l < c.levels; ++l) {
@@ -167,10 +170,14 @@ int hz_precond(hz_handle hp, const void* v, void* x, int nrhs) {
   if (int s = check_nrhs(H_, nrhs, true)) return s;
   Level& L = H_->lv[0];
   for (int q = 0; q < nrhs; ++q) H_->st[q] = RhsStats();
-  if (L.dx == C128) return precond(H_, 1, v, C128, x, nrhs);
+  if (L.dx == C128) {
+    int s = precond(H_, 1, v, C128, x, nrhs);
+    return s ? s : collect_gmres_stats(H_, nrhs);
+  }
   int s = precond(H_, 1, v, C128, L.X, nrhs);
   if (s) return s;
-  return status_of(launch_convert(H_->ctx, C64, C128, L.X, x, (size_t)nrhs * L.n), "hz_precond");
+  s = status_of(launch_convert(H_->ctx, C64, C128, L.X, x, (size_t)nrhs * L.n), "hz_precond");
+  return s ? s : collect_gmres_stats(H_, nrhs);
 }
 
 static void fill_stats(Handle* H, hz_stats* stats, int nrhs, double ms) {
@@ -333,7 +340,8 @@ int hz_cslp_gmres(hz_handle hp, int level, int dtype, const void* b, void* x, in
   for (int q = 0; q < nrhs; ++q) H_->st[q] = RhsStats();
   int st = status_of(cudaMemsetAsync(x, 0, (size_t)nrhs * L.n * elem_bytes(dtype), H_->ctx.s), "hz_cslp_gmres");
   if (st) return st;
-  return cslp_gmres(H_, level, b, x, nrhs, iterations);
+  st = cslp_gmres(H_, level, b, x, nrhs, iterations);
+  return st ? st : collect_gmres_stats(H_, nrhs);
 }
 
 const char* hz_strerror(int s) {

@@ -41,8 +41,9 @@ int status_of(cudaError_t e, const char* where) {
     if (s_) return s_;    \
   } while (0)
 
-static const char* kFamilies[F_COUNT] = {"level_op",  "mg_down", "mg_up",  "defl_restrict", "defl_prolong",
-                                         "multidot",  "axpy",    "reduce", "dense",         "misc"};
+static const char* kFamilies[F_COUNT] = {"level_op", "mg_down", "mg_up",  "defl_restrict", "defl_prolong",
+                                         "multidot", "axpy",    "reduce", "dense",         "misc",
+                                         "gmres_persistent"};
 const char* family_name(int f) { return (f >= 0 && f < F_COUNT) ? kFamilies[f] : "?"; }
 
 // ---------------------------------------------------------------------------------- profiler
@@ -410,6 +411,31 @@ int setup(Handle* h, const double* k_dev) {
       CS(dalloc(h, &L.Vg, (L.capg + 1) * bn * ep));
       CS(dalloc(h, &L.wg, bn * ep));
       CS(alloc_scalars(h, L.scg, L.capg, nb));
+      if (cfg.device_gmres) {
+        int gmax = gmres_max_grid(L.dpre, L.R, L.capg);
+        // one CTA per stencil tile (32 x 16 nodes), at most one CTA per SM: every grid barrier
+        // then serialises at most #SM arrivals
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int want = std::min(sms, ((L.nx + 31) / 32) * ((L.ny + 15) / 16));
+        L.ggrid = std::min(gmax, want);
+        if (L.ggrid > 0) {
+          void* p;
+          CS(dalloc(h, &L.wg2, L.n * ep));
+          L.gpstride = 2 * (L.capg + 1) + 2;
+          CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
+          L.gpartA = (double*)p;
+          CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
+          L.gpartB = (double*)p;
+          CS(dalloc(h, &p, sizeof(double) * (2 * (size_t)L.capg * (L.capg + 1) + 2 * (size_t)L.capg +
+                                             3 * (size_t)L.gpstride)));
+          L.gR = (double*)p;
+          CS(dalloc(h, &p, sizeof(GmresState) * nb));
+          L.gst = (GmresState*)p;
+          CK(cudaMemsetAsync(L.gst, 0, sizeof(GmresState) * nb, h->ctx.s));
+        }
+      }
     }
   }
   h->ws_bytes = dot_ws_bytes((int)maxnv, nb);
@@ -576,7 +602,8 @@ static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, voi
     double* flag = n2 + nb;
     CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hA, h->ws, 1));
     CK(launch_update(c, dvec, V, bn, nv, hA, ldA, dvec, w, n, nb, n1, h->ws));
-    CK(launch_dgks_flag(c, hA + 2 * nv, ldA, n1, flag, nb, 0.5));
+    const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
+    CK(launch_dgks_flag(c, hA + 2 * nv, ldA, n1, flag, nb, eta2));
     CK(launch_multidot(c, dvec, V, bn, nv, w, n, nb, hB, h->ws, 0, flag));
     CK(launch_update(c, dvec, V, bn, nv, hB, 2 * nv, dvec, w, n, nb, n2, h->ws, flag));
     const size_t cnt = (size_t)nb * (ldA + 2 * nv + 3);
@@ -677,12 +704,49 @@ static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, voi
   return HZ_OK;
 }
 
+int collect_gmres_stats(Handle* h, int nb) {
+  for (auto& L : h->lv) {
+    if (!L.gst) continue;
+    std::vector<GmresState> gs(nb);
+    CK(cudaMemcpyAsync(gs.data(), L.gst, sizeof(GmresState) * nb, cudaMemcpyDeviceToHost, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    int err = 0;
+    for (int q = 0; q < nb; ++q) {
+      h->st[q].cslp_it[L.l - 1] += (int)gs[q].total_its;
+      gs[q].total_its = 0;
+      err |= gs[q].err;
+    }
+    CK(cudaMemcpyAsync(L.gst, gs.data(), sizeof(GmresState) * nb, cudaMemcpyHostToDevice, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    if (err) {
+      set_error("a grid barrier of the persistent GMRES kernel exceeded its wait budget");
+      return HZ_ETIMEOUT;
+    }
+  }
+  return HZ_OK;
+}
+
 // CSLP inverse by unpreconditioned GMRES on M_l (levels > mg_max_level): x += GMRES(b).
 int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
   LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
   const int dt = L.dpre;
   OpDesc M = L.opM(dt, h->cfg.beta1, h->cfg.beta2);
+  if (L.ggrid > 0) {  // whole solve on the device, one cooperative launch per right-hand side
+    const size_t eb = elem_bytes(dt);
+    for (int q = 0; q < nb; ++q)
+      CK(launch_gmres_persistent(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb, (char*)x + (size_t)q * L.n * eb,
+                                 L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride, L.gR, L.gst + q, L.capg,
+                                 h->cfg.cslp_tol, L.ggrid,
+                                 h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta));
+    if (its_out) {
+      std::vector<GmresState> gs(nb);
+      CK(cudaMemcpyAsync(gs.data(), L.gst, sizeof(GmresState) * nb, cudaMemcpyDeviceToHost, h->ctx.s));
+      CK(cudaStreamSynchronize(h->ctx.s));
+      for (int q = 0; q < nb; ++q) its_out[q] = gs[q].its;
+    }
+    return HZ_OK;
+  }
   auto op = [&](const void* xin, void* wout) -> int {
     CK(launch_level_op(h->ctx, M, 0, dt, dt, dt, xin, nullptr, wout, 0.0, nb));
     return HZ_OK;
@@ -830,6 +894,7 @@ int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags)
       }
     }
   }
+  CS(collect_gmres_stats(h, nb));
   int first = HZ_OK;
   for (int q = 0; q < nb; ++q) {
     h->st[q].outer = total[q];

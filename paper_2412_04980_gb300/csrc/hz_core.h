@@ -3,7 +3,7 @@
 #include <complex>
 #include <vector>
 
-#include "../../include/hz.h"
+#include "hz.h"
 #include "hz_internal.h"
 
 namespace hz {
@@ -55,6 +55,14 @@ struct Level {
   void* Vg = nullptr;                        // (capg + 1) batches, dpre
   void* wg = nullptr;
   Scalars scg;
+  // persistent GMRES (device_gmres): second work vector, partials, Hessenberg, control blocks
+  void* wg2 = nullptr;
+  double* gpartA = nullptr;
+  double* gpartB = nullptr;
+  int gpstride = 0;
+  double* gR = nullptr;
+  GmresState* gst = nullptr;                 // nbmax control blocks
+  int ggrid = 0;                             // cooperative grid size (0: host-driven GMRES)
   OpDesc opA(int dt) const;
   OpDesc opM(int dt, double b1, double b2) const;
 };
@@ -97,5 +105,7 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb);
 int coarse_solve(Handle* h, int l, int nb);
 int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags);
 int wait_event(Handle* h, cudaEvent_t ev);
+// Fold the persistent-GMRES iteration counters into h->st and check their error flags.
+int collect_gmres_stats(Handle* h, int nb);
 
 }  // namespace hz

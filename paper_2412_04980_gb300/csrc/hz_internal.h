@@ -25,6 +25,7 @@ enum Family {
   F_REDUCE,         // second-stage reductions
   F_DENSE,          // dense coarsest multigrid solve
   F_MISC,           // conversions, copies
+  F_GMRES,          // persistent whole-solve GMRES kernel
   F_COUNT
 };
 const char* family_name(int f);
@@ -134,6 +135,28 @@ cudaError_t launch_combine(Ctx& c, int dtx, const void* X, size_t ldx, int nv, c
 // y^b = alpha_b x^b: alpha complex (2 doubles per rhs) or, with recip, 1/sqrt(alpha_b) (1 double per rhs).
 cudaError_t launch_scale_dev(Ctx& c, int dt, const void* x, void* y, const double* alpha_dev, int recip, size_t n,
                              int nb);
+
+// ---- persistent GMRES (kern_gmres.cu) ---------------------------------------------------
+// Per-right-hand-side control block of the cooperative GMRES kernel (device memory, zeroed).
+struct GmresState {
+  unsigned count;        // grid barrier arrivals (own 128-byte line: atomics only)
+  unsigned pad0[31];
+  unsigned gen;          // grid barrier generation (own line: polled by waiting CTAs)
+  unsigned pad1[31];
+  int err;               // 1: a barrier wait exceeded its clock budget
+  int its;               // iterations of the last solve
+  double est;            // residual estimate of the last solve
+  long long total_its;   // iterations accumulated since the last statistics read
+  long long pad2[13];
+};
+// Largest cooperative grid for the kernel variant (0 if it cannot be launched).
+int gmres_max_grid(int dt, int R, int cap);
+// x += GMRES(M, b) for one right-hand side, whole solve in one cooperative launch.
+// V: (cap+1) * n, w0/w1: n (dtype dt); partA/partB: grid * pstride doubles;
+// Rg: 2 * cap * (cap + 1) + 2 * cap + 3 * pstride doubles (Hessenberg, y, reduced values).
+cudaError_t launch_gmres_persistent(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
+                                    void* w1, double* partA, double* partB, int pstride, double* Rg, GmresState* st,
+                                    int cap, double tol, int grid, double eta2);
 
 // ---- exact coarse stencils (stencil_gen.cpp) ----------------------------------------
 // 1-D Galerkin masks of level l (1-based), length 2R+1, as exact rationals rounded once.

@@ -1,0 +1,521 @@
+// Persistent GMRES for the CSLP inverse on the coarse levels (Section 4.2: unpreconditioned
+// GMRES on M_l to relative tolerance 0.1, at most floor(6 N_l^(1/4)) iterations, zero
+// initial guess).  One cooperative launch runs the whole solve:
+//
+//   op      w_new = M_l (s * w_old) by the shared tile engine; the owning tile also writes
+//           V_j = s * w_old (normalisation fused into the stencil, w ping-pongs).
+//   dots    h = V^H w and ||w||^2 over grid-stride slices, 8 vectors per pass.
+//   update  w -= V h with ||w||^2; a second classical pass only when ||w'|| < ||w||/sqrt(2).
+//   reduce  every CTA sums all CTA partials itself in one fixed order, so every CTA holds
+//           bitwise-identical coefficients and takes identical decisions.
+//   Givens  complex rotations and the residual estimate |g_{j+1}| in FP64, redundantly in
+//           each CTA; CTA 0 keeps the rotated Hessenberg columns for the final solve.
+//
+// Grid-wide ordering uses a sense-reversal barrier whose spin is bounded by a clock64
+// budget: a CTA that runs out sets an error flag, every CTA returns at its next barrier,
+// and the host reports HZ_ETIMEOUT.  Partials alternate between two buffers so that no
+// CTA overwrites partials another CTA is still reading.
+#include <cuda_runtime.h>
+
+#include "hz_core.h"
+#include "hz_device.cuh"
+
+using namespace hzd;
+
+namespace {
+
+constexpr int NT = 512;
+constexpr int NW = NT / 32;
+constexpr int CV = 8;
+constexpr int TOX = 32, TOY = 16;
+constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz per barrier wait
+
+// Loads of data that other CTAs write during the launch bypass L1 (not coherent across SMs).
+__device__ __forceinline__ cx<float> ldcg(const cx<float>* p) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+__device__ __forceinline__ cx<double> ldcg(const cx<double>* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+
+__device__ __forceinline__ bool failed(const hz::GmresState* gs) { return *((volatile const int*)&gs->err) != 0; }
+
+__device__ __forceinline__ bool grid_sync(hz::GmresState* gs, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gs->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gs->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (failed(gs)) break;
+        if (clock64() - t0 > kSpinCycles) {
+          atomicExch(&gs->err, 1);
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return !failed(gs);
+}
+
+// Grid barrier that also reduces CTA partials: the last CTA to arrive sums
+// part[b * pstride + i] over all CTAs b for i < m (one warp per value, lanes stride over CTAs,
+// fixed order, so the result does not depend on which CTA arrives last), stores the sums in
+// red[] (global), then releases the others.  Every CTA returns with red[0..m) copied to out[].
+__device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks, const double* part, int pstride,
+                                            int m, double* red, double* out) {
+  __shared__ int last;
+  __shared__ unsigned gen0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gen0 = *((volatile unsigned*)&gs->gen);
+    __threadfence();
+    last = atomicAdd(&gs->count, 1u) == nblocks - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < m; i += NT / 32) {
+      double t = 0;
+      int b = lane;
+      for (; b + 96 < (int)nblocks; b += 128) {  // four independent L2 loads in flight
+        const double a0 = __ldcg(part + (size_t)b * pstride + i);
+        const double a1 = __ldcg(part + (size_t)(b + 32) * pstride + i);
+        const double a2 = __ldcg(part + (size_t)(b + 64) * pstride + i);
+        const double a3 = __ldcg(part + (size_t)(b + 96) * pstride + i);
+        t += (a0 + a1) + (a2 + a3);
+      }
+      for (; b < (int)nblocks; b += 32) t += __ldcg(part + (size_t)b * pstride + i);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) red[i] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    }
+  } else {
+    if (threadIdx.x == 0) {
+      volatile unsigned* vgen = &gs->gen;
+      const long long t0 = clock64();
+      while (*vgen == gen0) {
+        if (failed(gs)) break;
+        if (clock64() - t0 > kSpinCycles) {
+          atomicExch(&gs->err, 1);
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (failed(gs)) return false;
+  for (int i = threadIdx.x; i < m; i += NT) out[i] = __ldcg(red + i);
+  __syncthreads();
+  return true;
+}
+
+// Warp transpose-reduction (see kern_vec.cu): lane l ends with the warp sum of value l % CNT.
+template <typename T, int CNT>
+__device__ __forceinline__ T warp_tsum(T (&v)[CNT]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int half = CNT / 2; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      T send = upper ? v[i] : v[i + half];
+      T keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  T x = v[0];
+#pragma unroll
+  for (int o = CNT; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename T>
+struct ScaledSrc {
+  const cx<T>* x;
+  int nx;
+  T s;
+  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const { return s * ldcg(x + (size_t)gy * nx + gx); }
+};
+
+struct KShared {  // Krylov scratch in shared memory (after the tile)
+  double* h;      // 2 * (cap + 1) + 1 reduced values of the current pass
+  double* h1;     // first-pass coefficients kept for the Hessenberg column
+  double* gc;     // cap Givens cosines
+  double* gs;     // 2 * cap Givens sines (complex)
+  double* g;      // 2 * (cap + 1) rotated right-hand side
+  double* wred;   // NW warps x 16 values, then NW norms
+  int* flags;     // [0] stop, [1] reorth
+  double* scal;   // [0] next scale, [1] beta, [2] ||w||^2, [3] ||w'||^2
+};
+
+template <typename T>
+__device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
+                          double* wred) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int passes = nv > 0 ? nv : (with_norm ? 1 : 0);
+  for (int c0 = 0; c0 < passes; c0 += CV) {
+    const int cnt = max(0, min(CV, nv - c0));
+    T ar[CV], ai[CV];
+    T wn = T(0);
+#pragma unroll
+    for (int i = 0; i < CV; ++i) ar[i] = ai[i] = T(0);
+    const bool nrm = with_norm && c0 == 0;
+    for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+      const cx<T> we = ldcg(w + e);
+      if (nrm) wn += we.re * we.re + we.im * we.im;
+#pragma unroll
+      for (int i = 0; i < CV; ++i)
+        if (i < cnt) {
+          const cx<T> v = ldcg(V + (size_t)(c0 + i) * n + e);
+          ar[i] += v.re * we.re + v.im * we.im;
+          ai[i] += v.re * we.im - v.im * we.re;
+        }
+    }
+    T vals[2 * CV];
+#pragma unroll
+    for (int i = 0; i < CV; ++i) {
+      vals[2 * i] = ar[i];
+      vals[2 * i + 1] = ai[i];
+    }
+    const T ws = warp_tsum<T, 2 * CV>(vals);
+    if (lane < 2 * CV) wred[wid * 2 * CV + lane] = double(ws);
+    if (nrm) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+      if (lane == 0) wred[NW * 2 * CV + wid] = double(wn);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * CV && (threadIdx.x >> 1) < cnt) {
+      double t = 0;
+      for (int q = 0; q < NT / 32; ++q) t += wred[q * 2 * CV + threadIdx.x];
+      part[(size_t)blockIdx.x * pstride + 2 * c0 + threadIdx.x] = t;
+    }
+    if (nrm && threadIdx.x == 0) {
+      double t = 0;
+      for (int q = 0; q < NT / 32; ++q) t += wred[NW * 2 * CV + q];
+      part[(size_t)blockIdx.x * pstride + 2 * nv] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// w -= sum_i h_i V_i over this CTA's slice; CTA partial of ||w||^2 into part[blockIdx.x * pstride]
+template <typename T>
+__device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T* sc, cx<T>* w, double* part,
+                            int pstride, double* wred) {
+  for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(h[i]);
+  __syncthreads();
+  T acc = T(0);
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+    cx<T> x = ldcg(w + e);
+    for (int i = 0; i < nv; ++i) {
+      const cx<T> v = ldcg(V + (size_t)i * n + e);
+      const T cr = sc[2 * i], ci = sc[2 * i + 1];
+      x.re -= cr * v.re - ci * v.im;
+      x.im -= cr * v.im + ci * v.re;
+    }
+    w[e] = x;
+    acc += x.re * x.re + x.im * x.im;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = double(acc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < NT / 32; ++q) t += wred[q];
+    part[(size_t)blockIdx.x * pstride] = t;
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict__ b, cx<T>* __restrict__ x,
+                                              cx<T>* V, cx<T>* w0, cx<T>* w1, double* partA, double* partB,
+                                              int pstride, double* Rg, hz::GmresState* st, int cap, double tol,
+                                              double eta2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned G = gridDim.x;
+  const size_t n = (size_t)P.nx * P.ny;
+  const int tilesx = (P.nx + TOX - 1) / TOX, tilesy = (P.ny + TOY - 1) / TOY;
+  const int ntiles = tilesx * tilesy;
+  unsigned char* kp = smem + tile_smem_bytes<T, R>(TOX, TOY);
+  KShared K;
+  K.h = reinterpret_cast<double*>(kp);
+  K.h1 = K.h + 2 * (cap + 1) + 2;
+  K.gc = K.h1 + 2 * (cap + 1) + 2;
+  K.gs = K.gc + cap;
+  K.g = K.gs + 2 * cap;
+  K.wred = K.g + 2 * (cap + 1);
+  K.scal = K.wred + NW * 2 * CV + NW;
+  K.flags = reinterpret_cast<int*>(K.scal + 4);
+  T* sc = reinterpret_cast<T*>(K.flags + 4);
+  double* red = Rg + 2 * (size_t)cap * (cap + 1) + 2 * (size_t)cap;  // 3 * pstride reduced values
+
+  // beta = ||b||
+  dots_pass<T>(V, n, 0, b, partA, pstride, true, K.wred);
+  if (!grid_reduce(st, G, partA, pstride, 1, red, K.scal + 1)) return;
+  const double beta = sqrt(K.scal[1]);
+  if (!(beta > 0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->its = 0;
+      st->est = 0;
+    }
+    return;
+  }
+  const double tol_abs = tol * beta;
+  if (threadIdx.x == 0) {
+    K.g[0] = beta;
+    K.g[1] = 0;
+  }
+  const cx<T>* src = b;
+  double s = 1.0 / beta;
+  cx<T>* wcur = w0;
+  cx<T>* wnext = w1;
+  int jstop = 0;
+  double est = beta;
+  for (int j = 0; j < cap; ++j) {
+    // op: V_j = s * src (own tile nodes), wnext = M_l V_j
+    cx<T>* Vj = V + (size_t)j * n;
+    for (int t = blockIdx.x; t < ntiles; t += G) {
+      const int ox0 = (t % tilesx) * TOX, oy0 = (t / tilesx) * TOY;
+      TileView<T, R> tv = make_tile<T, R>(smem, TOX, TOY, ox0, oy0);
+      tile_fill<T, R>(tv, P, ScaledSrc<T>{src, P.nx, T(s)});
+      for (int q = threadIdx.x; q < TOX * TOY; q += NT) {
+        const int ox = q % TOX, oy = q / TOX;
+        const int gx = ox0 + ox, gy = oy0 + oy;
+        if (gx >= P.nx || gy >= P.ny) continue;
+        const size_t i = (size_t)gy * P.nx + gx;
+        wnext[i] = tile_op<T, R>(tv, P, ox, oy);
+        Vj[i] = tv.u(ox + R, oy + R);
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(st, G)) return;
+    // pass 1: h = V^H w, ||w||^2
+    const int nv = j + 1;
+    dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
+    if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
+    for (int i = threadIdx.x; i < 2 * nv + 1; i += NT) K.h1[i] = K.h[i];
+    update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred);
+    if (!grid_reduce(st, G, partB, pstride, 1, red + 2 * pstride, K.scal + 3)) return;
+    const double wn2 = K.h1[2 * nv];
+    double hn2 = K.scal[3];
+    if (!(hn2 >= eta2 * wn2)) {  // second classical pass
+      dots_pass<T>(V, n, nv, wnext, partA, pstride, false, K.wred);
+      if (!grid_reduce(st, G, partA, pstride, 2 * nv, red, K.h)) return;
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) K.h1[i] += K.h[i];
+      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred);
+      if (!grid_reduce(st, G, partB, pstride, 1, red + 2 * pstride, K.scal + 3)) return;
+      hn2 = K.scal[3];
+    }
+    __syncthreads();
+    // Givens rotations (FP64, identical in every CTA)
+    if (threadIdx.x == 0) {
+      const double hn = hn2 > 0 ? sqrt(hn2) : 0.0;
+      double* col = K.h1;  // column j: complex entries 0..j
+      for (int i = 0; i < j; ++i) {
+        const double c = K.gc[i], sr = K.gs[2 * i], si = K.gs[2 * i + 1];
+        const double ar = col[2 * i], ai = col[2 * i + 1], br = col[2 * i + 2], bi = col[2 * i + 3];
+        // (a, b) <- (c a + s b, -conj(s) a + c b)
+        col[2 * i] = c * ar + (sr * br - si * bi);
+        col[2 * i + 1] = c * ai + (sr * bi + si * br);
+        col[2 * i + 2] = -(sr * ar + si * ai) + c * br;
+        col[2 * i + 3] = -(sr * ai - si * ar) + c * bi;
+      }
+      const double ar = col[2 * j], ai = col[2 * j + 1];
+      const double aa = sqrt(ar * ar + ai * ai);
+      const double tt = sqrt(aa * aa + hn * hn);
+      double c, sr, si;
+      if (tt == 0) {
+        c = 1;
+        sr = si = 0;
+      } else if (aa == 0) {
+        c = 0;
+        sr = 1;
+        si = 0;
+      } else {
+        c = aa / tt;
+        sr = (ar / aa) * hn / tt;
+        si = (ai / aa) * hn / tt;
+      }
+      K.gc[j] = c;
+      K.gs[2 * j] = sr;
+      K.gs[2 * j + 1] = si;
+      col[2 * j] = c * ar + sr * hn;
+      col[2 * j + 1] = c * ai + si * hn;
+      const double gr = K.g[2 * j], gi = K.g[2 * j + 1];
+      K.g[2 * j + 2] = -(sr * gr + si * gi);
+      K.g[2 * j + 3] = -(sr * gi - si * gr);
+      K.g[2 * j] = c * gr;
+      K.g[2 * j + 1] = c * gi;
+      const double e = sqrt(K.g[2 * j + 2] * K.g[2 * j + 2] + K.g[2 * j + 3] * K.g[2 * j + 3]);
+      K.scal[2] = e;
+      K.flags[0] = (e <= tol_abs || hn == 0.0 || j + 1 == cap || !(e == e)) ? 1 : 0;
+      K.scal[0] = hn > 0 ? 1.0 / hn : 0.0;
+      if (blockIdx.x == 0)
+        for (int i = 0; i <= j; ++i) {
+          Rg[2 * ((size_t)j * (cap + 1) + i)] = col[2 * i];
+          Rg[2 * ((size_t)j * (cap + 1) + i) + 1] = col[2 * i + 1];
+        }
+    }
+    __syncthreads();
+    est = K.scal[2];
+    if (K.flags[0]) {
+      jstop = j + 1;
+      break;
+    }
+    s = K.scal[0];
+    src = wnext;
+    cx<T>* tmp = wcur;
+    wcur = wnext;
+    wnext = tmp;
+  }
+  // y = R^-1 g (CTA 0), then x += V y everywhere
+  double* y = Rg + 2 * (size_t)cap * (cap + 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // Rg and y are written and read by this thread only
+    for (int i = jstop - 1; i >= 0; --i) {
+      double sr = K.g[2 * i], si = K.g[2 * i + 1];
+      for (int q = i + 1; q < jstop; ++q) {
+        const double rr = Rg[2 * ((size_t)q * (cap + 1) + i)], ri = Rg[2 * ((size_t)q * (cap + 1) + i) + 1];
+        sr -= rr * y[2 * q] - ri * y[2 * q + 1];
+        si -= rr * y[2 * q + 1] + ri * y[2 * q];
+      }
+      const double dr = Rg[2 * ((size_t)i * (cap + 1) + i)], di = Rg[2 * ((size_t)i * (cap + 1) + i) + 1];
+      const double d = dr * dr + di * di;
+      y[2 * i] = (sr * dr + si * di) / d;
+      y[2 * i + 1] = (si * dr - sr * di) / d;
+    }
+    st->its = jstop;
+    st->est = est;
+    st->total_its += jstop;
+  }
+  if (!grid_sync(st, G)) return;
+  for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(__ldcg(y + i));
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)G * NT) {
+    cx<T> acc = x[e];
+    for (int i = 0; i < jstop; ++i) {
+      const cx<T> v = ldcg(V + (size_t)i * n + e);
+      const T cr = sc[2 * i], ci = sc[2 * i + 1];
+      acc.re += cr * v.re - ci * v.im;
+      acc.im += cr * v.im + ci * v.re;
+    }
+    x[e] = acc;
+  }
+}
+
+template <typename T>
+OpP<T> mkop(const hz::OpDesc& d) {
+  OpP<T> p;
+  p.nx = d.nx;
+  p.ny = d.ny;
+  p.R = d.R;
+  p.bc = d.bc;
+  p.c = T(d.c);
+  p.H = T(d.H);
+  p.ks = T(d.ks);
+  p.sr = T(d.sr);
+  p.si = T(d.si);
+  p.ksr = T(d.ks * d.sr);
+  p.ksi = T(d.ks * d.si);
+  for (int i = 0; i < 7; ++i) {
+    p.m[i] = T(d.m[i]);
+    p.l[i] = T(d.l[i]);
+  }
+  if constexpr (sizeof(T) == 8) p.k = reinterpret_cast<const T*>(d.k_d);
+  else p.k = reinterpret_cast<const T*>(d.k_f);
+  return p;
+}
+
+template <typename T, int R>
+size_t kshared_bytes(int cap) {
+  return tile_smem_bytes<T, R>(TOX, TOY) + sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) +
+                                                             NW * 2 * CV + NW + 4) +
+         sizeof(int) * 4 + sizeof(T) * 2 * (cap + 1) + 64;
+}
+
+template <typename T, int R>
+cudaError_t gmres_t(hz::Ctx& c, const hz::OpDesc& d, const void* b, void* x, void* V, void* w0, void* w1,
+                    double* partA, double* partB, int pstride, double* Rg, hz::GmresState* st, int cap, double tol,
+                    int grid, double eta2) {
+  const size_t sm = kshared_bytes<T, R>(cap);
+  cudaError_t e = cudaFuncSetAttribute(k_gmres<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  OpP<T> P = mkop<T>(d);
+  const cx<T>* bb = reinterpret_cast<const cx<T>*>(b);
+  cx<T>* xx = reinterpret_cast<cx<T>*>(x);
+  cx<T>* VV = reinterpret_cast<cx<T>*>(V);
+  cx<T>* a0 = reinterpret_cast<cx<T>*>(w0);
+  cx<T>* a1 = reinterpret_cast<cx<T>*>(w1);
+  void* args[] = {&P, &bb, &xx, &VV, &a0, &a1, &partA, &partB, &pstride, &Rg, &st, &cap, &tol, &eta2};
+  hz::ProfScope ps(c, hz::F_GMRES, 0.0);
+  return cudaLaunchCooperativeKernel((const void*)k_gmres<T, R>, dim3(grid), dim3(NT), args, sm, c.s);
+}
+
+template <typename T, int R>
+int max_grid_t(int cap) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const size_t sm = kshared_bytes<T, R>(cap);
+  if (cudaFuncSetAttribute(k_gmres<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres<T, R>, NT, sm) != cudaSuccess) return 0;
+  return per * sms;
+}
+
+}  // namespace
+
+namespace hz {
+
+int gmres_max_grid(int dt, int R, int cap) {
+  if (dt == C128) {
+    if (R == 1) return max_grid_t<double, 1>(cap);
+    if (R == 2) return max_grid_t<double, 2>(cap);
+    if (R == 3) return max_grid_t<double, 3>(cap);
+  } else {
+    if (R == 1) return max_grid_t<float, 1>(cap);
+    if (R == 2) return max_grid_t<float, 2>(cap);
+    if (R == 3) return max_grid_t<float, 3>(cap);
+  }
+  return 0;
+}
+
+cudaError_t launch_gmres_persistent(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
+                                    void* w1, double* partA, double* partB, int pstride, double* Rg, GmresState* st,
+                                    int cap, double tol, int grid, double eta2) {
+  if (dt == C128) {
+    if (M.R == 1) return gmres_t<double, 1>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+    if (M.R == 2) return gmres_t<double, 2>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+    if (M.R == 3) return gmres_t<double, 3>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+  } else {
+    if (M.R == 1) return gmres_t<float, 1>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+    if (M.R == 2) return gmres_t<float, 2>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+    if (M.R == 3) return gmres_t<float, 3>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hz
