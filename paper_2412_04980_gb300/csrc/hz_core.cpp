@@ -418,7 +418,9 @@ int setup(Handle* h, const double* k_dev) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int want = std::min(sms, ((L.nx + 31) / 32) * ((L.ny + 15) / 16));
+        // small levels: at least ~256 nodes per CTA slice so the vector phases stay short
+        int want = std::min<long long>(sms, std::max<long long>(((L.nx + 31) / 32) * ((L.ny + 15) / 16),
+                                                                 ((long long)L.n + 255) / 256));
         L.ggrid = std::min(gmax, want);
         if (L.ggrid > 0) {
           void* p;

@@ -171,10 +171,75 @@ struct KShared {  // Krylov scratch in shared memory (after the tile)
   double* scal;   // [0] next scale, [1] beta, [2] ||w||^2, [3] ||w'||^2
 };
 
+// Contiguous slice of the vector owned by this CTA.
+__device__ __forceinline__ void my_slice(size_t n, size_t& s0, size_t& s1) {
+  const size_t S = (n + gridDim.x - 1) / gridDim.x;
+  s0 = (size_t)blockIdx.x * S;
+  s1 = s0 + S < n ? s0 + S : n;
+  if (s0 > n) s0 = n;
+}
+
+// CTA partials of h_i = V_i^H w (i < nv) and, with with_norm, ||w||^2 over this CTA's slice.
+// Warps split the vectors (warp q takes i = q, q + NW, ...; the norm is one more "vector"),
+// lanes stream the slice; every partial is a complete sum over the slice, written by one lane.
 template <typename T>
-__device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
+__device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  size_t s0, s1;
+  my_slice(n, s0, s1);
+  const int jobs = nv + (with_norm ? 1 : 0);
+  for (int i = wid; i < jobs; i += NW) {
+    const bool is_norm = i == nv;
+    const cx<T>* Vi = V + (size_t)(is_norm ? 0 : i) * n;
+    T ar = T(0), ai = T(0);
+    size_t e = s0 + lane;
+    for (; e + 96 < s1; e += 128) {
+      cx<T> wv[4], vv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) wv[k] = ldcg(w + e + 32 * k);
+      if (!is_norm) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) vv[k] = ldcg(Vi + e + 32 * k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) vv[k] = wv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        ar += vv[k].re * wv[k].re + vv[k].im * wv[k].im;
+        ai += vv[k].re * wv[k].im - vv[k].im * wv[k].re;
+      }
+    }
+    for (; e < s1; e += 32) {
+      const cx<T> wv = ldcg(w + e);
+      const cx<T> vv = is_norm ? wv : ldcg(Vi + e);
+      ar += vv.re * wv.re + vv.im * wv.im;
+      ai += vv.re * wv.im - vv.im * wv.re;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) {
+      if (is_norm) {
+        part[(size_t)blockIdx.x * pstride + 2 * nv] = double(ar);
+      } else {
+        part[(size_t)blockIdx.x * pstride + 2 * i] = double(ar);
+        part[(size_t)blockIdx.x * pstride + 2 * i + 1] = double(ai);
+      }
+    }
+  }
+}
+
+// Element-parallel variant for large slices: every thread takes 4 elements of the slice and
+// accumulates 8 vectors per pass; a warp transpose-reduction and one block combine per pass.
+template <typename T>
+__device__ void dots_elem(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
                           double* wred) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  size_t s0, s1;
+  my_slice(n, s0, s1);
   const int passes = nv > 0 ? nv : (with_norm ? 1 : 0);
   for (int c0 = 0; c0 < passes; c0 += CV) {
     const int cnt = max(0, min(CV, nv - c0));
@@ -183,15 +248,29 @@ __device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
 #pragma unroll
     for (int i = 0; i < CV; ++i) ar[i] = ai[i] = T(0);
     const bool nrm = with_norm && c0 == 0;
-    for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
-      const cx<T> we = ldcg(w + e);
-      if (nrm) wn += we.re * we.re + we.im * we.im;
+    for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += 4 * NT) {
+      cx<T> we[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const size_t e = e0 + k * NT;
+        we[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
+        if (nrm) wn += we[k].re * we[k].re + we[k].im * we[k].im;
+      }
 #pragma unroll
       for (int i = 0; i < CV; ++i)
         if (i < cnt) {
-          const cx<T> v = ldcg(V + (size_t)(c0 + i) * n + e);
-          ar[i] += v.re * we.re + v.im * we.im;
-          ai[i] += v.re * we.im - v.im * we.re;
+          const cx<T>* Vi = V + (size_t)(c0 + i) * n;
+          cx<T> v[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const size_t e = e0 + k * NT;
+            v[k] = e < s1 ? ldcg(Vi + e) : mk<T>(T(0), T(0));
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            ar[i] += v[k].re * we[k].re + v[k].im * we[k].im;
+            ai[i] += v[k].re * we[k].im - v[k].im * we[k].re;
+          }
         }
     }
     T vals[2 * CV];
@@ -210,36 +289,112 @@ __device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
     __syncthreads();
     if (threadIdx.x < 2 * CV && (threadIdx.x >> 1) < cnt) {
       double t = 0;
-      for (int q = 0; q < NT / 32; ++q) t += wred[q * 2 * CV + threadIdx.x];
+      for (int q = 0; q < NW; ++q) t += wred[q * 2 * CV + threadIdx.x];
       part[(size_t)blockIdx.x * pstride + 2 * c0 + threadIdx.x] = t;
     }
     if (nrm && threadIdx.x == 0) {
       double t = 0;
-      for (int q = 0; q < NT / 32; ++q) t += wred[NW * 2 * CV + q];
+      for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CV + q];
       part[(size_t)blockIdx.x * pstride + 2 * nv] = t;
     }
     __syncthreads();
   }
 }
 
+constexpr size_t kLargeSlice = 8 * NT;  // slices above this use the element-parallel phases
+
+template <typename T>
+__device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
+                          double* wred) {
+  if ((n + gridDim.x - 1) / gridDim.x > kLargeSlice) dots_elem<T>(V, n, nv, w, part, pstride, with_norm, wred);
+  else dots_warp<T>(V, n, nv, w, part, pstride, with_norm);
+}
+
+// x[e] (+/-)= sum_i c_i V_i[e]; 8 vectors per step with all loads issued first (8 in flight).
+template <typename T, bool SUB>
+__device__ __forceinline__ cx<T> axpy_all(cx<T> x, const cx<T>* V, size_t n, int nv, const T* sc, size_t e) {
+  int i = 0;
+  for (; i + 7 < nv; i += 8) {
+    cx<T> v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = ldcg(V + (size_t)(i + u) * n + e);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T cr = sc[2 * (i + u)], ci = sc[2 * (i + u) + 1];
+      const T pr = cr * v[u].re - ci * v[u].im, pi = cr * v[u].im + ci * v[u].re;
+      if (SUB) {
+        x.re -= pr;
+        x.im -= pi;
+      } else {
+        x.re += pr;
+        x.im += pi;
+      }
+    }
+  }
+  for (; i < nv; ++i) {
+    const cx<T> v = ldcg(V + (size_t)i * n + e);
+    const T cr = sc[2 * i], ci = sc[2 * i + 1];
+    const T pr = cr * v.re - ci * v.im, pi = cr * v.im + ci * v.re;
+    if (SUB) {
+      x.re -= pr;
+      x.im -= pi;
+    } else {
+      x.re += pr;
+      x.im += pi;
+    }
+  }
+  return x;
+}
+
 // w -= sum_i h_i V_i over this CTA's slice; CTA partial of ||w||^2 into part[blockIdx.x * pstride]
 template <typename T>
 __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T* sc, cx<T>* w, double* part,
-                            int pstride, double* wred) {
+                            int pstride, double* wred, bool with_norm = true) {
   for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(h[i]);
   __syncthreads();
+  size_t s0, s1;
+  my_slice(n, s0, s1);
   T acc = T(0);
-  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
-    cx<T> x = ldcg(w + e);
-    for (int i = 0; i < nv; ++i) {
-      const cx<T> v = ldcg(V + (size_t)i * n + e);
-      const T cr = sc[2 * i], ci = sc[2 * i + 1];
-      x.re -= cr * v.re - ci * v.im;
-      x.im -= cr * v.im + ci * v.re;
+  if (s1 - s0 > kLargeSlice) {
+    for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += 4 * NT) {
+      cx<T> x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const size_t e = e0 + k * NT;
+        x[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
+      }
+      for (int i = 0; i < nv; ++i) {
+        const cx<T>* Vi = V + (size_t)i * n;
+        const T cr = sc[2 * i], ci = sc[2 * i + 1];
+        cx<T> v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const size_t e = e0 + k * NT;
+          v[k] = e < s1 ? ldcg(Vi + e) : mk<T>(T(0), T(0));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          x[k].re -= cr * v[k].re - ci * v[k].im;
+          x[k].im -= cr * v[k].im + ci * v[k].re;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const size_t e = e0 + k * NT;
+        if (e < s1) {
+          w[e] = x[k];
+          acc += x[k].re * x[k].re + x[k].im * x[k].im;
+        }
+      }
     }
-    w[e] = x;
-    acc += x.re * x.re + x.im * x.im;
+  } else {
+    for (size_t e = s0 + threadIdx.x; e < s1; e += NT) {
+      const cx<T> x = axpy_all<T, true>(ldcg(w + e), V, n, nv, sc, e);
+      w[e] = x;
+      acc += x.re * x.re + x.im * x.im;
+    }
   }
+  if (!with_norm) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = double(acc);
@@ -249,6 +404,65 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
     for (int q = 0; q < NT / 32; ++q) t += wred[q];
     part[(size_t)blockIdx.x * pstride] = t;
   }
+}
+
+// One Givens step on Hessenberg column j (entries h[0..2j+1] plus, with h2, a second-pass
+// correction), subdiagonal hn2 = |h_{j+1,j}|^2, in the arithmetic type G_ with the rotation
+// state (gc, gs, g) held in shared memory in that type.  Writes the rotated column to Rc
+// (FP64, CTA 0 only), the residual estimate |g_{j+1}|, the stop flag and 1/h_{j+1,j}.
+template <typename G_>
+__device__ void givens_step(int j, int cap, const double* h, const double* h2, double hn2, G_* col, G_* gc, G_* gs,
+                            G_* g, double* Rc, double tol_abs, double* est, int* stop, double* scale) {
+  for (int i = 0; i <= j; ++i) {
+    col[2 * i] = G_(h[2 * i] + (h2 ? h2[2 * i] : 0.0));
+    col[2 * i + 1] = G_(h[2 * i + 1] + (h2 ? h2[2 * i + 1] : 0.0));
+  }
+  const G_ hn = hn2 > 0 ? G_(sqrt(hn2)) : G_(0);
+  for (int i = 0; i < j; ++i) {
+    const G_ c = gc[i], sr = gs[2 * i], si = gs[2 * i + 1];
+    const G_ ar = col[2 * i], ai = col[2 * i + 1], br = col[2 * i + 2], bi = col[2 * i + 3];
+    // (a, b) <- (c a + s b, -conj(s) a + c b)
+    col[2 * i] = c * ar + (sr * br - si * bi);
+    col[2 * i + 1] = c * ai + (sr * bi + si * br);
+    col[2 * i + 2] = -(sr * ar + si * ai) + c * br;
+    col[2 * i + 3] = -(sr * ai - si * ar) + c * bi;
+  }
+  const G_ ar = col[2 * j], ai = col[2 * j + 1];
+  const G_ aa = sqrt(ar * ar + ai * ai);
+  const G_ tt = sqrt(aa * aa + hn * hn);
+  G_ c, sr, si;
+  if (tt == G_(0)) {
+    c = G_(1);
+    sr = si = G_(0);
+  } else if (aa == G_(0)) {
+    c = G_(0);
+    sr = G_(1);
+    si = G_(0);
+  } else {
+    c = aa / tt;
+    sr = (ar / aa) * hn / tt;
+    si = (ai / aa) * hn / tt;
+  }
+  gc[j] = c;
+  gs[2 * j] = sr;
+  gs[2 * j + 1] = si;
+  col[2 * j] = c * ar + sr * hn;
+  col[2 * j + 1] = c * ai + si * hn;
+  const G_ gr = g[2 * j], gi = g[2 * j + 1];
+  const G_ g2r = -(sr * gr + si * gi), g2i = -(sr * gi - si * gr);
+  g[2 * j + 2] = g2r;
+  g[2 * j + 3] = g2i;
+  g[2 * j] = c * gr;
+  g[2 * j + 1] = c * gi;
+  const double e = double(sqrt(g2r * g2r + g2i * g2i));
+  *est = e;
+  *stop = (e <= tol_abs || hn == G_(0) || j + 1 == cap || !(e == e)) ? 1 : 0;
+  *scale = hn2 > 0 ? 1.0 / sqrt(hn2) : 0.0;
+  if (Rc)
+    for (int i = 0; i <= j; ++i) {
+      Rc[2 * i] = double(col[2 * i]);
+      Rc[2 * i + 1] = double(col[2 * i + 1]);
+    }
 }
 
 template <typename T, int R>
@@ -265,13 +479,17 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   KShared K;
   K.h = reinterpret_cast<double*>(kp);
   K.h1 = K.h + 2 * (cap + 1) + 2;
-  K.gc = K.h1 + 2 * (cap + 1) + 2;
+  K.gc = K.h1 + 2 * (cap + 1) + 2;  // (FP64 slots reused as typed Givens state below)
   K.gs = K.gc + cap;
   K.g = K.gs + 2 * cap;
   K.wred = K.g + 2 * (cap + 1);
   K.scal = K.wred + NW * 2 * CV + NW;
   K.flags = reinterpret_cast<int*>(K.scal + 4);
   T* sc = reinterpret_cast<T*>(K.flags + 4);
+  T* gcT = reinterpret_cast<T*>(K.gc);      // cap cosines
+  T* gsT = reinterpret_cast<T*>(K.gs);      // 2 cap sines
+  T* gT = reinterpret_cast<T*>(K.g);        // 2 (cap + 1) rotated right-hand side
+  T* colT = sc + 2 * (cap + 1);             // 2 (cap + 1) rotated column
   double* red = Rg + 2 * (size_t)cap * (cap + 1) + 2 * (size_t)cap;  // 3 * pstride reduced values
 
   // beta = ||b||
@@ -287,8 +505,8 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   }
   const double tol_abs = tol * beta;
   if (threadIdx.x == 0) {
-    K.g[0] = beta;
-    K.g[1] = 0;
+    gT[0] = T(beta);
+    gT[1] = T(0);
   }
   const cx<T>* src = b;
   double s = 1.0 / beta;
@@ -314,74 +532,44 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       __syncthreads();
     }
     if (!grid_sync(st, G)) return;
-    // pass 1: h = V^H w, ||w||^2
+    // h = V^H w and ||w||^2; ||w'||^2 = ||w||^2 - sum |h_i|^2 (Pythagoras) unless the vector
+    // loses more than reorth_eta of its norm, in which case a second classical pass runs
     const int nv = j + 1;
     dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
     if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
-    for (int i = threadIdx.x; i < 2 * nv + 1; i += NT) K.h1[i] = K.h[i];
-    update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred);
-    if (!grid_reduce(st, G, partB, pstride, 1, red + 2 * pstride, K.scal + 3)) return;
-    const double wn2 = K.h1[2 * nv];
-    double hn2 = K.scal[3];
-    if (!(hn2 >= eta2 * wn2)) {  // second classical pass
-      dots_pass<T>(V, n, nv, wnext, partA, pstride, false, K.wred);
-      if (!grid_reduce(st, G, partA, pstride, 2 * nv, red, K.h)) return;
-      for (int i = threadIdx.x; i < 2 * nv; i += NT) K.h1[i] += K.h[i];
-      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred);
-      if (!grid_reduce(st, G, partB, pstride, 1, red + 2 * pstride, K.scal + 3)) return;
-      hn2 = K.scal[3];
-    }
-    __syncthreads();
-    // Givens rotations (FP64, identical in every CTA)
     if (threadIdx.x == 0) {
-      const double hn = hn2 > 0 ? sqrt(hn2) : 0.0;
-      double* col = K.h1;  // column j: complex entries 0..j
-      for (int i = 0; i < j; ++i) {
-        const double c = K.gc[i], sr = K.gs[2 * i], si = K.gs[2 * i + 1];
-        const double ar = col[2 * i], ai = col[2 * i + 1], br = col[2 * i + 2], bi = col[2 * i + 3];
-        // (a, b) <- (c a + s b, -conj(s) a + c b)
-        col[2 * i] = c * ar + (sr * br - si * bi);
-        col[2 * i + 1] = c * ai + (sr * bi + si * br);
-        col[2 * i + 2] = -(sr * ar + si * ai) + c * br;
-        col[2 * i + 3] = -(sr * ai - si * ar) + c * bi;
-      }
-      const double ar = col[2 * j], ai = col[2 * j + 1];
-      const double aa = sqrt(ar * ar + ai * ai);
-      const double tt = sqrt(aa * aa + hn * hn);
-      double c, sr, si;
-      if (tt == 0) {
-        c = 1;
-        sr = si = 0;
-      } else if (aa == 0) {
-        c = 0;
-        sr = 1;
-        si = 0;
-      } else {
-        c = aa / tt;
-        sr = (ar / aa) * hn / tt;
-        si = (ai / aa) * hn / tt;
-      }
-      K.gc[j] = c;
-      K.gs[2 * j] = sr;
-      K.gs[2 * j + 1] = si;
-      col[2 * j] = c * ar + sr * hn;
-      col[2 * j + 1] = c * ai + si * hn;
-      const double gr = K.g[2 * j], gi = K.g[2 * j + 1];
-      K.g[2 * j + 2] = -(sr * gr + si * gi);
-      K.g[2 * j + 3] = -(sr * gi - si * gr);
-      K.g[2 * j] = c * gr;
-      K.g[2 * j + 1] = c * gi;
-      const double e = sqrt(K.g[2 * j + 2] * K.g[2 * j + 2] + K.g[2 * j + 3] * K.g[2 * j + 3]);
-      K.scal[2] = e;
-      K.flags[0] = (e <= tol_abs || hn == 0.0 || j + 1 == cap || !(e == e)) ? 1 : 0;
-      K.scal[0] = hn > 0 ? 1.0 / hn : 0.0;
-      if (blockIdx.x == 0)
-        for (int i = 0; i <= j; ++i) {
-          Rg[2 * ((size_t)j * (cap + 1) + i)] = col[2 * i];
-          Rg[2 * ((size_t)j * (cap + 1) + i) + 1] = col[2 * i + 1];
-        }
+      T hs = T(0);
+      for (int i = 0; i < 2 * nv; ++i) hs += T(K.h[i]) * T(K.h[i]);
+      const double wn2 = K.h[2 * nv];
+      const double hp = wn2 - double(hs);
+      K.scal[3] = hp;
+      K.flags[1] = !(hp >= eta2 * wn2);
+      if (!K.flags[1])
+        givens_step<T>(j, cap, K.h, nullptr, hp, colT, gcT, gsT, gT,
+                       blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
+                       K.scal);
     }
     __syncthreads();
+    if (K.flags[1]) {  // second classical pass
+      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
+      if (!grid_sync(st, G)) return;
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) K.h1[i] = K.h[i];
+      dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
+      if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
+      if (threadIdx.x == 0) {
+        T hs = T(0);
+        for (int i = 0; i < 2 * nv; ++i) hs += T(K.h[i]) * T(K.h[i]);
+        const double hp = K.h[2 * nv] - double(hs);
+        givens_step<T>(j, cap, K.h1, K.h, hp, colT, gcT, gsT, gT,
+                       blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
+                       K.scal);
+      }
+      __syncthreads();
+    }
+    if (!K.flags[0]) {  // w' = w - V h (with the last pass's coefficients); the next op needs it complete
+      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
+      if (!grid_sync(st, G)) return;
+    }
     est = K.scal[2];
     if (K.flags[0]) {
       jstop = j + 1;
@@ -397,7 +585,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   double* y = Rg + 2 * (size_t)cap * (cap + 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // Rg and y are written and read by this thread only
     for (int i = jstop - 1; i >= 0; --i) {
-      double sr = K.g[2 * i], si = K.g[2 * i + 1];
+      double sr = double(gT[2 * i]), si = double(gT[2 * i + 1]);
       for (int q = i + 1; q < jstop; ++q) {
         const double rr = Rg[2 * ((size_t)q * (cap + 1) + i)], ri = Rg[2 * ((size_t)q * (cap + 1) + i) + 1];
         sr -= rr * y[2 * q] - ri * y[2 * q + 1];
@@ -415,16 +603,9 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   if (!grid_sync(st, G)) return;
   for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(__ldcg(y + i));
   __syncthreads();
-  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)G * NT) {
-    cx<T> acc = x[e];
-    for (int i = 0; i < jstop; ++i) {
-      const cx<T> v = ldcg(V + (size_t)i * n + e);
-      const T cr = sc[2 * i], ci = sc[2 * i + 1];
-      acc.re += cr * v.re - ci * v.im;
-      acc.im += cr * v.im + ci * v.re;
-    }
-    x[e] = acc;
-  }
+  size_t s0, s1;
+  my_slice(n, s0, s1);
+  for (size_t e = s0 + threadIdx.x; e < s1; e += NT) x[e] = axpy_all<T, false>(x[e], V, n, jstop, sc, e);
 }
 
 template <typename T>
@@ -454,7 +635,7 @@ template <typename T, int R>
 size_t kshared_bytes(int cap) {
   return tile_smem_bytes<T, R>(TOX, TOY) + sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) +
                                                              NW * 2 * CV + NW + 4) +
-         sizeof(int) * 4 + sizeof(T) * 2 * (cap + 1) + 64;
+         sizeof(int) * 4 + sizeof(T) * 4 * (cap + 1) + 64;
 }
 
 template <typename T, int R>
