@@ -204,21 +204,36 @@ __device__ __forceinline__ void tile_fill(const TileView<T, R>& t, const OpP<T>&
     __syncthreads();
   }
   if (R >= 2) {
+    // x-passes with register windows: each work item is one tile row and 4 consecutive
+    // output columns, computed from 4 + 2R staged values per field
     const int OX = t.OX;
-    for (int idx = tid; idx < WY * OX; idx += nthr) {
-      int cy = idx / OX, ox = idx - cy * OX;
-      const cx<T>* ur = t.U + cy * WX + ox;   // cell (ox + R + d) at ur[R + d]
-      const cx<T>* wr = t.W + cy * WX + ox;
-      cx<T> a = mk<T>(T(0), T(0)), b = a, c = a;
+    const int nseg = (OX + 3) / 4;
+    for (int it = tid; it < WY * nseg; it += nthr) {
+      const int cy = it / nseg, sx = (it - cy * nseg) * 4;
+      const cx<T>* ur = t.U + cy * WX + sx;
+      const cx<T>* wr = t.W + cy * WX + sx;
+      cx<T> u[4 + 2 * R], w[4 + 2 * R];
 #pragma unroll
-      for (int d = 0; d <= 2 * R; ++d) {
-        a = a + P.l[d] * ur[d];
-        b = b + P.m[d] * ur[d];
-        c = c + P.m[d] * wr[d];
+      for (int k = 0; k < 4 + 2 * R; ++k) {
+        const bool ok = sx + k < WX;
+        u[k] = ok ? ur[k] : mk<T>(T(0), T(0));
+        w[k] = ok ? wr[k] : mk<T>(T(0), T(0));
       }
-      t.XA[idx] = a;
-      t.XB[idx] = b;
-      t.XC[idx] = c;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (sx + q >= OX) break;
+        cx<T> a = mk<T>(T(0), T(0)), b = a, c = a;
+#pragma unroll
+        for (int d = 0; d <= 2 * R; ++d) {
+          a = a + P.l[d] * u[q + d];
+          b = b + P.m[d] * u[q + d];
+          c = c + P.m[d] * w[q + d];
+        }
+        const int o = cy * OX + sx + q;
+        t.XA[o] = a;
+        t.XB[o] = b;
+        t.XC[o] = c;
+      }
     }
     __syncthreads();
   }
@@ -250,6 +265,53 @@ __device__ __forceinline__ cx<T> tile_op(const TileView<T, R>& t, const OpP<T>& 
       kk = kk + P.m[d] * t.XC[row];
     }
     return mk<T>(P.c * lap.re - (P.sr * kk.re - P.si * kk.im), P.c * lap.im - (P.sr * kk.im + P.si * kk.re));
+  }
+}
+
+}  // namespace hzd
+
+namespace hzd {
+
+// Operator values at up to SEG vertically consecutive output cells (ox, oy0 + q), q < cnt.
+// For R >= 2 the y-passes run on register windows of SEG + 2R staged rows per field; cells on
+// the physical boundary take the 5-point row through tile_op.
+template <typename T, int R, int SEG = 4>
+__device__ __forceinline__ void tile_op_seg(const TileView<T, R>& t, const OpP<T>& P, int ox, int oy0, int cnt,
+                                            cx<T> (&out)[4]) {
+  if (R == 1) {
+#pragma unroll
+    for (int q = 0; q < SEG; ++q)
+      if (q < cnt) out[q] = tile_op<T, R>(t, P, ox, oy0 + q);
+    return;
+  }
+  const int OX = t.OX, WY = t.WY();
+  cx<T> a[SEG + 2 * R], b[SEG + 2 * R], c[SEG + 2 * R];
+#pragma unroll
+  for (int k = 0; k < SEG + 2 * R; ++k) {
+    const int row = oy0 + k;
+    const bool ok = row < WY;
+    const int o = row * OX + ox;
+    a[k] = ok ? t.XA[o] : mk<T>(T(0), T(0));
+    b[k] = ok ? t.XB[o] : mk<T>(T(0), T(0));
+    c[k] = ok ? t.XC[o] : mk<T>(T(0), T(0));
+  }
+  const int gx = t.ox0 + ox;
+#pragma unroll
+  for (int q = 0; q < SEG; ++q) {
+    if (q >= cnt) break;
+    const int gy = t.oy0 + oy0 + q;
+    if (bsides(P, gx, gy) > 0) {
+      out[q] = tile_op<T, R>(t, P, ox, oy0 + q);
+      continue;
+    }
+    cx<T> lap = mk<T>(T(0), T(0)), kk = lap;
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) {
+      lap = lap + P.m[d] * a[q + d];
+      lap = lap + P.l[d] * b[q + d];
+      kk = kk + P.m[d] * c[q + d];
+    }
+    out[q] = mk<T>(P.c * lap.re - (P.sr * kk.re - P.si * kk.im), P.c * lap.im - (P.sr * kk.im + P.si * kk.re));
   }
 }
 

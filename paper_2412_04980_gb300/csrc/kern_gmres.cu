@@ -87,21 +87,29 @@ __device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks
   __syncthreads();
   if (last) {
     __threadfence();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = wid; i < m; i += NT / 32) {
+    // K lanes per value (K a power of two <= 32), every lane sums a strided subset of the CTA
+    // partials with its loads issued together, then the K lanes combine by shuffles
+    int K = 32;
+    while (K > 1 && (NT / K) < m) K >>= 1;
+    const int lane = threadIdx.x & 31;
+    const int per_warp = 32 / K;
+    for (int base = 0; base < m; base += (NT / 32) * per_warp) {
+      const int i = base + (threadIdx.x >> 5) * per_warp + lane / K;
+      const int k = lane % K;
       double t = 0;
-      int b = lane;
-      for (; b + 96 < (int)nblocks; b += 128) {  // four independent L2 loads in flight
-        const double a0 = __ldcg(part + (size_t)b * pstride + i);
-        const double a1 = __ldcg(part + (size_t)(b + 32) * pstride + i);
-        const double a2 = __ldcg(part + (size_t)(b + 64) * pstride + i);
-        const double a3 = __ldcg(part + (size_t)(b + 96) * pstride + i);
-        t += (a0 + a1) + (a2 + a3);
-      }
-      for (; b < (int)nblocks; b += 32) t += __ldcg(part + (size_t)b * pstride + i);
+      if (i < m) {
+        double a[8];
+        int b = k;
+        for (; b + 7 * K < (int)nblocks; b += 8 * K) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) red[i] = t;
+          for (int u = 0; u < 8; ++u) a[u] = __ldcg(part + (size_t)(b + u * K) * pstride + i);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) t += a[u];
+        }
+        for (; b < (int)nblocks; b += K) t += __ldcg(part + (size_t)b * pstride + i);
+      }
+      for (int o = K / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (i < m && k == 0) red[i] = t;
     }
     __threadfence();
     __syncthreads();
@@ -130,6 +138,23 @@ __device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks
   for (int i = threadIdx.x; i < m; i += NT) out[i] = __ldcg(red + i);
   __syncthreads();
   return true;
+}
+
+// Convert m reduced FP64 values to the arithmetic type in parallel and return, in every
+// thread, the sum of squares of the first m2 of them (one warp reduction).
+template <typename T>
+__device__ __forceinline__ T typed_copy_sumsq(const double* h, T* hT, int m, int m2, T* sred) {
+  for (int i = threadIdx.x; i < m; i += NT) hT[i] = T(h[i]);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T acc = T(0);
+    for (int i = threadIdx.x; i < m2; i += 32) acc += hT[i] * hT[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) *sred = acc;
+  }
+  __syncthreads();
+  return *sred;
 }
 
 // Warp transpose-reduction (see kern_vec.cu): lane l ends with the warp sum of value l % CNT.
@@ -411,23 +436,24 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
 // state (gc, gs, g) held in shared memory in that type.  Writes the rotated column to Rc
 // (FP64, CTA 0 only), the residual estimate |g_{j+1}|, the stop flag and 1/h_{j+1,j}.
 template <typename G_>
-__device__ void givens_step(int j, int cap, const double* h, const double* h2, double hn2, G_* col, G_* gc, G_* gs,
-                            G_* g, double* Rc, double tol_abs, double* est, int* stop, double* scale) {
-  for (int i = 0; i <= j; ++i) {
-    col[2 * i] = G_(h[2 * i] + (h2 ? h2[2 * i] : 0.0));
-    col[2 * i + 1] = G_(h[2 * i + 1] + (h2 ? h2[2 * i + 1] : 0.0));
-  }
+__device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn2, G_* col, G_* gc, G_* gs, G_* g,
+                            double* Rc, double tol_abs, double* est, int* stop, double* scale) {
+  // rotations i < j applied to the new column: the second entry of rotation i is the first
+  // entry of rotation i + 1, so it travels in registers; the other operands are independent loads
   const G_ hn = hn2 > 0 ? G_(sqrt(hn2)) : G_(0);
+  G_ ar = h[0] + (h2 ? h2[0] : G_(0)), ai = h[1] + (h2 ? h2[1] : G_(0));
   for (int i = 0; i < j; ++i) {
+    const G_ br = h[2 * i + 2] + (h2 ? h2[2 * i + 2] : G_(0));
+    const G_ bi = h[2 * i + 3] + (h2 ? h2[2 * i + 3] : G_(0));
     const G_ c = gc[i], sr = gs[2 * i], si = gs[2 * i + 1];
-    const G_ ar = col[2 * i], ai = col[2 * i + 1], br = col[2 * i + 2], bi = col[2 * i + 3];
     // (a, b) <- (c a + s b, -conj(s) a + c b)
     col[2 * i] = c * ar + (sr * br - si * bi);
     col[2 * i + 1] = c * ai + (sr * bi + si * br);
-    col[2 * i + 2] = -(sr * ar + si * ai) + c * br;
-    col[2 * i + 3] = -(sr * ai - si * ar) + c * bi;
+    const G_ nr = -(sr * ar + si * ai) + c * br;
+    const G_ ni = -(sr * ai - si * ar) + c * bi;
+    ar = nr;
+    ai = ni;
   }
-  const G_ ar = col[2 * j], ai = col[2 * j + 1];
   const G_ aa = sqrt(ar * ar + ai * ai);
   const G_ tt = sqrt(aa * aa + hn * hn);
   G_ c, sr, si;
@@ -490,6 +516,8 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   T* gsT = reinterpret_cast<T*>(K.gs);      // 2 cap sines
   T* gT = reinterpret_cast<T*>(K.g);        // 2 (cap + 1) rotated right-hand side
   T* colT = sc + 2 * (cap + 1);             // 2 (cap + 1) rotated column
+  T* hT = colT + 2 * (cap + 1);             // 2 (cap + 1) + 2 coefficients in the arithmetic type
+  T* h1T = hT + 2 * (cap + 1) + 2;          // 2 (cap + 1) first-pass coefficients
   double* red = Rg + 2 * (size_t)cap * (cap + 1) + 2 * (size_t)cap;  // 3 * pstride reduced values
 
   // beta = ||b||
@@ -521,13 +549,28 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       const int ox0 = (t % tilesx) * TOX, oy0 = (t / tilesx) * TOY;
       TileView<T, R> tv = make_tile<T, R>(smem, TOX, TOY, ox0, oy0);
       tile_fill<T, R>(tv, P, ScaledSrc<T>{src, P.nx, T(s)});
-      for (int q = threadIdx.x; q < TOX * TOY; q += NT) {
-        const int ox = q % TOX, oy = q / TOX;
-        const int gx = ox0 + ox, gy = oy0 + oy;
-        if (gx >= P.nx || gy >= P.ny) continue;
-        const size_t i = (size_t)gy * P.nx + gx;
-        wnext[i] = tile_op<T, R>(tv, P, ox, oy);
-        Vj[i] = tv.u(ox + R, oy + R);
+      if (R == 1) {
+        for (int q = threadIdx.x; q < TOX * TOY; q += NT) {
+          const int ox = q % TOX, oy = q / TOX;
+          const int gx = ox0 + ox, gy = oy0 + oy;
+          if (gx >= P.nx || gy >= P.ny) continue;
+          const size_t i = (size_t)gy * P.nx + gx;
+          wnext[i] = tile_op<T, R>(tv, P, ox, oy);
+          Vj[i] = tv.u(ox + R, oy + R);
+        }
+      } else {
+        for (int q = threadIdx.x; q < TOX * (TOY / 4); q += NT) {
+          const int ox = q % TOX, sy = (q / TOX) * 4;
+          const int cnt = min(4, P.ny - (oy0 + sy));
+          if (ox0 + ox >= P.nx || cnt <= 0) continue;
+          cx<T> v[4];
+          tile_op_seg<T, R>(tv, P, ox, sy, cnt, v);
+          for (int k = 0; k < cnt; ++k) {
+            const size_t i = (size_t)(oy0 + sy + k) * P.nx + (ox0 + ox);
+            wnext[i] = v[k];
+            Vj[i] = tv.u(ox + R, sy + k + R);
+          }
+        }
       }
       __syncthreads();
     }
@@ -537,30 +580,30 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     const int nv = j + 1;
     dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
     if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
-    if (threadIdx.x == 0) {
-      T hs = T(0);
-      for (int i = 0; i < 2 * nv; ++i) hs += T(K.h[i]) * T(K.h[i]);
-      const double wn2 = K.h[2 * nv];
-      const double hp = wn2 - double(hs);
-      K.scal[3] = hp;
-      K.flags[1] = !(hp >= eta2 * wn2);
-      if (!K.flags[1])
-        givens_step<T>(j, cap, K.h, nullptr, hp, colT, gcT, gsT, gT,
-                       blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
-                       K.scal);
+    {
+      const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
+      if (threadIdx.x == 0) {
+        const double wn2 = K.h[2 * nv];
+        const double hp = wn2 - double(hs);
+        K.scal[3] = hp;
+        K.flags[1] = !(hp >= eta2 * wn2);
+        if (!K.flags[1])
+          givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT,
+                         blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
+                         K.scal);
+      }
     }
     __syncthreads();
     if (K.flags[1]) {  // second classical pass
       update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
       if (!grid_sync(st, G)) return;
-      for (int i = threadIdx.x; i < 2 * nv; i += NT) K.h1[i] = K.h[i];
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) h1T[i] = hT[i];
       dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
       if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
+      const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
       if (threadIdx.x == 0) {
-        T hs = T(0);
-        for (int i = 0; i < 2 * nv; ++i) hs += T(K.h[i]) * T(K.h[i]);
         const double hp = K.h[2 * nv] - double(hs);
-        givens_step<T>(j, cap, K.h1, K.h, hp, colT, gcT, gsT, gT,
+        givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT,
                        blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
                        K.scal);
       }
@@ -635,7 +678,7 @@ template <typename T, int R>
 size_t kshared_bytes(int cap) {
   return tile_smem_bytes<T, R>(TOX, TOY) + sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) +
                                                              NW * 2 * CV + NW + 4) +
-         sizeof(int) * 4 + sizeof(T) * 4 * (cap + 1) + 64;
+         sizeof(int) * 4 + sizeof(T) * (8 * (cap + 1) + 4) + 64;
 }
 
 template <typename T, int R>

@@ -120,12 +120,8 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __r
   const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
   TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
   tile_fill<T, R>(t, P, GlobalSrc<T, TI>{x, P.nx});
-#pragma unroll
-  for (int p = 0; p < OYT / BY; ++p) {
-    const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+  auto emit = [&](int ox, int oy, cx<T> v) {
     const int gx = ox0 + ox, gy = oy0 + oy;
-    if (gx >= P.nx || gy >= P.ny) continue;
-    cx<T> v = tile_op<T, R>(t, P, ox, oy);
     const size_t i = (size_t)gy * P.nx + gx;
     cx<T> out;
     if (MODE == 0) {
@@ -136,6 +132,25 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __r
       else out = t.u(ox + R, oy + R) + omega * cdiv(r, op_diag<T, R>(P, gx, gy));
     }
     y[i] = cvt<TO>(out);
+  };
+  if (R == 1) {
+#pragma unroll
+    for (int p = 0; p < OYT / BY; ++p) {
+      const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+      if (ox0 + ox >= P.nx || oy0 + oy >= P.ny) continue;
+      emit(ox, oy, tile_op<T, R>(t, P, ox, oy));
+    }
+  } else {
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    constexpr int SEG = R == 2 ? 2 : 4;
+    for (int it = tid; it < OXT * (OYT / SEG); it += BX * BY) {
+      const int ox = it % OXT, sy = (it / OXT) * SEG;
+      const int cnt = min(SEG, P.ny - (oy0 + sy));
+      if (ox0 + ox >= P.nx || cnt <= 0) continue;
+      cx<T> v[4];
+      tile_op_seg<T, R, SEG>(t, P, ox, sy, cnt, v);
+      for (int q = 0; q < cnt; ++q) emit(ox, sy + q, v[q]);
+    }
   }
 }
 
@@ -172,15 +187,28 @@ __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const c
   }
   __syncthreads();
   tile_fill<T, R>(t, P, ZSrc<T>{Cs, CW, Imin, Jmin});
-#pragma unroll
-  for (int p = 0; p < OYT / BY; ++p) {
-    const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
-    const int gx = ox0 + ox, gy = oy0 + oy;
-    if (gx >= P.nx || gy >= P.ny) continue;
-    const size_t i = off + (size_t)gy * P.nx + gx;
-    cx<T> s = tile_op<T, R>(t, P, ox, oy);
+  auto emit = [&](int ox, int oy, cx<T> s) {
+    const size_t i = off + (size_t)(oy0 + oy) * P.nx + (ox0 + ox);
     rtil[i] = cvt<T>(v[i]) - s;
     if (tout) tout[i] = t.u(ox + R, oy + R);
+  };
+  if (R == 1) {
+#pragma unroll
+    for (int p = 0; p < OYT / BY; ++p) {
+      const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+      if (ox0 + ox >= P.nx || oy0 + oy >= P.ny) continue;
+      emit(ox, oy, tile_op<T, R>(t, P, ox, oy));
+    }
+  } else {
+    constexpr int SEG = R == 2 ? 2 : 4;
+    for (int it = tid; it < OXT * (OYT / SEG); it += BX * BY) {
+      const int ox = it % OXT, sy = (it / OXT) * SEG;
+      const int cnt = min(SEG, P.ny - (oy0 + sy));
+      if (ox0 + ox >= P.nx || cnt <= 0) continue;
+      cx<T> sv[4];
+      tile_op_seg<T, R, SEG>(t, P, ox, sy, cnt, sv);
+      for (int q = 0; q < cnt; ++q) emit(ox, sy + q, sv[q]);
+    }
   }
 }
 
@@ -258,12 +286,39 @@ __global__ void __launch_bounds__(BX* BY) k_mg_down(OpP<T> P, const cx<T>* __res
   cx<T>* RS = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OX, OY));
   tile_fill<T, R>(t, P, JacZeroSrc<T, R>{f, P, omega});
   const int tid = threadIdx.y * BX + threadIdx.x;
-  for (int idx = tid; idx < OX * OY; idx += BX * BY) {
-    int oy = idx / OX, ox = idx - oy * OX;
-    int gx = ox0 + ox, gy = oy0 + oy;
-    cx<T> r = mk<T>(T(0), T(0));
-    if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) r = f[(size_t)gy * P.nx + gx] - tile_op<T, R>(t, P, ox, oy);
-    RS[idx] = r;
+  if (R == 1) {
+    for (int idx = tid; idx < OX * OY; idx += BX * BY) {
+      int oy = idx / OX, ox = idx - oy * OX;
+      int gx = ox0 + ox, gy = oy0 + oy;
+      cx<T> r = mk<T>(T(0), T(0));
+      if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) r = f[(size_t)gy * P.nx + gx] - tile_op<T, R>(t, P, ox, oy);
+      RS[idx] = r;
+    }
+  } else {
+    constexpr int SEG = R == 2 ? 2 : 4;
+    constexpr int NSY = (OY + SEG - 1) / SEG;
+    for (int it = tid; it < OX * NSY; it += BX * BY) {
+      const int ox = it % OX, sy = (it / OX) * SEG;
+      const int cnt = min(SEG, OY - sy);
+      const int gx = ox0 + ox;
+      // rows of this segment that lie in the grid
+      int q0 = 0, q1 = cnt;
+      while (q0 < cnt && oy0 + sy + q0 < 0) ++q0;
+      while (q1 > q0 && oy0 + sy + q1 - 1 >= P.ny) --q1;
+      cx<T> v[4];
+      const bool colok = gx >= 0 && gx < P.nx;
+      if (colok && q1 > q0) {
+        cx<T> w4[4];
+        tile_op_seg<T, R, SEG>(t, P, ox, sy + q0, q1 - q0, w4);
+        for (int q = q0; q < q1; ++q) v[q] = w4[q - q0];
+      }
+      for (int q = 0; q < cnt; ++q) {
+        const int gy = oy0 + sy + q;
+        cx<T> r = mk<T>(T(0), T(0));
+        if (colok && q >= q0 && q < q1) r = f[(size_t)gy * P.nx + gx] - v[q];
+        RS[(sy + q) * OX + ox] = r;
+      }
+    }
   }
   __syncthreads();
   const int ox = threadIdx.x, oy = threadIdx.y;
@@ -298,16 +353,31 @@ __global__ void __launch_bounds__(BX* BY) k_mg_up(OpP<T> P, const cx<T>* __restr
   }
   __syncthreads();
   tile_fill<T, R>(t, P, UpSrc<T, R>{f, P, omega, Es, EW, Imin, Jmin});
-#pragma unroll
-  for (int p = 0; p < OYT / BY; ++p) {
-    const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+  auto emit = [&](int ox, int oy, cx<T> val) {
     const int gx = ox0 + ox, gy = oy0 + oy;
-    if (gx >= P.nx || gy >= P.ny) continue;
     const size_t i = (size_t)gy * P.nx + gx;
-    cx<T> r = f[i] - tile_op<T, R>(t, P, ox, oy);
+    cx<T> r = f[i] - val;
     cx<T> out = t.u(ox + R, oy + R) + omega * cdiv(r, op_diag<T, R>(P, gx, gy));
     if (add) out = out + add[off + i];
     y[off + i] = out;
+  };
+  if (R == 1) {
+#pragma unroll
+    for (int p = 0; p < OYT / BY; ++p) {
+      const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
+      if (ox0 + ox >= P.nx || oy0 + oy >= P.ny) continue;
+      emit(ox, oy, tile_op<T, R>(t, P, ox, oy));
+    }
+  } else {
+    constexpr int SEG = R == 2 ? 2 : 4;
+    for (int it = tid; it < OXT * (OYT / SEG); it += BX * BY) {
+      const int ox = it % OXT, sy = (it / OXT) * SEG;
+      const int cnt = min(SEG, P.ny - (oy0 + sy));
+      if (ox0 + ox >= P.nx || cnt <= 0) continue;
+      cx<T> v[4];
+      tile_op_seg<T, R, SEG>(t, P, ox, sy, cnt, v);
+      for (int q = 0; q < cnt; ++q) emit(ox, sy + q, v[q]);
+    }
   }
 }
 
