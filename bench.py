@@ -63,6 +63,13 @@ def parse():
     ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply"],
                     help="time one building block on the workload's finest grid instead of a solve")
     ap.add_argument("--repeat", type=int, default=20)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving trace: mixed requests with Poisson arrivals through hz_server_*")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--max-active", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=48.0)
+    ap.add_argument("--load", type=float, default=1.0,
+                    help="offered arrival rate as a multiple of the one-at-a-time service rate")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--out", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -272,6 +279,98 @@ def micro(args):
     print(json.dumps(res))
 
 
+SERVE_MIX = [
+    # name, weight, problem factory, solver configuration
+    ("mp1b_129/fp64", 0.30, lambda: mp_named("mp1b_129"), dict(levels=2, precision="fp64")),
+    ("wedge_289x481/mixed", 0.30, lambda: mp_named("wedge_289x481"), dict(levels=4, negdef_from_level=5,
+                                                                          precision="mixed")),
+    ("random_513/mixed", 0.25, lambda: mp_random(513, 4), dict(levels=4, negdef_from_level=4, precision="mixed")),
+    ("random_1025/mixed", 0.15, lambda: mp_named("random_1025"), dict(levels=4, negdef_from_level=4,
+                                                                      precision="mixed")),
+]
+
+
+def mp_named(name):
+    import model_problems as mp
+    return mp.named(name)
+
+
+def mp_random(n, levels):
+    import model_problems as mp
+    return mp.random_field(n, 5.0, seed=3, levels=levels, negdef_from_level=4)
+
+
+def serve(args):
+    """Serving trace: a seeded mix of request types (sizes 129^2 to 1025^2, FP64 and mixed
+    precision, constant / wedge / random wavenumber fields, point sources at seeded top-row
+    nodes) arriving as a Poisson process, served by hz_server_* with max_active workers under
+    a device-memory budget.  The offered rate is --load times the one-at-a-time service rate
+    measured first, so max_active = 1 saturates at load 1 and overlap shows as lower latency
+    and higher solves/s.  Reports both servers on the same trace."""
+    import numpy as np
+    import torch
+
+    import model_problems as mp
+    import paper_2412_04980_gb300 as hz
+
+    torch.cuda.set_device(0)
+    rng = np.random.Generator(np.random.PCG64(2024))
+    types = [(nm, w, f(), cfg) for nm, w, f, cfg in SERVE_MIX]
+    wts = np.array([t[1] for t in types])
+    kinds = rng.choice(len(types), size=args.requests, p=wts / wts.sum())
+    reqs = []
+    for q, ti in enumerate(kinds):
+        nm, _, p, cfg = types[ti]
+        i = int(rng.integers(1, p.nx - 1))
+        reqs.append((ti, p.k, mp.point_source(p.nx, p.ny, i, p.ny - 1, p.h), p.h, cfg))
+    # one-at-a-time service time per type (alone, after one warm-up), through the same server path
+    alone_ms = {}
+    srv = hz.Server(budget_bytes=int(args.budget_gb * 2 ** 30), max_active=1)
+    for ti, (nm, _, p, cfg) in enumerate(types):
+        for rep_ in range(2):
+            t = srv.submit(p.k, p.b[0], p.h, **dict(cfg))
+            _, st, ms = srv.wait(t)
+        alone_ms[nm] = ms
+    srv.close()
+    mean_service = sum(wts[i] / wts.sum() * alone_ms[types[i][0]] for i in range(len(types))) / 1e3
+    rate = args.load / mean_service
+    gaps = rng.exponential(1.0 / rate, size=args.requests)
+    out = {}
+    for ma in sorted({1, args.max_active}):
+        srv = hz.Server(budget_bytes=int(args.budget_gb * 2 ** 30), max_active=ma)
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for (ti, k, b, h, cfg), g in zip(reqs, gaps):
+            due += g
+            dt = due - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(k, b, h, **dict(cfg)))
+        lat = []
+        its = []
+        for t in tickets:
+            _, st, ms = srv.wait(t, timeout_s=900)
+            lat.append(ms)
+            its.append(st[0]["outer_iterations"])
+        wall = time.perf_counter() - t0
+        rep_ = srv.report()
+        srv.close()
+        out[f"max_active_{ma}"] = {"solves_per_s": args.requests / wall, "p50_ms": rep_["p50_ms"],
+                                   "p99_ms": rep_["p99_ms"], "peak_gb": rep_["peak_bytes"] / 2 ** 30,
+                                   "completed": rep_["completed"], "failed": rep_["failed"], "wall_s": wall}
+    best = out[f"max_active_{args.max_active}"]
+    line = {"metric": "serving solves/s at a 1e-6 relative residual (mixed requests, Poisson arrivals)",
+            "mode": "serve", "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"requests": args.requests, "load": args.load, "offered_rate_per_s": rate,
+                       "budget_gb": args.budget_gb, "max_active": args.max_active,
+                       "mix": {nm: w for nm, w, _, _ in SERVE_MIX},
+                       "requests_per_type": {types[i][0]: int((kinds == i).sum()) for i in range(len(types))}},
+            "alone_ms": alone_ms, "servers": out}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -284,6 +383,8 @@ def main():
 
     if args.micro:
         return micro(args)
+    if args.serve:
+        return serve(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

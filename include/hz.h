@@ -218,6 +218,72 @@ int hz_cslp_gmres(hz_handle h, int level, int dtype, const void* b, void* x, int
  * Errors: HZ_EINVAL (null pointer, nrhs < 1 or > HZ_NOALLOC_MAX_RHS), HZ_ECUDA. */
 int hz_true_residual_noalloc(hz_handle h, const void* b, const void* u, int nrhs, double* relres_dev);
 
+/* ---- serving ------------------------------------------------------------------------ */
+/* A server runs many independent solves (different grids, wavenumber fields, configurations)
+ * on the current device at once.  Each admitted request gets its own handle and stream:
+ * hierarchy and Krylov bases stay resident for the whole solve, and the work of concurrent
+ * requests overlaps on the GPU.  Requests are taken in arrival order; one whose footprint
+ * (hz_estimate_bytes + its device copies of k, b and u) does not fit what the running
+ * requests leave of the budget waits, while later requests that fit are admitted.  A
+ * request's result does not depend on what else runs: it equals hz_solve on a handle of its
+ * own.  The paper solves one problem at a time; this layer is not part of its method. */
+typedef struct hz_server_s* hz_server;
+
+typedef struct {
+  hz_grid grid;            /* finest grid, HZ_BC_SOMMERFELD */
+  hz_config config;        /* solver configuration; config.max_rhs >= nrhs */
+  const double* k_host;    /* nx*ny real FP64 wavenumbers, host; copied by hz_submit */
+  const double* b_host;    /* nrhs*nx*ny HZ_C128 right-hand sides, host; copied by hz_submit */
+  double* u_host;          /* nrhs*nx*ny HZ_C128 solutions, host, caller-owned; written by the
+                              server before the request is reported finished (zero initial guess) */
+  hz_stats* stats_host;    /* nrhs statistics written at completion, or NULL */
+  int nrhs;                /* right-hand sides solved together, >= 1 */
+  double tol;              /* outer relative residual tolerance, in (0, 1) */
+} hz_request;
+
+typedef struct {
+  long long completed;     /* requests that finished with HZ_OK */
+  long long failed;        /* requests that finished with another status */
+  long long queued;        /* requests waiting for admission */
+  int active;              /* requests running now */
+  double p50_ms, p99_ms;   /* latency (submit to result on the host) over completed requests */
+  double solves_per_s;     /* completed requests / (last completion - first submit) */
+  size_t peak_bytes;       /* largest sum of admitted footprints seen */
+  size_t budget_bytes;     /* the budget given to hz_server_create */
+} hz_server_stats;
+
+/* Device bytes hz_setup would allocate for this grid and configuration (bytes requested
+ * from cudaMalloc; an upper bound of hz_memory_bytes of the resulting handle).  Host-only.
+ * Errors: HZ_EINVAL (null pointer). */
+int hz_estimate_bytes(const hz_grid* grid, const hz_config* cfg, size_t* bytes);
+
+/* Start a server on the calling thread's current device with max_active worker threads
+ * (at most that many requests run at once) and a device-memory budget in bytes.
+ * Errors: HZ_EINVAL (null out, max_active < 1, zero budget), HZ_ENOMEM, HZ_ECUDA. */
+int hz_server_create(size_t mem_budget_bytes, int max_active, hz_server* out);
+
+/* Queue a request; *ticket identifies it.  k and b are copied before the call returns; u_host
+ * and stats_host must stay valid until the request is reported finished.
+ * Errors: HZ_EINVAL (null pointer, nrhs < 1, tol outside (0, 1), max_rhs < nrhs, Dirichlet
+ * grid), HZ_ENOMEM (footprint larger than the whole budget).  Errors of the solve itself
+ * (bad sizes or configuration, device failures, HZ_ENOTCONV) are the request's final status. */
+int hz_submit(hz_server s, const hz_request* req, uint64_t* ticket);
+
+/* HZ_PENDING while the request is queued or running, else its final status; *latency_ms
+ * (may be NULL) receives submit-to-completion time once finished.  On a failed request
+ * hz_last_error() of the calling thread then holds the request's detailed message. */
+int hz_poll(hz_server s, uint64_t ticket, double* latency_ms);
+
+/* Block up to timeout_s seconds for the request; returns like hz_poll, or HZ_ETIMEOUT. */
+int hz_wait(hz_server s, uint64_t ticket, double timeout_s, double* latency_ms);
+
+/* Counters and latency percentiles since creation. */
+int hz_server_report(hz_server s, hz_server_stats* out);
+
+/* Let running requests finish, finish queued ones with HZ_EINVAL without running them,
+ * join the workers and free the server (tickets become invalid). */
+int hz_server_destroy(hz_server s);
+
 /* ---- diagnostics ------------------------------------------------------------------- */
 
 /* Name of a status code. */

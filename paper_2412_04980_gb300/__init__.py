@@ -20,7 +20,7 @@ __all__ = [
     "HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ENOTCONV", "HZ_EBREAKDOWN", "HZ_ETIMEOUT", "HZ_ECUDA",
     "HZ_ENOTSUP", "HZ_PENDING", "HZ_BC_SOMMERFELD", "HZ_BC_DIRICHLET", "HZ_PREC_FP64", "HZ_PREC_MIXED",
     "HZ_C128", "HZ_C64", "HZ_OP_A", "HZ_OP_M", "HzGrid", "HzConfig", "HzStats", "HzError", "lib",
-    "library_path", "Helmholtz",
+    "library_path", "Helmholtz", "HzRequest", "HzServerStats", "Server", "estimate_bytes",
 ]
 
 HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ENOTCONV, HZ_EBREAKDOWN, HZ_ETIMEOUT, HZ_ECUDA, HZ_ENOTSUP, HZ_PENDING = range(9)
@@ -71,6 +71,24 @@ class HzStats(ctypes.Structure):
         }
 
 
+class HzRequest(ctypes.Structure):
+    _fields_ = [
+        ("grid", HzGrid), ("config", HzConfig), ("k_host", ctypes.c_void_p), ("b_host", ctypes.c_void_p),
+        ("u_host", ctypes.c_void_p), ("stats_host", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("tol", ctypes.c_double),
+    ]
+
+
+class HzServerStats(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+        ("active", ctypes.c_int), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+        ("solves_per_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class HzError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: status {status} ({detail})")
@@ -105,6 +123,13 @@ _SIGS = {
     "hz_kernel_family_count": (_I, []),
     "hz_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "hz_true_residual_noalloc": (_I, [_P, _P, _P, _I, _P]),
+    "hz_estimate_bytes": (_I, [ctypes.POINTER(HzGrid), ctypes.POINTER(HzConfig), ctypes.POINTER(ctypes.c_size_t)]),
+    "hz_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "hz_submit": (_I, [_P, ctypes.POINTER(HzRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    "hz_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_D)]),
+    "hz_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(_D)]),
+    "hz_server_report": (_I, [_P, ctypes.POINTER(HzServerStats)]),
+    "hz_server_destroy": (_I, [_P]),
 }
 
 _LIB = None
@@ -354,3 +379,81 @@ class Helmholtz:
         _check(lib().hz_profile_read(self._h, family, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
                "hz_profile_read")
         return n.value, ms.value, by.value
+
+
+def _precision(cfg: dict) -> dict:
+    prec = cfg.pop("precision", "fp64")
+    cfg["precision"] = {"fp64": HZ_PREC_FP64, "mixed": HZ_PREC_MIXED}.get(prec, prec)
+    return cfg
+
+
+def estimate_bytes(nx: int, ny: int, h: float, **cfg) -> int:
+    """hz_estimate_bytes: device bytes hz_setup allocates for this grid and configuration."""
+    out = ctypes.c_size_t()
+    g = HzGrid(nx, ny, float(h), HZ_BC_SOMMERFELD)
+    c = config(**_precision(dict(cfg)))
+    _check(lib().hz_estimate_bytes(ctypes.byref(g), ctypes.byref(c), ctypes.byref(out)), "hz_estimate_bytes")
+    return out.value
+
+
+class Server:
+    """Concurrent solves on the current device (hz_server_*): ``submit`` copies k and b and
+    returns a ticket; ``wait`` blocks until the solution is in the numpy array it returns."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 2):
+        self._s = ctypes.c_void_p()
+        _check(lib().hz_server_create(int(budget_bytes), int(max_active), ctypes.byref(self._s)), "hz_server_create")
+        self._live = {}
+
+    def submit(self, k_np, b_np, h: float, tol: float = 1e-6, **cfg) -> int:
+        import numpy as np
+        k = np.ascontiguousarray(k_np, dtype=np.float64)
+        b = np.ascontiguousarray(b_np, dtype=np.complex128)
+        ny, nx = k.shape
+        nrhs = 1 if b.ndim == 2 else b.shape[0]
+        if b.shape[-2:] != (ny, nx):
+            raise ValueError("b must have k's shape (optionally with a leading rhs axis)")
+        cfg = _precision(dict(cfg))
+        cfg.setdefault("max_rhs", nrhs)
+        u = np.empty_like(b)
+        stats = (HzStats * nrhs)()
+        req = HzRequest(HzGrid(nx, ny, float(h), HZ_BC_SOMMERFELD), config(**cfg), k.ctypes.data, b.ctypes.data,
+                        u.ctypes.data, ctypes.addressof(stats), nrhs, float(tol))
+        t = ctypes.c_uint64()
+        _check(lib().hz_submit(self._s, ctypes.byref(req), ctypes.byref(t)), "hz_submit")
+        self._live[t.value] = (u, stats)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (status, latency_ms)."""
+        ms = ctypes.c_double()
+        st = lib().hz_poll(self._s, ticket, ctypes.byref(ms))
+        return None if st == HZ_PENDING else (st, ms.value)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0, check: bool = True):
+        """(u, stats, latency_ms) of a finished request; raises HzError on failure if check."""
+        ms = ctypes.c_double()
+        st = lib().hz_wait(self._s, ticket, float(timeout_s), ctypes.byref(ms))
+        if st == HZ_ETIMEOUT and self.poll(ticket) is None:   # still running (not the solve's own timeout)
+            _check(st, "hz_wait")
+        u, stats = self._live.pop(ticket)
+        if check:
+            _check(st, "server request")
+        return u, [x.as_dict() for x in stats], ms.value
+
+    def report(self) -> dict:
+        out = HzServerStats()
+        _check(lib().hz_server_report(self._s, ctypes.byref(out)), "hz_server_report")
+        return out.as_dict()
+
+    def close(self):
+        if self._s:
+            lib().hz_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

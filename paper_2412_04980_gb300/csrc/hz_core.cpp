@@ -284,6 +284,70 @@ static std::vector<double> inject(const std::vector<double>& k, int nx, int ny) 
   return out;
 }
 
+// Cooperative grid of the persistent GMRES kernel: one CTA per 32 x 16 stencil tile and at
+// least ~256 nodes per CTA slice, at most one CTA per SM (every grid barrier then serialises
+// at most #SM arrivals).
+int gmres_grid_want(int nx, int ny) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long n = (long long)nx * ny;
+  return (int)std::min<long long>(sms, std::max<long long>(((nx + 31) / 32) * ((ny + 15) / 16), (n + 255) / 256));
+}
+
+// Device bytes hz_setup allocates for this grid and configuration (an upper bound: the
+// cooperative grid is taken at its largest), used for admission against a memory budget.
+size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
+  const int ml = cfg.levels, nb = cfg.max_rhs;
+  const bool mixed = cfg.precision == HZ_PREC_MIXED;
+  size_t total = 0, maxnv = 2;
+  auto scal = [&](int cap) { return sizeof(double) * ((size_t)nb * 4 * (cap + 1) + 3 * (size_t)nb + 2 * (size_t)nb * (cap + 1)); };
+  int nx = g.nx, ny = g.ny;
+  for (int l = 1; l <= ml; ++l) {
+    const size_t n = (size_t)nx * ny, bn = (size_t)nb * n;
+    const size_t eb = (l == 1 || !mixed) ? 16 : 8, ep = mixed ? 8 : 16, ex = ep;
+    total += n * 12;  // k in FP64 and FP32
+    int cap;
+    if (l == 1) cap = cfg.restart;
+    else if (l == ml) cap = (cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level) ? 1 : krylov_cap(cfg.c_it, n);
+    else cap = (l == 2) ? cfg.l2_maxit : 1;
+    cap = std::max(cap, 1);
+    maxnv = std::max(maxnv, (size_t)cap + 1);
+    total += (cap + 1) * bn * eb + cap * bn * ex + bn * eb + 3 * bn * ep + (l >= 2 ? 2 * bn * eb : 0) + scal(cap);
+    if (l <= cfg.mg_max_level) {
+      int mx = nx, my = ny;
+      const bool general = !(cfg.mg_nu1 == 1 && cfg.mg_nu2 == 1);
+      if (general) total += 2 * bn * ep;
+      for (;;) {
+        if (std::min(mx, my) <= cfg.mg_coarsest_side || (mx - 1) % 2 || (my - 1) % 2 || std::min(mx, my) < 5) break;
+        mx = (mx + 1) / 2;
+        my = (my + 1) / 2;
+        const size_t m = (size_t)mx * my;
+        total += m * 12 + 2 * (size_t)nb * m * ep + (general ? 2 * (size_t)nb * m * ep : 0);
+      }
+      const size_t nc = (size_t)mx * my;
+      total += nc * nc * 16;
+    } else {
+      const int capg = std::max(1, krylov_cap(cfg.c_it, n));
+      maxnv = std::max(maxnv, (size_t)capg + 1);
+      const bool dev = cfg.device_gmres != 0;
+      const size_t gbr = dev ? n : bn;
+      total += (capg + 1) * gbr * ep + gbr * ep + scal(capg);
+      if (dev) {
+        const size_t ps = 2 * (size_t)(capg + 1) + 2;
+        total += n * ep + 2 * sizeof(double) * 152 * ps +
+                 sizeof(double) * (2 * (size_t)capg * (capg + 1) + 2 * (size_t)capg + 3 * ps) + sizeof(GmresState) * nb;
+      }
+    }
+    if (l < ml) {
+      nx = (nx + 1) / 2;
+      ny = (ny + 1) / 2;
+    }
+  }
+  total += dot_ws_bytes((int)maxnv, nb) + scal(1) + (size_t)nb * g.nx * g.ny * 16;
+  return total;
+}
+
 // ---------------------------------------------------------------------------------- set-up
 int setup(Handle* h, const double* k_dev) {
   const hz_grid& g = h->g;
@@ -408,35 +472,29 @@ int setup(Handle* h, const double* k_dev) {
     } else {
       L.capg = std::max(1, krylov_cap(cfg.c_it, L.n));
       maxnv = std::max(maxnv, (size_t)L.capg + 1);
-      CS(dalloc(h, &L.Vg, (L.capg + 1) * bn * ep));
-      CS(dalloc(h, &L.wg, bn * ep));
-      CS(alloc_scalars(h, L.scg, L.capg, nb));
       if (cfg.device_gmres) {
         int gmax = gmres_max_grid(L.dpre, L.R, L.capg);
-        // one CTA per stencil tile (32 x 16 nodes), at most one CTA per SM: every grid barrier
-        // then serialises at most #SM arrivals
-        int dev = 0, sms = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // small levels: at least ~256 nodes per CTA slice so the vector phases stay short
-        int want = std::min<long long>(sms, std::max<long long>(((L.nx + 31) / 32) * ((L.ny + 15) / 16),
-                                                                 ((long long)L.n + 255) / 256));
-        L.ggrid = std::min(gmax, want);
-        if (L.ggrid > 0) {
-          void* p;
-          CS(dalloc(h, &L.wg2, L.n * ep));
-          L.gpstride = 2 * (L.capg + 1) + 2;
-          CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
-          L.gpartA = (double*)p;
-          CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
-          L.gpartB = (double*)p;
-          CS(dalloc(h, &p, sizeof(double) * (2 * (size_t)L.capg * (L.capg + 1) + 2 * (size_t)L.capg +
-                                             3 * (size_t)L.gpstride)));
-          L.gR = (double*)p;
-          CS(dalloc(h, &p, sizeof(GmresState) * nb));
-          L.gst = (GmresState*)p;
-          CK(cudaMemsetAsync(L.gst, 0, sizeof(GmresState) * nb, h->ctx.s));
-        }
+        L.ggrid = std::min(gmax, gmres_grid_want(L.nx, L.ny));
+      }
+      // the cooperative kernel solves one right-hand side at a time: its basis holds one rhs
+      const size_t gb_rhs = L.ggrid > 0 ? L.n : bn;
+      CS(dalloc(h, &L.Vg, (L.capg + 1) * gb_rhs * ep));
+      CS(dalloc(h, &L.wg, gb_rhs * ep));
+      CS(alloc_scalars(h, L.scg, L.capg, nb));
+      if (L.ggrid > 0) {
+        void* p;
+        CS(dalloc(h, &L.wg2, L.n * ep));
+        L.gpstride = 2 * (L.capg + 1) + 2;
+        CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
+        L.gpartA = (double*)p;
+        CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
+        L.gpartB = (double*)p;
+        CS(dalloc(h, &p, sizeof(double) * (2 * (size_t)L.capg * (L.capg + 1) + 2 * (size_t)L.capg +
+                                           3 * (size_t)L.gpstride)));
+        L.gR = (double*)p;
+        CS(dalloc(h, &p, sizeof(GmresState) * nb));
+        L.gst = (GmresState*)p;
+        CK(cudaMemsetAsync(L.gst, 0, sizeof(GmresState) * nb, h->ctx.s));
       }
     }
   }
@@ -713,10 +771,19 @@ int collect_gmres_stats(Handle* h, int nb) {
     CK(cudaMemcpyAsync(gs.data(), L.gst, sizeof(GmresState) * nb, cudaMemcpyDeviceToHost, h->ctx.s));
     CK(cudaStreamSynchronize(h->ctx.s));
     int err = 0;
+    double bytes = 0;
     for (int q = 0; q < nb; ++q) {
       h->st[q].cslp_it[L.l - 1] += (int)gs[q].total_its;
+      bytes += gs[q].total_bytes;
       gs[q].total_its = 0;
+      gs[q].total_bytes = 0;
+      gs[q].total_reorth = 0;
       err |= gs[q].err;
+    }
+    // the kernel's algorithmic bytes are known only after it ran: credit them to the family
+    if (h->prof.on[F_GMRES]) {
+      h->prof.bytes[F_GMRES] += bytes;
+      if (L.l < kProfLevels) h->prof.bytes_lv[F_GMRES][L.l] += bytes;
     }
     CK(cudaMemcpyAsync(L.gst, gs.data(), sizeof(GmresState) * nb, cudaMemcpyHostToDevice, h->ctx.s));
     CK(cudaStreamSynchronize(h->ctx.s));

@@ -95,6 +95,8 @@ int dalloc(Handle* h, void** p, size_t bytes);
 int status_of(cudaError_t e, const char* where);
 
 int setup(Handle* h, const double* k_dev);
+int gmres_grid_want(int nx, int ny);
+size_t estimate_bytes(const hz_grid& g, const hz_config& cfg);
 void destroy(Handle* h);
 
 // drivers (all on nb right-hand sides in lockstep)

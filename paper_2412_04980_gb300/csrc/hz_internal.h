@@ -147,7 +147,9 @@ struct GmresState {
   int its;               // iterations of the last solve
   double est;            // residual estimate of the last solve
   long long total_its;   // iterations accumulated since the last statistics read
-  long long pad2[13];
+  double total_bytes;    // algorithmic bytes (reads + writes of vectors and k) since the last read
+  long long total_reorth;// second Gram-Schmidt passes since the last statistics read
+  long long pad2[11];
 };
 // Largest cooperative grid for the kernel variant (0 if it cannot be launched).
 int gmres_max_grid(int dt, int R, int cap);

@@ -542,6 +542,10 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   cx<T>* wnext = w1;
   int jstop = 0;
   double est = beta;
+  // algorithmic bytes of this solve in units of one vector (e n): ||b|| reads b once
+  const double eb = (double)sizeof(cx<T>), ekb = (double)sizeof(T);
+  double vec_units = 1.0, k_units = 0.0;
+  int reorths = 0;
   for (int j = 0; j < cap; ++j) {
     // op: V_j = s * src (own tile nodes), wnext = M_l V_j
     cx<T>* Vj = V + (size_t)j * n;
@@ -575,9 +579,12 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       __syncthreads();
     }
     if (!grid_sync(st, G)) return;
+    vec_units += 3.0;  // read src, write V_j and w
+    k_units += 1.0;
     // h = V^H w and ||w||^2; ||w'||^2 = ||w||^2 - sum |h_i|^2 (Pythagoras) unless the vector
     // loses more than reorth_eta of its norm, in which case a second classical pass runs
     const int nv = j + 1;
+    vec_units += nv + 1;  // read V_0..V_j and w
     dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
     if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
     {
@@ -595,6 +602,8 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     }
     __syncthreads();
     if (K.flags[1]) {  // second classical pass
+      ++reorths;
+      vec_units += (nv + 2) + (nv + 1);  // w -= V h (read V, w; write w), then V^H w again
       update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
       if (!grid_sync(st, G)) return;
       for (int i = threadIdx.x; i < 2 * nv; i += NT) h1T[i] = hT[i];
@@ -610,6 +619,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       __syncthreads();
     }
     if (!K.flags[0]) {  // w' = w - V h (with the last pass's coefficients); the next op needs it complete
+      vec_units += nv + 2;
       update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
       if (!grid_sync(st, G)) return;
     }
@@ -642,6 +652,9 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     st->its = jstop;
     st->est = est;
     st->total_its += jstop;
+    st->total_reorth += reorths;
+    // x += V y reads jstop basis vectors and x and writes x
+    st->total_bytes += (vec_units + jstop + 2) * eb * (double)n + k_units * ekb * (double)n;
   }
   if (!grid_sync(st, G)) return;
   for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(__ldcg(y + i));

@@ -74,3 +74,29 @@ def test_kernel_families(L):
     n = L.hz_kernel_family_count()
     names = [L.hz_kernel_family_name(i).decode() for i in range(n)]
     assert "mg_down" in names and "level_op" in names
+
+
+def test_estimate_bytes_host_only(L):
+    """hz_estimate_bytes needs no device: it grows with the grid and with max_rhs, and the
+    one-rhs basis of the cooperative GMRES path makes multi-rhs estimates smaller there."""
+    import paper_2412_04980_gb300 as hz
+    e = lambda n, **c: hz.estimate_bytes(n, n, 5.0, **c)
+    small, big = e(129, levels=2), e(257, levels=2)
+    assert 0 < small < big
+    assert e(513, levels=5, max_rhs=1) < e(513, levels=5, max_rhs=4)
+    assert e(513, levels=5, max_rhs=4, device_gmres=1) < e(513, levels=5, max_rhs=4, device_gmres=0)
+    assert e(513, levels=5, precision="mixed") < e(513, levels=5, precision="fp64")
+    assert L.hz_estimate_bytes(None, None, None) == hz.HZ_EINVAL
+
+
+def test_server_rejects_bad_arguments(L):
+    import paper_2412_04980_gb300 as hz
+    s = ctypes.c_void_p()
+    assert L.hz_server_create(0, 1, ctypes.byref(s)) == hz.HZ_EINVAL
+    assert L.hz_server_create(1 << 20, 0, ctypes.byref(s)) == hz.HZ_EINVAL
+    assert L.hz_server_create(1 << 20, 1, None) == hz.HZ_EINVAL
+    t = ctypes.c_uint64()
+    assert L.hz_submit(None, None, ctypes.byref(t)) == hz.HZ_EINVAL
+    assert L.hz_poll(None, 1, None) == hz.HZ_EINVAL
+    assert L.hz_wait(None, 1, 0.0, None) == hz.HZ_EINVAL
+    assert L.hz_server_destroy(None) == hz.HZ_OK
