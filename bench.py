@@ -43,7 +43,14 @@ WORKLOADS = {
     "random_1025": "1025x1025 seeded random-velocity model, k_max h = 0.3, 4-level MADP, tol 1e-6",
 }
 METRIC = "solves/s at a 1e-6 relative residual (time-to-solution = ms_per_step)"
-COUNTS_FILE = os.path.join(ROOT, "profiles", "solve_counts.json")
+# Iteration counts of one solve of each workload at tol 1e-6, mixed precision, as the GPU
+# solver reports them (hz_stats): the reference arm prices one solve of the oracle by timing
+# each of its primitives once per level and multiplying by these counts.
+SOLVE_COUNTS = {
+    "random_4097": {"outer": 18, "level_iterations": [0, 487, 487, 487, 487, 487, 0, 0, 0, 0],
+                    "level_calls": [0, 18, 487, 487, 487, 487, 0, 0, 0, 0],
+                    "cslp_gmres_iterations": [0, 0, 13550, 11436, 20406, 27245, 0, 0, 0, 0]},
+}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -154,11 +161,7 @@ def run_oracle_sample(workload: str, counts: dict) -> dict:
 
 
 def load_counts(workload: str):
-    if os.path.exists(COUNTS_FILE):
-        with open(COUNTS_FILE) as f:
-            allc = json.load(f)
-        return allc.get(workload)
-    return None
+    return SOLVE_COUNTS.get(workload)
 
 
 def cpu_line(workload, res, steps_note):
