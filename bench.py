@@ -41,6 +41,7 @@ WORKLOADS = {
     "wedge_289x481": "289x481 synthetic three-layer wedge, f = 20 Hz, kh_max = 0.1745, 4-level MADP, tol 1e-6",
     "mp1b_129": "129x129 constant k = 20, point source at the centre, 2-level, tol 1e-6",
     "random_1025": "1025x1025 seeded random-velocity model, k_max h = 0.3, 4-level MADP, tol 1e-6",
+    "random_513": "513x513 seeded random-velocity model, k_max h = 0.3, 3-level MADP, tol 1e-6",
 }
 METRIC = "solves/s at a 1e-6 relative residual (time-to-solution = ms_per_step)"
 # Iteration counts of one solve of each workload at tol 1e-6, mixed precision, as the GPU
@@ -65,16 +66,21 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--device-gmres", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="GMRES CSLP form: 1 cluster/grid by level size, 2 cooperative grid, 3 cluster, "
+                         "0 host-driven")
     ap.add_argument("--reorth-eta", type=float, default=None,
                     help="Gram-Schmidt reorthogonalisation threshold (library default if omitted)")
     ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply"],
                     help="time one building block on the workload's finest grid instead of a solve")
     ap.add_argument("--repeat", type=int, default=20)
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per call in --micro mode")
     ap.add_argument("--serve", action="store_true",
                     help="serving trace: mixed requests with Poisson arrivals through hz_server_*")
-    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--serve-sizes", default="257,513,1025,2049")
     ap.add_argument("--max-active", type=int, default=4)
-    ap.add_argument("--budget-gb", type=float, default=48.0)
+    ap.add_argument("--budget-gb", type=float, default=160.0)
     ap.add_argument("--load", type=float, default=1.0,
                     help="offered arrival rate as a multiple of the one-at-a-time service rate")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -252,8 +258,11 @@ def micro(args):
     prec = args.precision
     cdt = torch.complex64 if prec == "mixed" else torch.complex128
     extra = {"mg_max_level": 0} if args.micro == "gmres" else {}
-    H = hz.Helmholtz(k, p.h, levels=1, precision=prec, **extra)
-    f = torch.from_numpy(mp.random_complex((p.ny, p.nx), seed=7)).to(dev)
+    if args.device_gmres is not None:
+        extra["device_gmres"] = args.device_gmres
+    H = hz.Helmholtz(k, p.h, levels=1, precision=prec, max_rhs=args.nrhs, **extra)
+    shape = (p.ny, p.nx) if args.nrhs == 1 else (args.nrhs, p.ny, p.nx)
+    f = torch.from_numpy(mp.random_complex(shape, seed=7)).to(dev)
     if args.micro != "apply":
         f = f.to(cdt)
     fams = H.kernel_families()
@@ -271,6 +280,7 @@ def micro(args):
     e1.record()
     torch.cuda.synchronize()
     res = {"micro": args.micro, "workload": args.workload, "precision": prec, "repeat": args.repeat,
+           "nrhs": args.nrhs, "device_gmres": H.cfg.device_gmres,
            "ms_per_call": e0.elapsed_time(e1) / args.repeat}
     if args.micro == "gmres":
         res["iterations"] = out[1]
@@ -282,95 +292,92 @@ def micro(args):
     print(json.dumps(res))
 
 
-SERVE_MIX = [
-    # name, weight, problem factory, solver configuration
-    ("mp1b_129/fp64", 0.30, lambda: mp_named("mp1b_129"), dict(levels=2, precision="fp64")),
-    ("wedge_289x481/mixed", 0.30, lambda: mp_named("wedge_289x481"), dict(levels=4, negdef_from_level=5,
-                                                                          precision="mixed")),
-    ("random_513/mixed", 0.25, lambda: mp_random(513, 4), dict(levels=4, negdef_from_level=4, precision="mixed")),
-    ("random_1025/mixed", 0.15, lambda: mp_named("random_1025"), dict(levels=4, negdef_from_level=4,
-                                                                      precision="mixed")),
-]
+SERVE_LEVELS = {257: 2, 513: 3, 1025: 4, 2049: 5, 4097: 6}   # coarsest level 129^2
 
 
-def mp_named(name):
+def serve_trace(n_req: int, sizes, seed: int = 2024):
+    """Seeded request stream: grid side uniform over `sizes`, a random-velocity model seeded per
+    request (k_max h = 0.3, h = 5 m), 1-8 point sources on the top row, deflation levels down to a
+    129^2 coarsest grid, levels >= 4 treated as negative definite."""
+    import numpy as np
+
     import model_problems as mp
-    return mp.named(name)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(n_req):
+        n = int(sizes[int(rng.integers(len(sizes)))])
+        ns = int(rng.integers(1, 9))
+        p = mp.random_field(n, 5.0, seed=1000 + q, kh_max=0.3, levels=SERVE_LEVELS[n], negdef_from_level=4, nsrc=ns)
+        out.append(p)
+    return out
 
 
-def mp_random(n, levels):
-    import model_problems as mp
-    return mp.random_field(n, 5.0, seed=3, levels=levels, negdef_from_level=4)
+def run_trace(hz, reqs, arrivals, max_active, budget, precision):
+    """Submit reqs at the given arrival offsets (seconds; None = all at once) to a fresh server;
+    returns per-request latency and the server's report."""
+    srv = hz.Server(budget_bytes=budget, max_active=max_active)
+    tickets = []
+    t0 = time.perf_counter()
+    for i, p in enumerate(reqs):
+        if arrivals is not None:
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+        tickets.append(srv.submit(p.k, p.b, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level,
+                                  precision=precision, max_rhs=p.nrhs))
+    lat, worst = [], 0.0
+    for t in tickets:
+        _, st, ms = srv.wait(t, timeout_s=3600)
+        lat.append(ms)
+        worst = max(worst, max(x["true_relres"] for x in st))
+    wall = time.perf_counter() - t0
+    rep = srv.report()
+    srv.close()
+    nrhs = sum(p.nrhs for p in reqs)
+    lat_sorted = sorted(lat)
+    return {"requests_per_s": len(reqs) / wall, "rhs_per_s": nrhs / wall, "wall_s": wall,
+            "p50_ms": statistics.median(lat),
+            "p99_ms": lat_sorted[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)],
+            "peak_gb": rep["peak_bytes"] / 2 ** 30, "completed": rep["completed"], "failed": rep["failed"],
+            "max_true_relres": worst, "max_active": max_active, "precision": precision}
 
 
 def serve(args):
-    """Serving trace: a seeded mix of request types (sizes 129^2 to 1025^2, FP64 and mixed
-    precision, constant / wedge / random wavenumber fields, point sources at seeded top-row
-    nodes) arriving as a Poisson process, served by hz_server_* with max_active workers under
-    a device-memory budget.  The offered rate is --load times the one-at-a-time service rate
-    measured first, so max_active = 1 saturates at load 1 and overlap shows as lower latency
-    and higher solves/s.  Reports both servers on the same trace."""
+    """Serving stream (the solve-request workload with Poisson arrivals): seeded requests of
+    several grid sizes, wavenumber fields and source counts, admitted by a device-memory budget
+    through hz_server_*.  Passes over the same trace: (1) mixed precision one at a time with all
+    requests queued at once, which measures the service rate; (2) Poisson arrivals at --load
+    times that rate, mixed precision, --max-active concurrent solves; (3) the same arrivals, mixed
+    precision one at a time; (4) the same arrivals, plain FP64 one at a time."""
     import numpy as np
     import torch
 
-    import model_problems as mp
     import paper_2412_04980_gb300 as hz
 
     torch.cuda.set_device(0)
-    rng = np.random.Generator(np.random.PCG64(2024))
-    types = [(nm, w, f(), cfg) for nm, w, f, cfg in SERVE_MIX]
-    wts = np.array([t[1] for t in types])
-    kinds = rng.choice(len(types), size=args.requests, p=wts / wts.sum())
-    reqs = []
-    for q, ti in enumerate(kinds):
-        nm, _, p, cfg = types[ti]
-        i = int(rng.integers(1, p.nx - 1))
-        reqs.append((ti, p.k, mp.point_source(p.nx, p.ny, i, p.ny - 1, p.h), p.h, cfg))
-    # one-at-a-time service time per type (alone, after one warm-up), through the same server path
-    alone_ms = {}
-    srv = hz.Server(budget_bytes=int(args.budget_gb * 2 ** 30), max_active=1)
-    for ti, (nm, _, p, cfg) in enumerate(types):
-        for rep_ in range(2):
-            t = srv.submit(p.k, p.b[0], p.h, **dict(cfg))
-            _, st, ms = srv.wait(t)
-        alone_ms[nm] = ms
-    srv.close()
-    mean_service = sum(wts[i] / wts.sum() * alone_ms[types[i][0]] for i in range(len(types))) / 1e3
-    rate = args.load / mean_service
-    gaps = rng.exponential(1.0 / rate, size=args.requests)
-    out = {}
-    for ma in sorted({1, args.max_active}):
-        srv = hz.Server(budget_bytes=int(args.budget_gb * 2 ** 30), max_active=ma)
-        tickets = []
-        t0 = time.perf_counter()
-        due = t0
-        for (ti, k, b, h, cfg), g in zip(reqs, gaps):
-            due += g
-            dt = due - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            tickets.append(srv.submit(k, b, h, **dict(cfg)))
-        lat = []
-        its = []
-        for t in tickets:
-            _, st, ms = srv.wait(t, timeout_s=900)
-            lat.append(ms)
-            its.append(st[0]["outer_iterations"])
-        wall = time.perf_counter() - t0
-        rep_ = srv.report()
-        srv.close()
-        out[f"max_active_{ma}"] = {"solves_per_s": args.requests / wall, "p50_ms": rep_["p50_ms"],
-                                   "p99_ms": rep_["p99_ms"], "peak_gb": rep_["peak_bytes"] / 2 ** 30,
-                                   "completed": rep_["completed"], "failed": rep_["failed"], "wall_s": wall}
-    best = out[f"max_active_{args.max_active}"]
-    line = {"metric": "serving solves/s at a 1e-6 relative residual (mixed requests, Poisson arrivals)",
-            "mode": "serve", "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
-            "higher_is_better": True, "data": "synthetic",
-            "config": {"requests": args.requests, "load": args.load, "offered_rate_per_s": rate,
-                       "budget_gb": args.budget_gb, "max_active": args.max_active,
-                       "mix": {nm: w for nm, w, _, _ in SERVE_MIX},
-                       "requests_per_type": {types[i][0]: int((kinds == i).sum()) for i in range(len(types))}},
-            "alone_ms": alone_ms, "servers": out}
+    sizes = [int(x) for x in args.serve_sizes.split(",")]
+    reqs = serve_trace(args.requests, sizes)
+    budget = int(args.budget_gb * 2 ** 30)
+    warm = serve_trace(1, [min(sizes)], seed=7)
+    run_trace(hz, warm, None, 1, budget, "mixed")
+    closed = run_trace(hz, reqs, None, 1, budget, "mixed")
+    rate = args.load * closed["requests_per_s"]
+    rng = np.random.Generator(np.random.PCG64(99))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    mixed_c = run_trace(hz, reqs, arrivals, args.max_active, budget, "mixed")
+    mixed_1 = run_trace(hz, reqs, arrivals, 1, budget, "mixed")
+    fp64_1 = None if args.no_fp64 else run_trace(hz, reqs, arrivals, 1, budget, "fp64")
+    line = {"metric": "serving: solve requests/s and p50/p99 latency at a 1e-6 relative residual",
+            "mode": "serve", "value": mixed_c["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32+f64 (FP32 preconditioner, FP64 outer)",
+            "config": {"workload": "serving stream: Poisson arrivals of seeded random-velocity solve requests",
+                       "requests": len(reqs), "sizes": sizes, "sources_per_request": "1-8 (uniform)",
+                       "rhs_total": sum(p.nrhs for p in reqs), "load": args.load,
+                       "offered_rate_per_s": rate, "budget_gb": args.budget_gb, "max_active": args.max_active,
+                       "requests_per_size": {str(n): sum(1 for p in reqs if p.nx == n) for n in sizes}},
+            "p50_ms": mixed_c["p50_ms"], "p99_ms": mixed_c["p99_ms"],
+            "passes": {"mixed_one_at_a_time_all_queued": closed, "mixed_concurrent_poisson": mixed_c,
+                       "mixed_one_at_a_time_poisson": mixed_1, "fp64_one_at_a_time_poisson": fp64_1}}
     print(json.dumps(line))
 
 
@@ -434,6 +441,8 @@ def main():
     b = torch.from_numpy(p.b[0]).to(dev)
     stream = torch.cuda.current_stream(dev)
     extra = {} if args.reorth_eta is None else {"reorth_eta": args.reorth_eta}
+    if args.device_gmres is not None:
+        extra["device_gmres"] = args.device_gmres
     H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision,
                      **extra)
     u = torch.empty_like(b)
@@ -554,6 +563,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
                    "levels": p.levels, "nrhs": 1, "precision": args.precision, "reorth_eta": H.cfg.reorth_eta,
+                   "device_gmres": H.cfg.device_gmres,
                    "l2": f"inputs larger than L2: b is {nbytes / 1e6:.0f} MB and the solver touches "
                          f"{mem_gb:.1f} GB of workspace per solve",
                    "parallelism": f"replicas x{world}"},

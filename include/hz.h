@@ -95,8 +95,12 @@ typedef struct {
   int mg_coarsest_side;  /* multigrid coarsening stops at this many nodes per side, default 20 */
   int max_rhs;           /* largest nrhs any call on this handle will pass, default 1 */
   double timeout_s;      /* limit for every host wait on the device, default 600 s */
-  int device_gmres;      /* 1 (default): each GMRES CSLP solve runs as one cooperative kernel
-                            with on-device Givens rotations; 0: host-driven Arnoldi steps */
+  int device_gmres;      /* 1 (default): each GMRES CSLP solve runs as one persistent kernel with
+                            on-device Givens rotations: one thread-block cluster per right-hand
+                            side, all in one launch, for calls on 4 or more right-hand sides on
+                            levels of at most 300,000 nodes; otherwise a cooperative grid per
+                            right-hand side; 2: always the cooperative grid; 3: always clusters;
+                            0: host-driven Arnoldi steps */
   double reorth_eta;     /* classical Gram-Schmidt runs a second pass when the orthogonalised
                             vector keeps less than reorth_eta of its norm ("twice is enough"
                             test), default 0.1; 1 = always two passes, 0 = one pass */

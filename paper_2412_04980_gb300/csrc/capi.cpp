@@ -83,6 +83,7 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (c.mg_max_level < 0 || c.mg_coarsest_side < 3) return bad("invalid multigrid level settings");
   if (!(c.timeout_s > 0)) return bad("timeout_s must be positive");
   if (!(c.reorth_eta >= 0 && c.reorth_eta <= 1)) return bad("reorth_eta must be in [0, 1]");
+  if (c.device_gmres < 0 || c.device_gmres > 3) return bad("device_gmres must be 0, 1, 2 or 3");
   if (g.bc == HZ_BC_DIRICHLET && c.levels != 1) return bad("Dirichlet grids support the level-1 operator only");
   int nx = g.nx, ny = g.ny;
   for (int l = 1; l < c.levels; ++l) {

@@ -13,8 +13,10 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 
 namespace hz {
 
@@ -22,6 +24,18 @@ namespace hz {
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 const char* last_error_message() { return g_err.c_str(); }
+
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> limit;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[func];
+  if (cur >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 int status_of(cudaError_t e, const char* where) {
   if (e == cudaSuccess) return HZ_OK;
@@ -287,6 +301,19 @@ static std::vector<double> inject(const std::vector<double>& k, int nx, int ny) 
 // Cooperative grid of the persistent GMRES kernel: one CTA per 32 x 16 stencil tile and at
 // least ~256 nodes per CTA slice, at most one CTA per SM (every grid barrier then serialises
 // at most #SM arrivals).
+// With device_gmres = 1, calls on at least kClusterMinRhs right-hand sides of a level with at
+// most kClusterMaxN nodes run the persistent GMRES as one thread-block cluster per right-hand
+// side (all at once); otherwise the cooperative grid runs per right-hand side.  A 16-CTA cluster
+// alone streams far less than the whole GPU (measured on GB300: 513^2, 9 iterations, 1 rhs
+// 0.92 ms cluster vs 0.36 ms grid; 8 rhs 2.28 ms vs 2.67 ms; at 1025^2 the grid wins at 8 rhs).
+constexpr int kClusterMinRhs = 4;
+constexpr size_t kClusterMaxN = 300000;
+
+// The cluster form may run on a level of n nodes (it then needs per-rhs GMRES workspace).
+static bool cluster_form_possible(const hz_config& cfg, size_t n) {
+  return cfg.device_gmres == 3 || (cfg.device_gmres == 1 && cfg.max_rhs >= kClusterMinRhs && n <= kClusterMaxN);
+}
+
 int gmres_grid_want(int nx, int ny) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -331,12 +358,16 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       const int capg = std::max(1, krylov_cap(cfg.c_it, n));
       maxnv = std::max(maxnv, (size_t)capg + 1);
       const bool dev = cfg.device_gmres != 0;
-      const size_t gbr = dev ? n : bn;
+      // upper bound: the cluster form keeps per-rhs workspace
+      const bool clus = cluster_form_possible(cfg, n);
+      const size_t gbr = (dev && !clus) ? n : bn;
+      const size_t gq = clus ? (size_t)nb : 1;
       total += (capg + 1) * gbr * ep + gbr * ep + scal(capg);
       if (dev) {
         const size_t ps = 2 * (size_t)(capg + 1) + 2;
-        total += n * ep + 2 * sizeof(double) * 152 * ps +
-                 sizeof(double) * (2 * (size_t)capg * (capg + 1) + 2 * (size_t)capg + 3 * ps) + sizeof(GmresState) * nb;
+        total += gq * n * ep + 2 * sizeof(double) * std::max<size_t>(152, 16 * gq) * ps +
+                 sizeof(double) * gq * (2 * (size_t)capg * (capg + 1) + 2 * (size_t)capg + 3 * ps) +
+                 sizeof(GmresState) * nb;
       }
     }
     if (l < ml) {
@@ -473,24 +504,32 @@ int setup(Handle* h, const double* k_dev) {
       L.capg = std::max(1, krylov_cap(cfg.c_it, L.n));
       maxnv = std::max(maxnv, (size_t)L.capg + 1);
       if (cfg.device_gmres) {
-        int gmax = gmres_max_grid(L.dpre, L.R, L.capg);
-        L.ggrid = std::min(gmax, gmres_grid_want(L.nx, L.ny));
+        L.ggrid = std::min(gmres_max_grid(L.dpre, L.R, L.capg), gmres_grid_want(L.nx, L.ny));
+        L.gcl = cluster_form_possible(cfg, L.n) ? gmres_cluster_size(L.dpre, L.R, L.capg) : 0;
+        if (L.ggrid <= 0 && L.gcl <= 0) {
+          set_error("the persistent GMRES kernel cannot be launched on this device");
+          return HZ_ENOTSUP;
+        }
       }
-      // the cooperative kernel solves one right-hand side at a time: its basis holds one rhs
-      const size_t gb_rhs = L.ggrid > 0 ? L.n : bn;
+      // the cooperative grid solves one right-hand side at a time (its workspace holds one rhs);
+      // the cluster form solves all nb at once (workspace per rhs)
+      const bool dev = L.ggrid > 0 || L.gcl > 0;
+      const size_t gb_rhs = (dev && !L.gcl) ? L.n : bn;
+      const size_t gq = L.gcl ? (size_t)nb : 1;
       CS(dalloc(h, &L.Vg, (L.capg + 1) * gb_rhs * ep));
       CS(dalloc(h, &L.wg, gb_rhs * ep));
       CS(alloc_scalars(h, L.scg, L.capg, nb));
-      if (L.ggrid > 0) {
+      if (dev) {
         void* p;
-        CS(dalloc(h, &L.wg2, L.n * ep));
+        CS(dalloc(h, &L.wg2, gq * L.n * ep));
         L.gpstride = 2 * (L.capg + 1) + 2;
-        CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
+        const size_t nparts = std::max<size_t>(L.ggrid, gq * L.gcl);
+        CS(dalloc(h, &p, sizeof(double) * nparts * L.gpstride));
         L.gpartA = (double*)p;
-        CS(dalloc(h, &p, sizeof(double) * (size_t)L.ggrid * L.gpstride));
+        CS(dalloc(h, &p, sizeof(double) * nparts * L.gpstride));
         L.gpartB = (double*)p;
-        CS(dalloc(h, &p, sizeof(double) * (2 * (size_t)L.capg * (L.capg + 1) + 2 * (size_t)L.capg +
-                                           3 * (size_t)L.gpstride)));
+        CS(dalloc(h, &p, sizeof(double) * gq * (2 * (size_t)L.capg * (L.capg + 1) + 2 * (size_t)L.capg +
+                                                3 * (size_t)L.gpstride)));
         L.gR = (double*)p;
         CS(dalloc(h, &p, sizeof(GmresState) * nb));
         L.gst = (GmresState*)p;
@@ -801,13 +840,20 @@ int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
   Level& L = h->lv[l - 1];
   const int dt = L.dpre;
   OpDesc M = L.opM(dt, h->cfg.beta1, h->cfg.beta2);
-  if (L.ggrid > 0) {  // whole solve on the device, one cooperative launch per right-hand side
+  if (L.ggrid > 0 || L.gcl > 0) {  // whole solve on the device
     const size_t eb = elem_bytes(dt);
-    for (int q = 0; q < nb; ++q)
-      CK(launch_gmres_persistent(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb, (char*)x + (size_t)q * L.n * eb,
-                                 L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride, L.gR, L.gst + q, L.capg,
-                                 h->cfg.cslp_tol, L.ggrid,
-                                 h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta));
+    const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
+    const bool use_cluster =
+        L.gcl > 0 && (h->cfg.device_gmres == 3 || nb >= kClusterMinRhs || L.ggrid <= 0);
+    if (use_cluster) {  // one launch, one thread-block cluster per right-hand side
+      CK(launch_gmres_persistent(h->ctx, M, dt, b, x, L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride, L.gR, L.gst,
+                                 L.capg, h->cfg.cslp_tol, L.gcl, true, nb, eta2));
+    } else {  // one cooperative launch per right-hand side
+      for (int q = 0; q < nb; ++q)
+        CK(launch_gmres_persistent(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb,
+                                   (char*)x + (size_t)q * L.n * eb, L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride,
+                                   L.gR, L.gst + q, L.capg, h->cfg.cslp_tol, L.ggrid, false, 1, eta2));
+    }
     if (its_out) {
       std::vector<GmresState> gs(nb);
       CK(cudaMemcpyAsync(gs.data(), L.gst, sizeof(GmresState) * nb, cudaMemcpyDeviceToHost, h->ctx.s));

@@ -62,7 +62,8 @@ struct Level {
   int gpstride = 0;
   double* gR = nullptr;
   GmresState* gst = nullptr;                 // nbmax control blocks
-  int ggrid = 0;                             // cooperative grid size (0: host-driven GMRES)
+  int ggrid = 0;                             // CTAs of the cooperative-grid form (0: host-driven GMRES)
+  int gcl = 0;                               // CTAs per cluster of the cluster form (0: not used)
   OpDesc opA(int dt) const;
   OpDesc opM(int dt, double b1, double b2) const;
 };

@@ -30,6 +30,11 @@ enum Family {
 };
 const char* family_name(int f);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The limit is process-wide
+// per kernel and handles on other threads may launch the same kernel with a larger size at the
+// same time, so it is only ever raised (under a lock), never lowered.
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
+
 constexpr int kProfLevels = 11;  // index 0: not inside a level; 1..10: deflation level
 struct Prof {
   struct Rec { cudaEvent_t a, b; double bytes; int level; };
@@ -153,12 +158,18 @@ struct GmresState {
 };
 // Largest cooperative grid for the kernel variant (0 if it cannot be launched).
 int gmres_max_grid(int dt, int R, int cap);
-// x += GMRES(M, b) for one right-hand side, whole solve in one cooperative launch.
+// Largest thread-block cluster (16 or 8 CTAs) the cluster form can run in, 0 if none.
+int gmres_cluster_size(int dt, int R, int cap);
+// x += GMRES(M, b), whole solve in one launch: one right-hand side on a cooperative grid of
+// `grid` CTAs, or (cluster) nrhs right-hand sides, each on its own thread-block cluster of
+// `grid` <= 16 CTAs; per right-hand side q the cluster form offsets b, x, w0, w1 by q n, V by
+// q (cap + 1) n, partA/partB by q grid pstride, Rg by q (2 cap (cap + 1) + 2 cap + 3 pstride)
+// and st by q.
 // V: (cap+1) * n, w0/w1: n (dtype dt); partA/partB: grid * pstride doubles;
 // Rg: 2 * cap * (cap + 1) + 2 * cap + 3 * pstride doubles (Hessenberg, y, reduced values).
 cudaError_t launch_gmres_persistent(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
                                     void* w1, double* partA, double* partB, int pstride, double* Rg, GmresState* st,
-                                    int cap, double tol, int grid, double eta2);
+                                    int cap, double tol, int grid, bool cluster, int nrhs, double eta2);
 
 // ---- exact coarse stencils (stencil_gen.cpp) ----------------------------------------
 // 1-D Galerkin masks of level l (1-based), length 2R+1, as exact rationals rounded once.

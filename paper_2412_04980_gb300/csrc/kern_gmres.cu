@@ -11,10 +11,14 @@
 //   Givens  complex rotations and the residual estimate |g_{j+1}| in FP64, redundantly in
 //           each CTA; CTA 0 keeps the rotated Hessenberg columns for the final solve.
 //
-// Grid-wide ordering uses a sense-reversal barrier whose spin is bounded by a clock64
-// budget: a CTA that runs out sets an error flag, every CTA returns at its next barrier,
-// and the host reports HZ_ETIMEOUT.  Partials alternate between two buffers so that no
-// CTA overwrites partials another CTA is still reading.
+// Two launch forms share the kernel body.  Cooperative grid (large levels): grid-wide
+// ordering by a sense-reversal barrier whose spin is bounded by a clock64 budget (a CTA
+// that runs out sets an error flag, every CTA returns at its next barrier, and the host
+// reports HZ_ETIMEOUT); the last CTA to arrive reduces the partials.  Thread-block cluster
+// (small levels, where a barrier costs more than the vector work): the whole solve runs in
+// one cluster of up to 16 CTAs, ordered by the hardware cluster barrier (release/acquire at
+// cluster scope), and every CTA sums the cluster's partials itself in one fixed order.
+// Barriers separate every write of a partial buffer from the reads of its previous contents.
 #include <cuda_runtime.h>
 
 #include "hz_core.h"
@@ -140,6 +144,48 @@ __device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks
   return true;
 }
 
+// Hardware barrier over all threads of all CTAs of the cluster; orders global-memory writes
+// before it with reads after it (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <bool CL>
+__device__ __forceinline__ bool bar_all(hz::GmresState* gs, unsigned nblocks) {
+  if constexpr (CL) {
+    cluster_barrier();
+    return true;
+  } else {
+    return grid_sync(gs, nblocks);
+  }
+}
+
+constexpr int kMaxCluster = 16;
+
+// Barrier + reduction of the CTA partials part[b * pstride + i], b < nblocks, i < m into out[]
+// (shared).  Cluster form: every CTA adds the partials itself in increasing b, so all CTAs
+// hold bitwise-identical sums.
+template <bool CL>
+__device__ __forceinline__ bool reduce_all(hz::GmresState* gs, unsigned nblocks, const double* part, int pstride,
+                                           int m, double* red, double* out) {
+  if constexpr (CL) {
+    cluster_barrier();
+    for (int i = threadIdx.x; i < m; i += NT) {
+      double a[kMaxCluster];
+#pragma unroll
+      for (int b = 0; b < kMaxCluster; ++b) a[b] = b < (int)nblocks ? __ldcg(part + (size_t)b * pstride + i) : 0.0;
+      double t = a[0];
+#pragma unroll
+      for (int b = 1; b < kMaxCluster; ++b) t += a[b];
+      out[i] = t;
+    }
+    __syncthreads();
+    return true;
+  } else {
+    return grid_reduce(gs, nblocks, part, pstride, m, red, out);
+  }
+}
+
 // Convert m reduced FP64 values to the arithmetic type in parallel and return, in every
 // thread, the sum of squares of the first m2 of them (one warp reduction).
 template <typename T>
@@ -196,10 +242,10 @@ struct KShared {  // Krylov scratch in shared memory (after the tile)
   double* scal;   // [0] next scale, [1] beta, [2] ||w||^2, [3] ||w'||^2
 };
 
-// Contiguous slice of the vector owned by this CTA.
-__device__ __forceinline__ void my_slice(size_t n, size_t& s0, size_t& s1) {
-  const size_t S = (n + gridDim.x - 1) / gridDim.x;
-  s0 = (size_t)blockIdx.x * S;
+// Contiguous slice of the vector owned by CTA bid of the G CTAs that share one solve.
+__device__ __forceinline__ void my_slice(size_t n, unsigned bid, unsigned G, size_t& s0, size_t& s1) {
+  const size_t S = (n + G - 1) / G;
+  s0 = (size_t)bid * S;
   s1 = s0 + S < n ? s0 + S : n;
   if (s0 > n) s0 = n;
 }
@@ -208,10 +254,11 @@ __device__ __forceinline__ void my_slice(size_t n, size_t& s0, size_t& s1) {
 // Warps split the vectors (warp q takes i = q, q + NW, ...; the norm is one more "vector"),
 // lanes stream the slice; every partial is a complete sum over the slice, written by one lane.
 template <typename T>
-__device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm) {
+__device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
+                          unsigned bid, unsigned G) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   size_t s0, s1;
-  my_slice(n, s0, s1);
+  my_slice(n, bid, G, s0, s1);
   const int jobs = nv + (with_norm ? 1 : 0);
   for (int i = wid; i < jobs; i += NW) {
     const bool is_norm = i == nv;
@@ -248,10 +295,10 @@ __device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
     }
     if (lane == 0) {
       if (is_norm) {
-        part[(size_t)blockIdx.x * pstride + 2 * nv] = double(ar);
+        part[(size_t)bid * pstride + 2 * nv] = double(ar);
       } else {
-        part[(size_t)blockIdx.x * pstride + 2 * i] = double(ar);
-        part[(size_t)blockIdx.x * pstride + 2 * i + 1] = double(ai);
+        part[(size_t)bid * pstride + 2 * i] = double(ar);
+        part[(size_t)bid * pstride + 2 * i + 1] = double(ai);
       }
     }
   }
@@ -261,10 +308,10 @@ __device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
 // accumulates 8 vectors per pass; a warp transpose-reduction and one block combine per pass.
 template <typename T>
 __device__ void dots_elem(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
-                          double* wred) {
+                          double* wred, unsigned bid, unsigned G) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   size_t s0, s1;
-  my_slice(n, s0, s1);
+  my_slice(n, bid, G, s0, s1);
   const int passes = nv > 0 ? nv : (with_norm ? 1 : 0);
   for (int c0 = 0; c0 < passes; c0 += CV) {
     const int cnt = max(0, min(CV, nv - c0));
@@ -315,12 +362,12 @@ __device__ void dots_elem(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
     if (threadIdx.x < 2 * CV && (threadIdx.x >> 1) < cnt) {
       double t = 0;
       for (int q = 0; q < NW; ++q) t += wred[q * 2 * CV + threadIdx.x];
-      part[(size_t)blockIdx.x * pstride + 2 * c0 + threadIdx.x] = t;
+      part[(size_t)bid * pstride + 2 * c0 + threadIdx.x] = t;
     }
     if (nrm && threadIdx.x == 0) {
       double t = 0;
       for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CV + q];
-      part[(size_t)blockIdx.x * pstride + 2 * nv] = t;
+      part[(size_t)bid * pstride + 2 * nv] = t;
     }
     __syncthreads();
   }
@@ -330,9 +377,9 @@ constexpr size_t kLargeSlice = 8 * NT;  // slices above this use the element-par
 
 template <typename T>
 __device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
-                          double* wred) {
-  if ((n + gridDim.x - 1) / gridDim.x > kLargeSlice) dots_elem<T>(V, n, nv, w, part, pstride, with_norm, wred);
-  else dots_warp<T>(V, n, nv, w, part, pstride, with_norm);
+                          double* wred, unsigned bid, unsigned G) {
+  if ((n + G - 1) / G > kLargeSlice) dots_elem<T>(V, n, nv, w, part, pstride, with_norm, wred, bid, G);
+  else dots_warp<T>(V, n, nv, w, part, pstride, with_norm, bid, G);
 }
 
 // x[e] (+/-)= sum_i c_i V_i[e]; 8 vectors per step with all loads issued first (8 in flight).
@@ -371,14 +418,14 @@ __device__ __forceinline__ cx<T> axpy_all(cx<T> x, const cx<T>* V, size_t n, int
   return x;
 }
 
-// w -= sum_i h_i V_i over this CTA's slice; CTA partial of ||w||^2 into part[blockIdx.x * pstride]
+// w -= sum_i h_i V_i over this CTA's slice; with_norm: CTA partial of ||w||^2 into part[bid * pstride]
 template <typename T>
 __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T* sc, cx<T>* w, double* part,
-                            int pstride, double* wred, bool with_norm = true) {
+                            int pstride, double* wred, bool with_norm, unsigned bid, unsigned G) {
   for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(h[i]);
   __syncthreads();
   size_t s0, s1;
-  my_slice(n, s0, s1);
+  my_slice(n, bid, G, s0, s1);
   T acc = T(0);
   if (s1 - s0 > kLargeSlice) {
     for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += 4 * NT) {
@@ -427,7 +474,7 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
   if (threadIdx.x == 0) {
     double t = 0;
     for (int q = 0; q < NT / 32; ++q) t += wred[q];
-    part[(size_t)blockIdx.x * pstride] = t;
+    part[(size_t)bid * pstride] = t;
   }
 }
 
@@ -491,14 +538,34 @@ __device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn
     }
 }
 
-template <typename T, int R>
+template <typename T, int R, bool CL>
 __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict__ b, cx<T>* __restrict__ x,
                                               cx<T>* V, cx<T>* w0, cx<T>* w1, double* partA, double* partB,
                                               int pstride, double* Rg, hz::GmresState* st, int cap, double tol,
                                               double eta2) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const unsigned G = gridDim.x;
   const size_t n = (size_t)P.nx * P.ny;
+  // CTAs that share this solve: the cluster (one right-hand side per cluster) or the whole grid
+  unsigned bid, G;
+  if constexpr (CL) {
+    unsigned q;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(bid));
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(G));
+    asm("mov.u32 %0, %%clusterid.x;" : "=r"(q));
+    const size_t rgs = 2 * (size_t)cap * (cap + 1) + 2 * (size_t)cap + 3 * (size_t)pstride;
+    b += q * n;
+    x += q * n;
+    V += q * (size_t)(cap + 1) * n;
+    w0 += q * n;
+    w1 += q * n;
+    partA += (size_t)q * G * pstride;
+    partB += (size_t)q * G * pstride;
+    Rg += q * rgs;
+    st += q;
+  } else {
+    bid = blockIdx.x;
+    G = gridDim.x;
+  }
   const int tilesx = (P.nx + TOX - 1) / TOX, tilesy = (P.ny + TOY - 1) / TOY;
   const int ntiles = tilesx * tilesy;
   unsigned char* kp = smem + tile_smem_bytes<T, R>(TOX, TOY);
@@ -521,11 +588,11 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   double* red = Rg + 2 * (size_t)cap * (cap + 1) + 2 * (size_t)cap;  // 3 * pstride reduced values
 
   // beta = ||b||
-  dots_pass<T>(V, n, 0, b, partA, pstride, true, K.wred);
-  if (!grid_reduce(st, G, partA, pstride, 1, red, K.scal + 1)) return;
+  dots_pass<T>(V, n, 0, b, partA, pstride, true, K.wred, bid, G);
+  if (!reduce_all<CL>(st, G, partA, pstride, 1, red, K.scal + 1)) return;
   const double beta = sqrt(K.scal[1]);
   if (!(beta > 0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
       st->its = 0;
       st->est = 0;
     }
@@ -549,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   for (int j = 0; j < cap; ++j) {
     // op: V_j = s * src (own tile nodes), wnext = M_l V_j
     cx<T>* Vj = V + (size_t)j * n;
-    for (int t = blockIdx.x; t < ntiles; t += G) {
+    for (int t = bid; t < ntiles; t += G) {
       const int ox0 = (t % tilesx) * TOX, oy0 = (t / tilesx) * TOY;
       TileView<T, R> tv = make_tile<T, R>(smem, TOX, TOY, ox0, oy0);
       tile_fill<T, R>(tv, P, ScaledSrc<T>{src, P.nx, T(s)});
@@ -578,15 +645,15 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       }
       __syncthreads();
     }
-    if (!grid_sync(st, G)) return;
+    if (!bar_all<CL>(st, G)) return;
     vec_units += 3.0;  // read src, write V_j and w
     k_units += 1.0;
     // h = V^H w and ||w||^2; ||w'||^2 = ||w||^2 - sum |h_i|^2 (Pythagoras) unless the vector
     // loses more than reorth_eta of its norm, in which case a second classical pass runs
     const int nv = j + 1;
     vec_units += nv + 1;  // read V_0..V_j and w
-    dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
-    if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
+    dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
+    if (!reduce_all<CL>(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
     {
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
       if (threadIdx.x == 0) {
@@ -596,7 +663,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
         K.flags[1] = !(hp >= eta2 * wn2);
         if (!K.flags[1])
           givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT,
-                         blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
+                         bid == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
                          K.scal);
       }
     }
@@ -604,24 +671,24 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     if (K.flags[1]) {  // second classical pass
       ++reorths;
       vec_units += (nv + 2) + (nv + 1);  // w -= V h (read V, w; write w), then V^H w again
-      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
-      if (!grid_sync(st, G)) return;
+      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false, bid, G);
+      if (!bar_all<CL>(st, G)) return;
       for (int i = threadIdx.x; i < 2 * nv; i += NT) h1T[i] = hT[i];
-      dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred);
-      if (!grid_reduce(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
+      dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
+      if (!reduce_all<CL>(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
       if (threadIdx.x == 0) {
         const double hp = K.h[2 * nv] - double(hs);
         givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT,
-                       blockIdx.x == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
+                       bid == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
                        K.scal);
       }
       __syncthreads();
     }
     if (!K.flags[0]) {  // w' = w - V h (with the last pass's coefficients); the next op needs it complete
       vec_units += nv + 2;
-      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false);
-      if (!grid_sync(st, G)) return;
+      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false, bid, G);
+      if (!bar_all<CL>(st, G)) return;
     }
     est = K.scal[2];
     if (K.flags[0]) {
@@ -636,7 +703,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   }
   // y = R^-1 g (CTA 0), then x += V y everywhere
   double* y = Rg + 2 * (size_t)cap * (cap + 1);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // Rg and y are written and read by this thread only
+  if (bid == 0 && threadIdx.x == 0) {  // Rg and y are written and read by this thread only
     for (int i = jstop - 1; i >= 0; --i) {
       double sr = double(gT[2 * i]), si = double(gT[2 * i + 1]);
       for (int q = i + 1; q < jstop; ++q) {
@@ -656,11 +723,11 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     // x += V y reads jstop basis vectors and x and writes x
     st->total_bytes += (vec_units + jstop + 2) * eb * (double)n + k_units * ekb * (double)n;
   }
-  if (!grid_sync(st, G)) return;
+  if (!bar_all<CL>(st, G)) return;
   for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(__ldcg(y + i));
   __syncthreads();
   size_t s0, s1;
-  my_slice(n, s0, s1);
+  my_slice(n, bid, G, s0, s1);
   for (size_t e = s0 + threadIdx.x; e < s1; e += NT) x[e] = axpy_all<T, false>(x[e], V, n, jstop, sc, e);
 }
 
@@ -697,19 +764,73 @@ size_t kshared_bytes(int cap) {
 template <typename T, int R>
 cudaError_t gmres_t(hz::Ctx& c, const hz::OpDesc& d, const void* b, void* x, void* V, void* w0, void* w1,
                     double* partA, double* partB, int pstride, double* Rg, hz::GmresState* st, int cap, double tol,
-                    int grid, double eta2) {
+                    int grid, bool cluster, int nrhs, double eta2) {
   const size_t sm = kshared_bytes<T, R>(cap);
-  cudaError_t e = cudaFuncSetAttribute(k_gmres<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   OpP<T> P = mkop<T>(d);
   const cx<T>* bb = reinterpret_cast<const cx<T>*>(b);
   cx<T>* xx = reinterpret_cast<cx<T>*>(x);
   cx<T>* VV = reinterpret_cast<cx<T>*>(V);
   cx<T>* a0 = reinterpret_cast<cx<T>*>(w0);
   cx<T>* a1 = reinterpret_cast<cx<T>*>(w1);
+  if (cluster) {  // nrhs clusters of `grid` CTAs, cluster q solves right-hand side q
+    if (grid < 1 || grid > kMaxCluster || nrhs < 1) return cudaErrorInvalidValue;
+    cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, true>), sm);
+    if (e != cudaSuccess) return e;
+    if (grid > 8 && (e = cudaFuncSetAttribute(k_gmres<T, R, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                        cudaSuccess)
+      return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid * nrhs);
+    lc.blockDim = dim3(NT);
+    lc.dynamicSmemBytes = sm;
+    lc.stream = c.s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = grid;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    hz::ProfScope ps(c, hz::F_GMRES, 0.0);
+    return cudaLaunchKernelEx(&lc, k_gmres<T, R, true>, P, bb, xx, VV, a0, a1, partA, partB, pstride, Rg, st, cap, tol,
+                              eta2);
+  }
+  if (nrhs != 1) return cudaErrorInvalidValue;  // the cooperative grid solves one right-hand side
+  cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, false>), sm);
+  if (e != cudaSuccess) return e;
   void* args[] = {&P, &bb, &xx, &VV, &a0, &a1, &partA, &partB, &pstride, &Rg, &st, &cap, &tol, &eta2};
   hz::ProfScope ps(c, hz::F_GMRES, 0.0);
-  return cudaLaunchCooperativeKernel((const void*)k_gmres<T, R>, dim3(grid), dim3(NT), args, sm, c.s);
+  return cudaLaunchCooperativeKernel((const void*)k_gmres<T, R, false>, dim3(grid), dim3(NT), args, sm, c.s);
+}
+
+// Largest cluster (16, else 8) of the cluster form that the device can place, 0 if none.
+template <typename T, int R>
+int cluster_size_t(int cap) {
+  const size_t sm = kshared_bytes<T, R>(cap);
+  if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, true>), sm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const bool np = cudaFuncSetAttribute(k_gmres<T, R, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess;
+  cudaGetLastError();
+  for (int C = np ? kMaxCluster : 8; C >= 8; C /= 2) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(C);
+    lc.blockDim = dim3(NT);
+    lc.dynamicSmemBytes = sm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, k_gmres<T, R, true>, &lc) == cudaSuccess && num >= 1) return C;
+    cudaGetLastError();
+  }
+  return 0;
 }
 
 template <typename T, int R>
@@ -718,8 +839,9 @@ int max_grid_t(int cap) {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   const size_t sm = kshared_bytes<T, R>(cap);
-  if (cudaFuncSetAttribute(k_gmres<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres<T, R>, NT, sm) != cudaSuccess) return 0;
+  if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, false>), sm) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres<T, R, false>, NT, sm) != cudaSuccess) return 0;
   return per * sms;
 }
 
@@ -740,18 +862,34 @@ int gmres_max_grid(int dt, int R, int cap) {
   return 0;
 }
 
+int gmres_cluster_size(int dt, int R, int cap) {
+  if (dt == C128) {
+    if (R == 1) return cluster_size_t<double, 1>(cap);
+    if (R == 2) return cluster_size_t<double, 2>(cap);
+    if (R == 3) return cluster_size_t<double, 3>(cap);
+  } else {
+    if (R == 1) return cluster_size_t<float, 1>(cap);
+    if (R == 2) return cluster_size_t<float, 2>(cap);
+    if (R == 3) return cluster_size_t<float, 3>(cap);
+  }
+  return 0;
+}
+
 cudaError_t launch_gmres_persistent(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
                                     void* w1, double* partA, double* partB, int pstride, double* Rg, GmresState* st,
-                                    int cap, double tol, int grid, double eta2) {
+                                    int cap, double tol, int grid, bool cluster, int nrhs, double eta2) {
+#define HZ_GM(T_, R_) \
+  return gmres_t<T_, R_>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, cluster, nrhs, eta2)
   if (dt == C128) {
-    if (M.R == 1) return gmres_t<double, 1>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
-    if (M.R == 2) return gmres_t<double, 2>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
-    if (M.R == 3) return gmres_t<double, 3>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+    if (M.R == 1) HZ_GM(double, 1);
+    if (M.R == 2) HZ_GM(double, 2);
+    if (M.R == 3) HZ_GM(double, 3);
   } else {
-    if (M.R == 1) return gmres_t<float, 1>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
-    if (M.R == 2) return gmres_t<float, 2>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
-    if (M.R == 3) return gmres_t<float, 3>(c, M, b, x, V, w0, w1, partA, partB, pstride, Rg, st, cap, tol, grid, eta2);
+    if (M.R == 1) HZ_GM(float, 1);
+    if (M.R == 2) HZ_GM(float, 2);
+    if (M.R == 3) HZ_GM(float, 3);
   }
+#undef HZ_GM
   return cudaErrorInvalidValue;
 }
 

@@ -426,8 +426,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(const cx<T>* __restrict__ e
 // ---------------------------------------------------------------------------------------
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaSuccess;
+  return hz::ensure_dyn_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 inline unsigned grid1d(size_t n) {

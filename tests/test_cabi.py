@@ -78,13 +78,17 @@ def test_kernel_families(L):
 
 def test_estimate_bytes_host_only(L):
     """hz_estimate_bytes needs no device: it grows with the grid and with max_rhs, and the
-    one-rhs basis of the cooperative GMRES path makes multi-rhs estimates smaller there."""
+    one-rhs basis of the cooperative-grid GMRES (device_gmres = 2) makes multi-rhs estimates
+    smaller there than with per-rhs workspace."""
     import paper_2412_04980_gb300 as hz
     e = lambda n, **c: hz.estimate_bytes(n, n, 5.0, **c)
     small, big = e(129, levels=2), e(257, levels=2)
     assert 0 < small < big
     assert e(513, levels=5, max_rhs=1) < e(513, levels=5, max_rhs=4)
-    assert e(513, levels=5, max_rhs=4, device_gmres=1) < e(513, levels=5, max_rhs=4, device_gmres=0)
+    assert e(513, levels=5, max_rhs=4, device_gmres=2) < e(513, levels=5, max_rhs=4, device_gmres=0)
+    assert e(513, levels=5, max_rhs=4, device_gmres=2) < e(513, levels=5, max_rhs=4, device_gmres=3)
+    assert e(513, levels=5, max_rhs=3, device_gmres=1) == e(513, levels=5, max_rhs=3, device_gmres=2)
+    assert e(513, levels=5, max_rhs=4, device_gmres=1) == e(513, levels=5, max_rhs=4, device_gmres=3)
     assert e(513, levels=5, precision="mixed") < e(513, levels=5, precision="fp64")
     assert L.hz_estimate_bytes(None, None, None) == hz.HZ_EINVAL
 

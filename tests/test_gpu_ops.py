@@ -187,10 +187,11 @@ def test_mg_vcycle_general_path_matches(hz):
 
 # ---- a9: CSLP inverse by GMRES (levels >= 3) -------------------------------------------------------
 @pytest.mark.parametrize("level", [3, 4])
-@pytest.mark.parametrize("device_gmres", [1, 0])
+@pytest.mark.parametrize("device_gmres", [1, 3, 0])
 def test_cslp_gmres_fp64(hz, level, device_gmres):
-    """Whole-solve cooperative kernel (device_gmres = 1) and host-driven Arnoldi steps
-    (device_gmres = 0) both reproduce the oracle's GMRES: same iteration count, same x."""
+    """Whole-solve kernel as a cooperative grid (device_gmres = 1 with one right-hand side), in
+    one thread-block cluster (3) and host-driven Arnoldi steps (0) all reproduce the oracle's
+    GMRES: same iteration count, same x."""
     ny, nx = 257, 257
     h = 5.0
     p = mp.random_field(257, h, seed=3, kh_max=0.3, levels=4)
@@ -207,12 +208,14 @@ def test_cslp_gmres_fp64(hz, level, device_gmres):
     assert its_ref <= krylov_cap(6.0, cy * cx)
 
 
-@pytest.mark.parametrize("level", [1, 3])
-def test_cslp_gmres_fp32(hz, level):
+@pytest.mark.parametrize("level,n,device_gmres", [(1, 1025, 1), (3, 257, 1), (3, 257, 3), (1, 257, 3), (1, 1025, 3)])
+def test_cslp_gmres_fp32(hz, level, n, device_gmres):
     """FP32 GMRES (device kernel) reaches the 0.1 tolerance measured in FP64 and stays within
-    two iterations of the FP64 oracle; level 1 runs GMRES on a 1025^2 grid (mg_max_level = 0)."""
-    p = mp.random_field(1025 if level == 1 else 257, 5.0, seed=3, kh_max=0.3, levels=4 if level == 3 else 1)
-    H = handle(hz, p.k, p.h, levels=p.levels, precision="mixed", mg_max_level=0 if level == 1 else 2)
+    two iterations of the FP64 oracle; level 1 runs GMRES on the finest grid (mg_max_level = 0),
+    as a cooperative grid (1) and in one cluster with large per-CTA slices (3)."""
+    p = mp.random_field(n, 5.0, seed=3, kh_max=0.3, levels=4 if level == 3 else 1)
+    H = handle(hz, p.k, p.h, levels=p.levels, precision="mixed", mg_max_level=0 if level == 1 else 2,
+               device_gmres=device_gmres)
     cy, cx = H.level_size(level)
     kl = T.inject(p.k, 2 ** (level - 1))
     b = round32(mp.random_complex((cy, cx), seed=25))

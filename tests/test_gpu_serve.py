@@ -36,8 +36,8 @@ def _alone(hz, p, cfg):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("device_gmres", [1, 0])
-@pytest.mark.parametrize("max_rhs", [1, 3])
+@pytest.mark.parametrize("device_gmres", [1, 2, 3, 0])
+@pytest.mark.parametrize("max_rhs", [1, 4])
 def test_estimate_bounds_setup_bytes(hz, precision, device_gmres, max_rhs):
     p = mp.random_field(513, 5.0, seed=3, kh_max=0.3, levels=5)
     cfg = dict(levels=5, precision=precision, device_gmres=device_gmres, max_rhs=max_rhs, negdef_from_level=5)

@@ -62,10 +62,14 @@ def test_solve_wedge_289x481(hz, precision):
     assert abs(st["outer_iterations"] - rst.outer_iterations) <= 1
 
 
-def test_solve_batched_equals_alone(hz):
-    """Three right-hand sides in one lockstep batch give the same result as each alone."""
+@pytest.mark.parametrize("device_gmres", [1, 3])
+def test_solve_batched_equals_alone(hz, device_gmres):
+    """Three right-hand sides in one lockstep batch give the same result as each alone, with the
+    level-3 GMRES as a cooperative grid per right-hand side (1) and as one cluster per
+    right-hand side in a single launch (3)."""
     p = mp.random_field(129, 5.0, seed=3, kh_max=0.3, levels=3, negdef_from_level=4, nsrc=3)
-    H = hz.Helmholtz(dev(p.k), p.h, levels=3, negdef_from_level=4, precision="mixed", max_rhs=3)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=3, negdef_from_level=4, precision="mixed", max_rhs=3,
+                     device_gmres=device_gmres)
     ub, stb = H.solve(dev(p.b), tol=1e-6)
     ub = host(ub)
     for r in range(3):
