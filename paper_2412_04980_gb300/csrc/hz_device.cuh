@@ -144,6 +144,9 @@ __device__ __forceinline__ TileView<T, R> make_tile(void* smem, int OX, int OY, 
   return t;
 }
 
+template <typename T, int R>
+__device__ __forceinline__ void tile_finish(const TileView<T, R>& t, const OpP<T>& P);
+
 // Stage 1: fill in-grid cells from src(gx, gy) (out-of-grid cells = 0) and W = k^2 u.
 // Stage 2: Sommerfeld ghost layer.  Stage 3 (R >= 2): x-passes.  Ends synchronised.
 template <typename T, int R, class Src>
@@ -168,6 +171,17 @@ __device__ __forceinline__ void tile_fill(const TileView<T, R>& t, const OpP<T>&
     if (R >= 2) t.W[idx] = w;
   }
   __syncthreads();
+  tile_finish<T, R>(t, P);
+}
+
+// Stages 2 and 3 of tile_fill (ghost layer, x-passes) on a tile whose U (and W) are staged
+// and synchronised.  Ends synchronised.
+template <typename T, int R>
+__device__ __forceinline__ void tile_finish(const TileView<T, R>& t, const OpP<T>& P) {
+  const int WX = t.WX(), WY = t.WY();
+  const int nthr = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int gx0 = t.ox0 - R, gy0 = t.oy0 - R;
   if (P.bc == 0) {
     const T two_h = T(2) * P.H;
     // left (gx = -1) and right (gx = nx) ghost columns, rows inside the grid

@@ -74,72 +74,35 @@ __device__ __forceinline__ bool grid_sync(hz::GmresState* gs, unsigned nblocks) 
   return !failed(gs);
 }
 
-// Grid barrier that also reduces CTA partials: the last CTA to arrive sums
-// part[b * pstride + i] over all CTAs b for i < m (one warp per value, lanes stride over CTAs,
-// fixed order, so the result does not depend on which CTA arrives last), stores the sums in
-// red[] (global), then releases the others.  Every CTA returns with red[0..m) copied to out[].
+// Grid barrier that also reduces CTA partials: after the barrier every CTA sums
+// part[b * pstride + i] over all CTAs b for i < m itself (one warp per value, K lanes striding
+// over the CTAs, then a fixed shuffle tree), so every CTA holds bitwise-identical sums in out[]
+// (shared) without a serial reduction by one CTA and a second wait for it.
 __device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks, const double* part, int pstride,
-                                            int m, double* red, double* out) {
-  __shared__ int last;
-  __shared__ unsigned gen0;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    gen0 = *((volatile unsigned*)&gs->gen);
-    __threadfence();
-    last = atomicAdd(&gs->count, 1u) == nblocks - 1;
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    // K lanes per value (K a power of two <= 32), every lane sums a strided subset of the CTA
-    // partials with its loads issued together, then the K lanes combine by shuffles
-    int K = 32;
-    while (K > 1 && (NT / K) < m) K >>= 1;
-    const int lane = threadIdx.x & 31;
-    const int per_warp = 32 / K;
-    for (int base = 0; base < m; base += (NT / 32) * per_warp) {
-      const int i = base + (threadIdx.x >> 5) * per_warp + lane / K;
-      const int k = lane % K;
-      double t = 0;
-      if (i < m) {
-        double a[8];
-        int b = k;
-        for (; b + 7 * K < (int)nblocks; b += 8 * K) {
+                                            int m, double* /*red*/, double* out) {
+  if (!grid_sync(gs, nblocks)) return false;
+  int K = 32;
+  while (K > 1 && (NT / K) < m) K >>= 1;
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / K;
+  for (int base = 0; base < m; base += (NT / 32) * per_warp) {
+    const int i = base + (threadIdx.x >> 5) * per_warp + lane / K;
+    const int k = lane % K;
+    double t = 0;
+    if (i < m) {
+      double a[8];
+      int b = k;
+      for (; b + 7 * K < (int)nblocks; b += 8 * K) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) a[u] = __ldcg(part + (size_t)(b + u * K) * pstride + i);
+        for (int u = 0; u < 8; ++u) a[u] = __ldcg(part + (size_t)(b + u * K) * pstride + i);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) t += a[u];
-        }
-        for (; b < (int)nblocks; b += K) t += __ldcg(part + (size_t)b * pstride + i);
+        for (int u = 0; u < 8; ++u) t += a[u];
       }
-      for (int o = K / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (i < m && k == 0) red[i] = t;
+      for (; b < (int)nblocks; b += K) t += __ldcg(part + (size_t)b * pstride + i);
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      atomicExch(&gs->count, 0u);
-      __threadfence();
-      atomicAdd(&gs->gen, 1u);
-    }
-  } else {
-    if (threadIdx.x == 0) {
-      volatile unsigned* vgen = &gs->gen;
-      const long long t0 = clock64();
-      while (*vgen == gen0) {
-        if (failed(gs)) break;
-        if (clock64() - t0 > kSpinCycles) {
-          atomicExch(&gs->err, 1);
-          break;
-        }
-        __nanosleep(32);
-      }
-      __threadfence();
-    }
+    for (int o = K / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (i < m && k == 0) out[i] = t;
   }
-  __syncthreads();
-  if (failed(gs)) return false;
-  for (int i = threadIdx.x; i < m; i += NT) out[i] = __ldcg(red + i);
   __syncthreads();
   return true;
 }
@@ -223,12 +186,38 @@ __device__ __forceinline__ T warp_tsum(T (&v)[CNT]) {
   return x;
 }
 
-template <typename T>
-struct ScaledSrc {
-  const cx<T>* x;
-  int nx;
-  T s;
-  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const { return s * ldcg(x + (size_t)gy * nx + gx); }
+// Software-pipelined staging of the operator tiles: every thread holds the source values (and
+// wavenumbers) of up to PF cells of the next tile in registers while the current tile computes.
+template <typename T, int R>
+struct TilePrefetch {
+  static constexpr int PF = ((TOX + 2 * R) * (TOY + 2 * R) + NT - 1) / NT;
+  cx<T> v[PF];
+  T k[PF];
+  __device__ __forceinline__ void load(const OpP<T>& P, const cx<T>* src, int ox0, int oy0) {
+    constexpr int WX = TOX + 2 * R, WY = TOY + 2 * R;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int idx = threadIdx.x + u * NT;
+      const int cy = idx / WX, cxx = idx - cy * WX;
+      const int gx = ox0 - R + cxx, gy = oy0 - R + cy;
+      const bool in = idx < WX * WY && gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny;
+      v[u] = in ? ldcg(src + (size_t)gy * P.nx + gx) : mk<T>(T(0), T(0));
+      if (R >= 2) k[u] = in ? P.k[(size_t)gy * P.nx + gx] : T(0);
+    }
+  }
+  // U = s v (zero outside the grid), W = k^2 U
+  __device__ __forceinline__ void store(const TileView<T, R>& t, T s) const {
+    constexpr int WX = TOX + 2 * R, WY = TOY + 2 * R;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int idx = threadIdx.x + u * NT;
+      if (idx < WX * WY) {
+        const cx<T> sv = s * v[u];
+        t.U[idx] = sv;
+        if (R >= 2) t.W[idx] = (k[u] * k[u]) * sv;
+      }
+    }
+  }
 };
 
 struct KShared {  // Krylov scratch in shared memory (after the tile)
@@ -383,16 +372,19 @@ __device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
 }
 
 // x[e] (+/-)= sum_i c_i V_i[e]; 8 vectors per step with all loads issued first (8 in flight).
+// The vectors are visited from V_{nv-1} down to V_0: the Gram-Schmidt dots just read the basis
+// upwards, so the most recently read vectors (still in L2) come first.
 template <typename T, bool SUB>
 __device__ __forceinline__ cx<T> axpy_all(cx<T> x, const cx<T>* V, size_t n, int nv, const T* sc, size_t e) {
-  int i = 0;
-  for (; i + 7 < nv; i += 8) {
+  int r = 0;
+  for (; r + 7 < nv; r += 8) {
     cx<T> v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = ldcg(V + (size_t)(i + u) * n + e);
+    for (int u = 0; u < 8; ++u) v[u] = ldcg(V + (size_t)(nv - 1 - r - u) * n + e);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const T cr = sc[2 * (i + u)], ci = sc[2 * (i + u) + 1];
+      const int i = nv - 1 - r - u;
+      const T cr = sc[2 * i], ci = sc[2 * i + 1];
       const T pr = cr * v[u].re - ci * v[u].im, pi = cr * v[u].im + ci * v[u].re;
       if (SUB) {
         x.re -= pr;
@@ -403,7 +395,8 @@ __device__ __forceinline__ cx<T> axpy_all(cx<T> x, const cx<T>* V, size_t n, int
       }
     }
   }
-  for (; i < nv; ++i) {
+  for (; r < nv; ++r) {
+    const int i = nv - 1 - r;
     const cx<T> v = ldcg(V + (size_t)i * n + e);
     const T cr = sc[2 * i], ci = sc[2 * i + 1];
     const T pr = cr * v.re - ci * v.im, pi = cr * v.im + ci * v.re;
@@ -435,7 +428,7 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
         const size_t e = e0 + k * NT;
         x[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
       }
-      for (int i = 0; i < nv; ++i) {
+      for (int i = nv - 1; i >= 0; --i) {  // downwards: the last-read vectors are in L2
         const cx<T>* Vi = V + (size_t)i * n;
         const T cr = sc[2 * i], ci = sc[2 * i + 1];
         cx<T> v[4];
@@ -480,26 +473,42 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
 
 // One Givens step on Hessenberg column j (entries h[0..2j+1] plus, with h2, a second-pass
 // correction), subdiagonal hn2 = |h_{j+1,j}|^2, in the arithmetic type G_ with the rotation
-// state (gc, gs, g) held in shared memory in that type.  Writes the rotated column to Rc
+// state (gc, gs, g) held in shared memory in that type.  Leaves the rotated column in col
 // (FP64, CTA 0 only), the residual estimate |g_{j+1}|, the stop flag and 1/h_{j+1,j}.
 template <typename G_>
 __device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn2, G_* col, G_* gc, G_* gs, G_* g,
-                            double* Rc, double tol_abs, double* est, int* stop, double* scale) {
+                            double tol_abs, double* est, int* stop, double* scale) {
   // rotations i < j applied to the new column: the second entry of rotation i is the first
-  // entry of rotation i + 1, so it travels in registers; the other operands are independent loads
+  // entry of rotation i + 1, so it travels in registers.  The other operands of 4 rotations are
+  // loaded into registers before the 4 steps run (the column stores could otherwise alias the
+  // next loads and serialise every step on shared-memory latency).
   const G_ hn = hn2 > 0 ? G_(sqrt(hn2)) : G_(0);
   G_ ar = h[0] + (h2 ? h2[0] : G_(0)), ai = h[1] + (h2 ? h2[1] : G_(0));
-  for (int i = 0; i < j; ++i) {
-    const G_ br = h[2 * i + 2] + (h2 ? h2[2 * i + 2] : G_(0));
-    const G_ bi = h[2 * i + 3] + (h2 ? h2[2 * i + 3] : G_(0));
-    const G_ c = gc[i], sr = gs[2 * i], si = gs[2 * i + 1];
-    // (a, b) <- (c a + s b, -conj(s) a + c b)
-    col[2 * i] = c * ar + (sr * br - si * bi);
-    col[2 * i + 1] = c * ai + (sr * bi + si * br);
-    const G_ nr = -(sr * ar + si * ai) + c * br;
-    const G_ ni = -(sr * ai - si * ar) + c * bi;
-    ar = nr;
-    ai = ni;
+  constexpr int GB = 4;
+  for (int i0 = 0; i0 < j; i0 += GB) {
+    G_ bR[GB], bI[GB], cC[GB], sR[GB], sI[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int i = min(i0 + u, j - 1);  // in-range index; steps past j - 1 are skipped below
+      bR[u] = h[2 * i + 2] + (h2 ? h2[2 * i + 2] : G_(0));
+      bI[u] = h[2 * i + 3] + (h2 ? h2[2 * i + 3] : G_(0));
+      cC[u] = gc[i];
+      sR[u] = gs[2 * i];
+      sI[u] = gs[2 * i + 1];
+    }
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      if (i0 + u < j) {
+        const G_ br = bR[u], bi = bI[u], c = cC[u], sr = sR[u], si = sI[u];
+        // (a, b) <- (c a + s b, -conj(s) a + c b)
+        col[2 * (i0 + u)] = c * ar + (sr * br - si * bi);
+        col[2 * (i0 + u) + 1] = c * ai + (sr * bi + si * br);
+        const G_ nr = -(sr * ar + si * ai) + c * br;
+        const G_ ni = -(sr * ai - si * ar) + c * bi;
+        ar = nr;
+        ai = ni;
+      }
+    }
   }
   const G_ aa = sqrt(ar * ar + ai * ai);
   const G_ tt = sqrt(aa * aa + hn * hn);
@@ -531,11 +540,6 @@ __device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn
   *est = e;
   *stop = (e <= tol_abs || hn == G_(0) || j + 1 == cap || !(e == e)) ? 1 : 0;
   *scale = hn2 > 0 ? 1.0 / sqrt(hn2) : 0.0;
-  if (Rc)
-    for (int i = 0; i <= j; ++i) {
-      Rc[2 * i] = double(col[2 * i]);
-      Rc[2 * i + 1] = double(col[2 * i + 1]);
-    }
 }
 
 template <typename T, int R, bool CL>
@@ -616,10 +620,15 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   for (int j = 0; j < cap; ++j) {
     // op: V_j = s * src (own tile nodes), wnext = M_l V_j
     cx<T>* Vj = V + (size_t)j * n;
+    TilePrefetch<T, R> pf;
+    if ((int)bid < ntiles) pf.load(P, src, ((int)bid % tilesx) * TOX, ((int)bid / tilesx) * TOY);
     for (int t = bid; t < ntiles; t += G) {
       const int ox0 = (t % tilesx) * TOX, oy0 = (t / tilesx) * TOY;
       TileView<T, R> tv = make_tile<T, R>(smem, TOX, TOY, ox0, oy0);
-      tile_fill<T, R>(tv, P, ScaledSrc<T>{src, P.nx, T(s)});
+      pf.store(tv, T(s));
+      __syncthreads();
+      if (t + (int)G < ntiles) pf.load(P, src, ((t + G) % tilesx) * TOX, ((t + G) / tilesx) * TOY);
+      tile_finish<T, R>(tv, P);
       if (R == 1) {
         for (int q = threadIdx.x; q < TOX * TOY; q += NT) {
           const int ox = q % TOX, oy = q / TOX;
@@ -662,8 +671,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
         K.scal[3] = hp;
         K.flags[1] = !(hp >= eta2 * wn2);
         if (!K.flags[1])
-          givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT,
-                         bid == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
+          givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
                          K.scal);
       }
     }
@@ -679,11 +687,13 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
       if (threadIdx.x == 0) {
         const double hp = K.h[2 * nv] - double(hs);
-        givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT,
-                       bid == 0 ? Rg + 2 * (size_t)j * (cap + 1) : nullptr, tol_abs, K.scal + 2, K.flags,
-                       K.scal);
+        givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags, K.scal);
       }
       __syncthreads();
+    }
+    if (bid == 0) {  // CTA 0 keeps the rotated column j (FP64) for the final triangular solve
+      double* Rc = Rg + 2 * (size_t)j * (cap + 1);
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) Rc[i] = double(colT[i]);
     }
     if (!K.flags[0]) {  // w' = w - V h (with the last pass's coefficients); the next op needs it complete
       vec_units += nv + 2;
