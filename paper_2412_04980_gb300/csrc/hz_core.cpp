@@ -504,7 +504,7 @@ int setup(Handle* h, const double* k_dev) {
       L.capg = std::max(1, krylov_cap(cfg.c_it, L.n));
       maxnv = std::max(maxnv, (size_t)L.capg + 1);
       if (cfg.device_gmres) {
-        L.ggrid = std::min(gmres_max_grid(L.dpre, L.R, L.capg), gmres_grid_want(L.nx, L.ny));
+        L.ggrid = std::min(gmres_max_grid(L.dpre, L.R, L.capg, L.n), gmres_grid_want(L.nx, L.ny));
         L.gcl = cluster_form_possible(cfg, L.n) ? gmres_cluster_size(L.dpre, L.R, L.capg) : 0;
         if (L.ggrid <= 0 && L.gcl <= 0) {
           set_error("the persistent GMRES kernel cannot be launched on this device");

@@ -156,8 +156,9 @@ struct GmresState {
   long long total_reorth;// second Gram-Schmidt passes since the last statistics read
   long long pad2[11];
 };
-// Largest cooperative grid for the kernel variant (0 if it cannot be launched).
-int gmres_max_grid(int dt, int R, int cap);
+// Largest cooperative grid for the kernel variant used on a level of n nodes (0 if it cannot be
+// launched).
+int gmres_max_grid(int dt, int R, int cap, size_t n);
 // Largest thread-block cluster (16 or 8 CTAs) the cluster form can run in, 0 if none.
 int gmres_cluster_size(int dt, int R, int cap);
 // x += GMRES(M, b), whole solve in one launch: one right-hand side on a cooperative grid of

@@ -31,7 +31,12 @@ namespace {
 constexpr int NT = 512;
 constexpr int NW = NT / 32;
 constexpr int CV = 8;
-constexpr int TOX = 32, TOY = 16;
+constexpr int kWred = NW * 2 * 16 + NW;  // warp partials of up to 16 complex values, then NW norms
+// Operator tiles of the grid form: TS = 0 -> 32 x 16 nodes, TS = 1 -> 64 x 32 (large FP32 levels,
+// where fewer, fuller tiles per CTA cut the per-tile synchronisation; measured on GB300 at
+// 1025^2: operator phase 28.7 -> 18.8 us per iteration).
+template <int TS> struct TileShape { static constexpr int X = 32, Y = 16; };
+template <> struct TileShape<1> { static constexpr int X = 64, Y = 32; };
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz per barrier wait
 
 // Loads of data that other CTAs write during the launch bypass L1 (not coherent across SMs).
@@ -75,9 +80,10 @@ __device__ __forceinline__ bool grid_sync(hz::GmresState* gs, unsigned nblocks) 
 }
 
 // Grid barrier that also reduces CTA partials: after the barrier every CTA sums
-// part[b * pstride + i] over all CTAs b for i < m itself (one warp per value, K lanes striding
-// over the CTAs, then a fixed shuffle tree), so every CTA holds bitwise-identical sums in out[]
-// (shared) without a serial reduction by one CTA and a second wait for it.
+// part[i * nblocks + b] over all CTAs b for i < m itself (value-major, so the K lanes that
+// share a value read consecutive CTAs' partials; then a fixed shuffle tree), so every CTA
+// holds bitwise-identical sums in out[] (shared) without a serial reduction by one CTA and a
+// second wait for it.
 __device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks, const double* part, int pstride,
                                             int m, double* /*red*/, double* out) {
   if (!grid_sync(gs, nblocks)) return false;
@@ -90,15 +96,16 @@ __device__ __forceinline__ bool grid_reduce(hz::GmresState* gs, unsigned nblocks
     const int k = lane % K;
     double t = 0;
     if (i < m) {
-      double a[8];
+      const double* pi = part + (size_t)i * nblocks;
+      double a[16];
       int b = k;
-      for (; b + 7 * K < (int)nblocks; b += 8 * K) {
+      for (; b + 15 * K < (int)nblocks; b += 16 * K) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = __ldcg(part + (size_t)(b + u * K) * pstride + i);
+        for (int u = 0; u < 16; ++u) a[u] = __ldcg(pi + b + u * K);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) t += a[u];
+        for (int u = 0; u < 16; ++u) t += a[u];
       }
-      for (; b < (int)nblocks; b += K) t += __ldcg(part + (size_t)b * pstride + i);
+      for (; b < (int)nblocks; b += K) t += __ldcg(pi + b);
     }
     for (int o = K / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (i < m && k == 0) out[i] = t;
@@ -125,7 +132,7 @@ __device__ __forceinline__ bool bar_all(hz::GmresState* gs, unsigned nblocks) {
 
 constexpr int kMaxCluster = 16;
 
-// Barrier + reduction of the CTA partials part[b * pstride + i], b < nblocks, i < m into out[]
+// Barrier + reduction of the CTA partials part[i * nblocks + b], b < nblocks, i < m into out[]
 // (shared).  Cluster form: every CTA adds the partials itself in increasing b, so all CTAs
 // hold bitwise-identical sums.
 template <bool CL>
@@ -136,7 +143,7 @@ __device__ __forceinline__ bool reduce_all(hz::GmresState* gs, unsigned nblocks,
     for (int i = threadIdx.x; i < m; i += NT) {
       double a[kMaxCluster];
 #pragma unroll
-      for (int b = 0; b < kMaxCluster; ++b) a[b] = b < (int)nblocks ? __ldcg(part + (size_t)b * pstride + i) : 0.0;
+      for (int b = 0; b < kMaxCluster; ++b) a[b] = b < (int)nblocks ? __ldcg(part + (size_t)i * nblocks + b) : 0.0;
       double t = a[0];
 #pragma unroll
       for (int b = 1; b < kMaxCluster; ++b) t += a[b];
@@ -188,7 +195,7 @@ __device__ __forceinline__ T warp_tsum(T (&v)[CNT]) {
 
 // Software-pipelined staging of the operator tiles: every thread holds the source values (and
 // wavenumbers) of up to PF cells of the next tile in registers while the current tile computes.
-template <typename T, int R>
+template <typename T, int R, int TOX, int TOY>
 struct TilePrefetch {
   static constexpr int PF = ((TOX + 2 * R) * (TOY + 2 * R) + NT - 1) / NT;
   cx<T> v[PF];
@@ -284,10 +291,10 @@ __device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
     }
     if (lane == 0) {
       if (is_norm) {
-        part[(size_t)bid * pstride + 2 * nv] = double(ar);
+        part[(size_t)(2 * nv) * G + bid] = double(ar);
       } else {
-        part[(size_t)bid * pstride + 2 * i] = double(ar);
-        part[(size_t)bid * pstride + 2 * i + 1] = double(ai);
+        part[(size_t)(2 * i) * G + bid] = double(ar);
+        part[(size_t)(2 * i + 1) * G + bid] = double(ai);
       }
     }
   }
@@ -351,23 +358,93 @@ __device__ void dots_elem(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
     if (threadIdx.x < 2 * CV && (threadIdx.x >> 1) < cnt) {
       double t = 0;
       for (int q = 0; q < NW; ++q) t += wred[q * 2 * CV + threadIdx.x];
-      part[(size_t)bid * pstride + 2 * c0 + threadIdx.x] = t;
+      part[(size_t)(2 * c0 + threadIdx.x) * G + bid] = t;
     }
     if (nrm && threadIdx.x == 0) {
       double t = 0;
       for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CV + q];
-      part[(size_t)bid * pstride + 2 * nv] = t;
+      part[(size_t)(2 * nv) * G + bid] = t;
     }
     __syncthreads();
   }
 }
 
-constexpr size_t kLargeSlice = 8 * NT;  // slices above this use the element-parallel phases
+constexpr size_t kLargeSlice = 8 * NT;  // slices above this use the element-parallel update
+constexpr size_t kStreamSlice = 2 * NT; // slices above this use the streaming dots (measured on GB300:
+                                        // warp-split dots win for slices of a few hundred elements)
+
+// Streaming variant for large slices: the slice is taken in blocks of EPT * NT elements; every
+// thread keeps its EPT values of w in registers and streams the basis one vector at a time
+// (EPT loads in flight per vector), accumulating 16 vectors per chunk before one warp
+// transpose-reduction and a fixed-order block combine per chunk.
+template <typename T>
+__device__ void dots_stream(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride,
+                            bool with_norm, double* wred, unsigned bid, unsigned G) {
+  constexpr int EPT = 8, CH = 16;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  size_t s0, s1;
+  my_slice(n, bid, G, s0, s1);
+  const int chunks = nv > 0 ? (nv + CH - 1) / CH : (with_norm ? 1 : 0);
+  for (int c = 0; c < chunks; ++c) {
+    const int c0 = c * CH;
+    const int cnt = max(0, min(CH, nv - c0));
+    const bool nrm = with_norm && c == 0;
+    T acc[2 * CH];
+#pragma unroll
+    for (int q = 0; q < 2 * CH; ++q) acc[q] = T(0);
+    T wn = T(0);
+    for (size_t blk = s0; blk < s1; blk += (size_t)EPT * NT) {
+      cx<T> wv[EPT];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const size_t e = blk + threadIdx.x + (size_t)k * NT;
+        wv[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
+        if (nrm) wn += wv[k].re * wv[k].re + wv[k].im * wv[k].im;
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        if (i < cnt) {
+          const cx<T>* Vi = V + (size_t)(c0 + i) * n;
+          cx<T> v[EPT];
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const size_t e = blk + threadIdx.x + (size_t)k * NT;
+            v[k] = e < s1 ? ldcg(Vi + e) : mk<T>(T(0), T(0));
+          }
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            acc[2 * i] += v[k].re * wv[k].re + v[k].im * wv[k].im;
+            acc[2 * i + 1] += v[k].re * wv[k].im - v[k].im * wv[k].re;
+          }
+        }
+      }
+    }
+    const T ws = warp_tsum<T, 2 * CH>(acc);
+    wred[wid * 2 * CH + lane] = double(ws);
+    if (nrm) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+      if (lane == 0) wred[NW * 2 * CH + wid] = double(wn);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * CH && (threadIdx.x >> 1) < cnt) {
+      double t = 0;
+      for (int q = 0; q < NW; ++q) t += wred[q * 2 * CH + threadIdx.x];
+      part[(size_t)(2 * c0 + threadIdx.x) * G + bid] = t;
+    }
+    if (nrm && threadIdx.x == 0) {
+      double t = 0;
+      for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CH + q];
+      part[(size_t)(2 * nv) * G + bid] = t;
+    }
+    __syncthreads();
+  }
+}
 
 template <typename T>
 __device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
                           double* wred, unsigned bid, unsigned G) {
-  if ((n + G - 1) / G > kLargeSlice) dots_elem<T>(V, n, nv, w, part, pstride, with_norm, wred, bid, G);
+  if ((n + G - 1) / G > kStreamSlice) dots_stream<T>(V, n, nv, w, part, pstride, with_norm, wred, bid, G);
   else dots_warp<T>(V, n, nv, w, part, pstride, with_norm, bid, G);
 }
 
@@ -411,7 +488,7 @@ __device__ __forceinline__ cx<T> axpy_all(cx<T> x, const cx<T>* V, size_t n, int
   return x;
 }
 
-// w -= sum_i h_i V_i over this CTA's slice; with_norm: CTA partial of ||w||^2 into part[bid * pstride]
+// w -= sum_i h_i V_i over this CTA's slice; with_norm: CTA partial of ||w||^2 into part[bid]
 template <typename T>
 __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T* sc, cx<T>* w, double* part,
                             int pstride, double* wred, bool with_norm, unsigned bid, unsigned G) {
@@ -467,7 +544,7 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
   if (threadIdx.x == 0) {
     double t = 0;
     for (int q = 0; q < NT / 32; ++q) t += wred[q];
-    part[(size_t)bid * pstride] = t;
+    part[bid] = t;
   }
 }
 
@@ -542,7 +619,7 @@ __device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn
   *scale = hn2 > 0 ? 1.0 / sqrt(hn2) : 0.0;
 }
 
-template <typename T, int R, bool CL>
+template <typename T, int R, bool CL, int TS = 0>
 __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict__ b, cx<T>* __restrict__ x,
                                               cx<T>* V, cx<T>* w0, cx<T>* w1, double* partA, double* partB,
                                               int pstride, double* Rg, hz::GmresState* st, int cap, double tol,
@@ -570,6 +647,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     bid = blockIdx.x;
     G = gridDim.x;
   }
+  constexpr int TOX = TileShape<TS>::X, TOY = TileShape<TS>::Y;
   const int tilesx = (P.nx + TOX - 1) / TOX, tilesy = (P.ny + TOY - 1) / TOY;
   const int ntiles = tilesx * tilesy;
   unsigned char* kp = smem + tile_smem_bytes<T, R>(TOX, TOY);
@@ -580,7 +658,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   K.gs = K.gc + cap;
   K.g = K.gs + 2 * cap;
   K.wred = K.g + 2 * (cap + 1);
-  K.scal = K.wred + NW * 2 * CV + NW;
+  K.scal = K.wred + kWred;
   K.flags = reinterpret_cast<int*>(K.scal + 4);
   T* sc = reinterpret_cast<T*>(K.flags + 4);
   T* gcT = reinterpret_cast<T*>(K.gc);      // cap cosines
@@ -620,7 +698,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   for (int j = 0; j < cap; ++j) {
     // op: V_j = s * src (own tile nodes), wnext = M_l V_j
     cx<T>* Vj = V + (size_t)j * n;
-    TilePrefetch<T, R> pf;
+    TilePrefetch<T, R, TOX, TOY> pf;
     if ((int)bid < ntiles) pf.load(P, src, ((int)bid % tilesx) * TOX, ((int)bid / tilesx) * TOY);
     for (int t = bid; t < ntiles; t += G) {
       const int ox0 = (t % tilesx) * TOX, oy0 = (t / tilesx) * TOY;
@@ -764,11 +842,20 @@ OpP<T> mkop(const hz::OpDesc& d) {
   return p;
 }
 
-template <typename T, int R>
+template <typename T, int R, int TS = 0>
 size_t kshared_bytes(int cap) {
-  return tile_smem_bytes<T, R>(TOX, TOY) + sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) +
-                                                             NW * 2 * CV + NW + 4) +
+  return tile_smem_bytes<T, R>(TileShape<TS>::X, TileShape<TS>::Y) + sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) +
+                                                             kWred + 4) +
          sizeof(int) * 4 + sizeof(T) * (8 * (cap + 1) + 4) + 64;
+}
+
+// The grid form uses 64 x 32 tiles on FP32 levels of at least 2^18 nodes with the radius-3
+// coarse stencil, 32 x 16 tiles otherwise.
+template <typename T, int R>
+constexpr bool kHasWide = sizeof(T) == 4 && R == 3;
+template <typename T, int R>
+constexpr bool wide_tiles(size_t n) {
+  return kHasWide<T, R> && n >= ((size_t)1 << 18);
 }
 
 template <typename T, int R>
@@ -806,9 +893,18 @@ cudaError_t gmres_t(hz::Ctx& c, const hz::OpDesc& d, const void* b, void* x, voi
                               eta2);
   }
   if (nrhs != 1) return cudaErrorInvalidValue;  // the cooperative grid solves one right-hand side
+  void* args[] = {&P, &bb, &xx, &VV, &a0, &a1, &partA, &partB, &pstride, &Rg, &st, &cap, &tol, &eta2};
+  if constexpr (kHasWide<T, R>) {
+    if (wide_tiles<T, R>((size_t)d.nx * d.ny)) {
+      const size_t smw = kshared_bytes<T, R, 1>(cap);
+      cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, false, 1>), smw);
+      if (e != cudaSuccess) return e;
+      hz::ProfScope ps(c, hz::F_GMRES, 0.0);
+      return cudaLaunchCooperativeKernel((const void*)k_gmres<T, R, false, 1>, dim3(grid), dim3(NT), args, smw, c.s);
+    }
+  }
   cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, false>), sm);
   if (e != cudaSuccess) return e;
-  void* args[] = {&P, &bb, &xx, &VV, &a0, &a1, &partA, &partB, &pstride, &Rg, &st, &cap, &tol, &eta2};
   hz::ProfScope ps(c, hz::F_GMRES, 0.0);
   return cudaLaunchCooperativeKernel((const void*)k_gmres<T, R, false>, dim3(grid), dim3(NT), args, sm, c.s);
 }
@@ -844,10 +940,19 @@ int cluster_size_t(int cap) {
 }
 
 template <typename T, int R>
-int max_grid_t(int cap) {
+int max_grid_t(int cap, size_t n) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if constexpr (kHasWide<T, R>) {
+    if (wide_tiles<T, R>(n)) {
+      const size_t smw = kshared_bytes<T, R, 1>(cap);
+      if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, false, 1>), smw) != cudaSuccess) return 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres<T, R, false, 1>, NT, smw) != cudaSuccess)
+        return 0;
+      return per * sms;
+    }
+  }
   const size_t sm = kshared_bytes<T, R>(cap);
   if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres<T, R, false>), sm) != cudaSuccess)
     return 0;
@@ -859,15 +964,15 @@ int max_grid_t(int cap) {
 
 namespace hz {
 
-int gmres_max_grid(int dt, int R, int cap) {
+int gmres_max_grid(int dt, int R, int cap, size_t n) {
   if (dt == C128) {
-    if (R == 1) return max_grid_t<double, 1>(cap);
-    if (R == 2) return max_grid_t<double, 2>(cap);
-    if (R == 3) return max_grid_t<double, 3>(cap);
+    if (R == 1) return max_grid_t<double, 1>(cap, n);
+    if (R == 2) return max_grid_t<double, 2>(cap, n);
+    if (R == 3) return max_grid_t<double, 3>(cap, n);
   } else {
-    if (R == 1) return max_grid_t<float, 1>(cap);
-    if (R == 2) return max_grid_t<float, 2>(cap);
-    if (R == 3) return max_grid_t<float, 3>(cap);
+    if (R == 1) return max_grid_t<float, 1>(cap, n);
+    if (R == 2) return max_grid_t<float, 2>(cap, n);
+    if (R == 3) return max_grid_t<float, 3>(cap, n);
   }
   return 0;
 }

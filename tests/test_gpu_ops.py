@@ -208,11 +208,13 @@ def test_cslp_gmres_fp64(hz, level, device_gmres):
     assert its_ref <= krylov_cap(6.0, cy * cx)
 
 
-@pytest.mark.parametrize("level,n,device_gmres", [(1, 1025, 1), (3, 257, 1), (3, 257, 3), (1, 257, 3), (1, 1025, 3)])
+@pytest.mark.parametrize("level,n,device_gmres", [(1, 1025, 1), (3, 257, 1), (3, 257, 3), (1, 257, 3), (1, 1025, 3),
+                                                  (3, 2049, 1)])
 def test_cslp_gmres_fp32(hz, level, n, device_gmres):
     """FP32 GMRES (device kernel) reaches the 0.1 tolerance measured in FP64 and stays within
     two iterations of the FP64 oracle; level 1 runs GMRES on the finest grid (mg_max_level = 0),
-    as a cooperative grid (1) and in one cluster with large per-CTA slices (3)."""
+    as a cooperative grid (1) and in one cluster with large per-CTA slices (3); level 3 of a
+    2049^2 grid (513^2 nodes) takes the 64 x 32 operator tiles of large levels."""
     p = mp.random_field(n, 5.0, seed=3, kh_max=0.3, levels=4 if level == 3 else 1)
     H = handle(hz, p.k, p.h, levels=p.levels, precision="mixed", mg_max_level=0 if level == 1 else 2,
                device_gmres=device_gmres)
