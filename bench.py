@@ -528,7 +528,8 @@ def main():
 
     counts = {"outer": stats[-1]["outer_iterations"], "level_iterations": stats[-1]["level_iterations"],
               "level_calls": stats[-1]["level_calls"],
-              "cslp_gmres_iterations": stats[-1]["cslp_gmres_iterations"]}
+              "cslp_gmres_iterations": stats[-1]["cslp_gmres_iterations"],
+              "cslp_gmres_reorth": stats[-1]["cslp_gmres_reorth"]}
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:

@@ -116,6 +116,8 @@ typedef struct {
   double true_relres;                          /* ||b - A_h u|| / ||b|| in FP64 */
   double est_relres;                           /* last Arnoldi least-squares estimate */
   double ms;                                   /* wall time of the solve in milliseconds */
+  int cslp_gmres_reorth[HZ_MAX_LEVELS];        /* [l-1]: second Gram-Schmidt passes of the
+                                                  persistent CSLP GMRES on level l */
 } hz_stats;
 
 /* ---- set-up ------------------------------------------------------------------------ */

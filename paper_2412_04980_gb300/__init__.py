@@ -60,6 +60,7 @@ class HzStats(ctypes.Structure):
         ("level_iterations", ctypes.c_int * HZ_MAX_LEVELS), ("level_calls", ctypes.c_int * HZ_MAX_LEVELS),
         ("cslp_gmres_iterations", ctypes.c_int * HZ_MAX_LEVELS), ("true_relres", ctypes.c_double),
         ("est_relres", ctypes.c_double), ("ms", ctypes.c_double),
+        ("cslp_gmres_reorth", ctypes.c_int * HZ_MAX_LEVELS),
     ]
 
     def as_dict(self) -> dict:
@@ -68,6 +69,7 @@ class HzStats(ctypes.Structure):
             "level_iterations": list(self.level_iterations), "level_calls": list(self.level_calls),
             "cslp_gmres_iterations": list(self.cslp_gmres_iterations), "true_relres": self.true_relres,
             "est_relres": self.est_relres, "ms": self.ms,
+            "cslp_gmres_reorth": list(self.cslp_gmres_reorth),
         }
 
 

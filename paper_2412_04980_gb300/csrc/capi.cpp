@@ -193,6 +193,7 @@ static void fill_stats(Handle* H, hz_stats* stats, int nrhs, double ms) {
       s.level_iterations[l] = r.lev_it[l];
       s.level_calls[l] = r.lev_calls[l];
       s.cslp_gmres_iterations[l] = r.cslp_it[l];
+      s.cslp_gmres_reorth[l] = r.cslp_reorth[l];
     }
     s.true_relres = r.true_rel;
     s.est_relres = r.est;

@@ -813,6 +813,7 @@ int collect_gmres_stats(Handle* h, int nb) {
     double bytes = 0;
     for (int q = 0; q < nb; ++q) {
       h->st[q].cslp_it[L.l - 1] += (int)gs[q].total_its;
+      h->st[q].cslp_reorth[L.l - 1] += (int)gs[q].total_reorth;
       bytes += gs[q].total_bytes;
       gs[q].total_its = 0;
       gs[q].total_bytes = 0;

@@ -71,6 +71,7 @@ struct Level {
 struct RhsStats {
   int outer = 0;
   int lev_it[HZ_MAX_LEVELS] = {}, lev_calls[HZ_MAX_LEVELS] = {}, cslp_it[HZ_MAX_LEVELS] = {};
+  int cslp_reorth[HZ_MAX_LEVELS] = {};
   double est = 0, true_rel = 0;
   int status = HZ_OK;
 };

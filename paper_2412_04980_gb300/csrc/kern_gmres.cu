@@ -789,21 +789,43 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     wcur = wnext;
     wnext = tmp;
   }
-  // y = R^-1 g (CTA 0), then x += V y everywhere
+  // y = R^-1 g by warp 0 of CTA 0 (column-oriented back substitution: lane 0 divides, the
+  // warp updates the remaining right-hand side from column i of R), then x += V y everywhere
   double* y = Rg + 2 * (size_t)cap * (cap + 1);
-  if (bid == 0 && threadIdx.x == 0) {  // Rg and y are written and read by this thread only
-    for (int i = jstop - 1; i >= 0; --i) {
-      double sr = double(gT[2 * i]), si = double(gT[2 * i + 1]);
-      for (int q = i + 1; q < jstop; ++q) {
-        const double rr = Rg[2 * ((size_t)q * (cap + 1) + i)], ri = Rg[2 * ((size_t)q * (cap + 1) + i) + 1];
-        sr -= rr * y[2 * q] - ri * y[2 * q + 1];
-        si -= rr * y[2 * q + 1] + ri * y[2 * q];
-      }
+  if (bid == 0 && threadIdx.x < 32) {  // Rg was written by this CTA; y is read after the barrier
+    const int lane = threadIdx.x;
+    double* gw = K.h;     // working right-hand side, FP64
+    double* dinv = K.h1;  // conj(R_ii) / |R_ii|^2, computed in parallel before the serial chain
+    for (int i = lane; i < 2 * jstop; i += 32) gw[i] = double(gT[i]);
+    for (int i = lane; i < jstop; i += 32) {
       const double dr = Rg[2 * ((size_t)i * (cap + 1) + i)], di = Rg[2 * ((size_t)i * (cap + 1) + i) + 1];
       const double d = dr * dr + di * di;
-      y[2 * i] = (sr * dr + si * di) / d;
-      y[2 * i + 1] = (si * dr - sr * di) / d;
+      dinv[2 * i] = dr / d;
+      dinv[2 * i + 1] = -di / d;
     }
+    __syncwarp();
+    for (int i = jstop - 1; i >= 0; --i) {
+      const double* Ri = Rg + 2 * (size_t)i * (cap + 1);  // R_{k,i}, k <= i
+      double yr = 0, yi = 0;
+      if (lane == 0) {
+        const double sr = gw[2 * i], si = gw[2 * i + 1];
+        const double ir = dinv[2 * i], ii = dinv[2 * i + 1];
+        yr = sr * ir - si * ii;
+        yi = sr * ii + si * ir;
+        y[2 * i] = yr;
+        y[2 * i + 1] = yi;
+      }
+      yr = __shfl_sync(0xffffffffu, yr, 0);
+      yi = __shfl_sync(0xffffffffu, yi, 0);
+      for (int k = lane; k < i; k += 32) {
+        const double rr = Ri[2 * k], ri = Ri[2 * k + 1];
+        gw[2 * k] -= rr * yr - ri * yi;
+        gw[2 * k + 1] -= rr * yi + ri * yr;
+      }
+      __syncwarp();
+    }
+  }
+  if (bid == 0 && threadIdx.x == 0) {
     st->its = jstop;
     st->est = est;
     st->total_its += jstop;

@@ -104,3 +104,30 @@ def test_server_rejects_bad_arguments(L):
     assert L.hz_poll(None, 1, None) == hz.HZ_EINVAL
     assert L.hz_wait(None, 1, 0.0, None) == hz.HZ_EINVAL
     assert L.hz_server_destroy(None) == hz.HZ_OK
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets the C compiler gives the
+    header's structs (checked with gcc, no GPU)."""
+    import subprocess
+    import paper_2412_04980_gb300 as hz
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    structs = {"hz_grid": hz.HzGrid, "hz_config": hz.HzConfig, "hz_stats": hz.HzStats, "hz_request": hz.HzRequest,
+               "hz_server_stats": hz.HzServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hz.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
