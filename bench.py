@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--device-gmres", type=int, default=None, choices=[0, 1, 2, 3],
+    ap.add_argument("--device-gmres", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="GMRES CSLP form: 1 cluster/grid by level size, 2 cooperative grid, 3 cluster, "
                          "0 host-driven")
     ap.add_argument("--reorth-eta", type=float, default=None,
@@ -452,6 +452,7 @@ def main():
             torch.distributed.barrier()
 
     mem_gb = H.memory_bytes() / 1e9
+    gmres_forms = {str(l): H.gmres_form(l) for l in range(1, p.levels + 1) if H.gmres_form(l)["form"] != "none"}
     for _ in range(args.warmup):
         _, st = H.solve(b, u, tol=1e-6)
     # which kernel family dominates (one profiled solve, not timed)
@@ -583,6 +584,7 @@ def main():
         "kernel_ms_per_solve": {f: round(v[0], 3) for f, v in fam_ms.items()},
         "kernel_ms_launches_gbs_by_level": lev_ms,
         "counts": counts,
+        "gmres_forms": gmres_forms,
         "cpu_baseline": cpu,
         "clocks": clk,
     }

@@ -99,11 +99,18 @@ typedef struct {
                             on-device Givens rotations: one thread-block cluster per right-hand
                             side, all in one launch, for calls on 4 or more right-hand sides on
                             levels of at most 300,000 nodes; otherwise a cooperative grid per
-                            right-hand side; 2: always the cooperative grid; 3: always clusters;
+                            right-hand side, with one tile per CTA where the level's tiling fits
+                            the GPU (FP32) and slice-distributed vector phases elsewhere;
+                            2: always the cooperative grid (tile-owned where it fits);
+                            3: always clusters; 4: always the slice-distributed grid;
                             0: host-driven Arnoldi steps */
   double reorth_eta;     /* classical Gram-Schmidt runs a second pass when the orthogonalised
                             vector keeps less than reorth_eta of its norm ("twice is enough"
                             test), default 0.1; 1 = always two passes, 0 = one pass */
+  int autotune;          /* 1 (default): with device_gmres = 1, time the tile-owned and the
+                            slice-distributed GMRES forms once per level shape (process-wide
+                            cache, at hz_setup) and keep the faster; 0: take the tile-owned
+                            form wherever it fits */
 } hz_config;
 
 /* Per-right-hand-side solve statistics. */
@@ -170,6 +177,17 @@ int hz_solve_host(hz_handle h, const double* b_host, double* u_host, int nrhs, d
 
 /* Grid size of deflation level l (1-based): *nx, *ny. */
 int hz_level_size(hz_handle h, int level, int* nx, int* ny);
+
+/* How a single right-hand side's CSLP GMRES runs on a level (diagnostics; no counterpart in the
+ * paper): *form = 0 no GMRES on this level (multigrid CSLP) or host-driven Arnoldi steps,
+ * 1 persistent slice-distributed cooperative grid, 2 persistent tile-owned cooperative grid,
+ * 3 one thread-block cluster; *ctas = CTAs of that launch; *cluster = CTAs per cluster used
+ * for calls on several right-hand sides (0 if the cluster form is off).  Errors: HZ_EINVAL. */
+#define HZ_GMRES_NONE    0
+#define HZ_GMRES_SLICE   1
+#define HZ_GMRES_TILE    2
+#define HZ_GMRES_CLUSTER 3
+int hz_level_gmres_form(hz_handle h, int level, int* form, int* ctas, int* cluster);
 
 /* y = A_l x (op = HZ_OP_A) or M_l x (HZ_OP_M) on deflation level l.  Level 1: the
  * 5-point rows of Section 2.1; level >= 2: the re-discretised Galerkin stencils of

@@ -51,6 +51,7 @@ class HzConfig(ctypes.Structure):
         ("mg_max_level", ctypes.c_int), ("mg_omega", ctypes.c_double), ("mg_nu1", ctypes.c_int),
         ("mg_nu2", ctypes.c_int), ("mg_coarsest_side", ctypes.c_int), ("max_rhs", ctypes.c_int),
         ("timeout_s", ctypes.c_double), ("device_gmres", ctypes.c_int), ("reorth_eta", ctypes.c_double),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -108,6 +109,7 @@ _SIGS = {
     "hz_solve": (_I, [_P, _P, _P, _I, _D, _U, ctypes.POINTER(HzStats)]),
     "hz_solve_host": (_I, [_P, _P, _P, _I, _D, _U, ctypes.POINTER(HzStats)]),
     "hz_level_size": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "hz_level_gmres_form": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "hz_level_apply": (_I, [_P, _I, _I, _I, _P, _P, _I]),
     "hz_level_jacobi": (_I, [_P, _I, _I, _P, _P, _P, _I]),
     "hz_defl_restrict": (_I, [_P, _I, _I, _P, _P, _I]),
@@ -239,6 +241,13 @@ class Helmholtz:
         nx, ny = ctypes.c_int(), ctypes.c_int()
         _check(lib().hz_level_size(self._h, level, ctypes.byref(nx), ctypes.byref(ny)), "hz_level_size")
         return ny.value, nx.value
+
+    def gmres_form(self, level: int) -> dict:
+        """hz_level_gmres_form: {'form': 'none'|'slice'|'tile'|'cluster', 'ctas': int, 'cluster': int}."""
+        f, c, cl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().hz_level_gmres_form(self._h, level, ctypes.byref(f), ctypes.byref(c), ctypes.byref(cl)),
+               "hz_level_gmres_form")
+        return {"form": ("none", "slice", "tile", "cluster")[f.value], "ctas": c.value, "cluster": cl.value}
 
     def mg_size(self, level: int, mg_level: int):
         nx, ny = ctypes.c_int(), ctypes.c_int()

@@ -64,6 +64,7 @@ int hz_config_init(hz_config* c) {
   c->timeout_s = 600.0;
   c->device_gmres = 1;
   c->reorth_eta = 0.1;
+  c->autotune = 1;
   return HZ_OK;
 }
 
@@ -83,7 +84,8 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (c.mg_max_level < 0 || c.mg_coarsest_side < 3) return bad("invalid multigrid level settings");
   if (!(c.timeout_s > 0)) return bad("timeout_s must be positive");
   if (!(c.reorth_eta >= 0 && c.reorth_eta <= 1)) return bad("reorth_eta must be in [0, 1]");
-  if (c.device_gmres < 0 || c.device_gmres > 3) return bad("device_gmres must be 0, 1, 2 or 3");
+  if (c.autotune != 0 && c.autotune != 1) return bad("autotune must be 0 or 1");
+  if (c.device_gmres < 0 || c.device_gmres > 4) return bad("device_gmres must be 0, 1, 2, 3 or 4");
   if (g.bc == HZ_BC_DIRICHLET && c.levels != 1) return bad("Dirichlet grids support the level-1 operator only");
   int nx = g.nx, ny = g.ny;
   for (int l = 1; l < c.levels; ++l) {
@@ -245,6 +247,19 @@ int hz_level_size(hz_handle hp, int level, int* nx, int* ny) {
   if (int s = check_level(H_, level)) return s;
   if (nx) *nx = H_->lv[level - 1].nx;
   if (ny) *ny = H_->lv[level - 1].ny;
+  return HZ_OK;
+}
+
+int hz_level_gmres_form(hz_handle hp, int level, int* form, int* ctas, int* cluster) {
+  GUARD_HANDLE(hp);
+  if (int s = check_level(H_, level)) return s;
+  const Level& L = H_->lv[level - 1];
+  int f = L.gtiles > 0 ? HZ_GMRES_TILE : (L.ggrid > 0 ? HZ_GMRES_SLICE : HZ_GMRES_NONE);
+  if (H_->cfg.device_gmres == 3 && L.gcl > 0) f = HZ_GMRES_CLUSTER;
+  if (form) *form = f;
+  if (ctas)
+    *ctas = f == HZ_GMRES_TILE ? L.gtiles : (f == HZ_GMRES_SLICE ? L.ggrid : (f == HZ_GMRES_CLUSTER ? L.gcl : 0));
+  if (cluster) *cluster = L.gcl;
   return HZ_OK;
 }
 

@@ -13,7 +13,9 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -506,6 +508,10 @@ int setup(Handle* h, const double* k_dev) {
       if (cfg.device_gmres) {
         L.ggrid = std::min(gmres_max_grid(L.dpre, L.R, L.capg, L.n), gmres_grid_want(L.nx, L.ny));
         L.gcl = cluster_form_possible(cfg, L.n) ? gmres_cluster_size(L.dpre, L.R, L.capg) : 0;
+        // one right-hand side at a time on levels whose tiling fits the grid: tile-owned form
+        // (FP32 vectors; the FP64 variant is register-bound)
+        if ((cfg.device_gmres == 1 || cfg.device_gmres == 2) && L.dpre == C64)
+          L.gtiles = gmres_tile_form(L.dpre, L.R, L.nx, L.ny, L.capg, &L.gtx, &L.gty);
         if (L.ggrid <= 0 && L.gcl <= 0) {
           set_error("the persistent GMRES kernel cannot be launched on this device");
           return HZ_ENOTSUP;
@@ -523,7 +529,7 @@ int setup(Handle* h, const double* k_dev) {
         void* p;
         CS(dalloc(h, &L.wg2, gq * L.n * ep));
         L.gpstride = 2 * (L.capg + 1) + 2;
-        const size_t nparts = std::max<size_t>(L.ggrid, gq * L.gcl);
+        const size_t nparts = std::max<size_t>(std::max<size_t>(L.ggrid, L.gtiles), gq * L.gcl);
         CS(dalloc(h, &p, sizeof(double) * nparts * L.gpstride));
         L.gpartA = (double*)p;
         CS(dalloc(h, &p, sizeof(double) * nparts * L.gpstride));
@@ -543,6 +549,93 @@ int setup(Handle* h, const double* k_dev) {
   CS(dalloc(h, &h->rres, (size_t)nb * h->lv[0].n * 16));
   h->st.assign(nb, RhsStats());
   CK(cudaStreamSynchronize(h->ctx.s));
+  if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_gmres(h));
+  return HZ_OK;
+}
+
+// ------------------------------------------------------------------------------ autotuning
+// Per level shape (nx, ny, precision, stencil radius, iteration cap) the faster of the
+// tile-owned and the slice-distributed GMRES forms, measured once per process: both run
+// min(cap, 24) iterations (tolerance 0) on a fixed pseudo-random right-hand side, twice, and the
+// second run's event time decides.  The workspace of the level is reused; statistics are reset.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, bool> g_tune;  // -> tile-owned form wins
+}  // namespace
+
+int autotune_gmres(Handle* h) {
+  for (auto& L : h->lv) {
+    if (L.gtiles <= 0 || L.ggrid <= 0) continue;
+    const auto key = std::make_tuple(L.nx, L.ny, L.dpre, L.R, L.capg);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        if (!it->second) L.gtiles = 0;
+        continue;
+      }
+    }
+    const size_t eb = elem_bytes(L.dpre);
+    std::vector<float> hb(2 * L.n);
+    uint32_t r = 12345u;
+    for (auto& v : hb) {  // xorshift32, values in [-1, 1)
+      r ^= r << 13;
+      r ^= r >> 17;
+      r ^= r << 5;
+      v = (float)((double)r / 2147483648.0 - 1.0);
+    }
+    if (eb == 16) {
+      std::vector<double> hd(hb.begin(), hb.end());
+      CK(cudaMemcpyAsync(L.t, hd.data(), L.n * eb, cudaMemcpyHostToDevice, h->ctx.s));
+      CK(cudaStreamSynchronize(h->ctx.s));
+    } else {
+      CK(cudaMemcpyAsync(L.t, hb.data(), L.n * eb, cudaMemcpyHostToDevice, h->ctx.s));
+      CK(cudaStreamSynchronize(h->ctx.s));
+    }
+    OpDesc M = L.opM(L.dpre, h->cfg.beta1, h->cfg.beta2);
+    const int K = std::min(L.capg, 24);
+    const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms[2] = {0, 0};
+    int st = HZ_OK;
+    for (int form = 0; form < 2 && st == HZ_OK; ++form) {
+      for (int rep = 0; rep < 2 && st == HZ_OK; ++rep) {
+        st = status_of(cudaMemsetAsync(L.rt, 0, L.n * eb, h->ctx.s), "autotune");
+        if (st) break;
+        st = status_of(cudaEventRecord(e0, h->ctx.s), "autotune");
+        if (st) break;
+        cudaError_t e = form == 0 ? launch_gmres_tile(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.gpartA, L.gpartB,
+                                                      L.gR, L.gst, K, 0.0, L.gtx, L.gty, eta2)
+                                  : launch_gmres_persistent(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.wg2, L.gpartA,
+                                                            L.gpartB, L.gpstride, L.gR, L.gst, K, 0.0, L.ggrid, false,
+                                                            1, eta2);
+        st = status_of(e, "autotune launch");
+        if (st) break;
+        st = status_of(cudaEventRecord(e1, h->ctx.s), "autotune");
+        if (st) break;
+        st = wait_event(h, e1);
+        if (st) break;
+        st = status_of(cudaEventElapsedTime(&ms[form], e0, e1), "autotune");
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    GmresState gs;
+    CK(cudaMemcpy(&gs, L.gst, sizeof(gs), cudaMemcpyDeviceToHost));
+    CK(cudaMemsetAsync(L.gst, 0, sizeof(GmresState) * h->nbmax, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    if (gs.err) {
+      set_error("a grid barrier of the persistent GMRES kernel exceeded its wait budget");
+      return HZ_ETIMEOUT;
+    }
+    const bool tile_wins = ms[0] <= ms[1];
+    if (!tile_wins) L.gtiles = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = tile_wins;
+  }
   return HZ_OK;
 }
 
@@ -849,6 +942,11 @@ int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
     if (use_cluster) {  // one launch, one thread-block cluster per right-hand side
       CK(launch_gmres_persistent(h->ctx, M, dt, b, x, L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride, L.gR, L.gst,
                                  L.capg, h->cfg.cslp_tol, L.gcl, true, nb, eta2));
+    } else if (L.gtiles > 0) {  // tile-owned form, one cooperative launch per right-hand side
+      for (int q = 0; q < nb; ++q)
+        CK(launch_gmres_tile(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb, (char*)x + (size_t)q * L.n * eb,
+                             L.Vg, L.wg, L.gpartA, L.gpartB, L.gR, L.gst + q, L.capg, h->cfg.cslp_tol, L.gtx, L.gty,
+                             eta2));
     } else {  // one cooperative launch per right-hand side
       for (int q = 0; q < nb; ++q)
         CK(launch_gmres_persistent(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb,

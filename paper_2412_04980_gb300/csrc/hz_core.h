@@ -64,6 +64,7 @@ struct Level {
   GmresState* gst = nullptr;                 // nbmax control blocks
   int ggrid = 0;                             // CTAs of the cooperative-grid form (0: host-driven GMRES)
   int gcl = 0;                               // CTAs per cluster of the cluster form (0: not used)
+  int gtiles = 0, gtx = 0, gty = 0;          // tile-owned form: CTAs (= tiles) and tile shape (0: not used)
   OpDesc opA(int dt) const;
   OpDesc opM(int dt, double b1, double b2) const;
 };
@@ -97,6 +98,8 @@ int dalloc(Handle* h, void** p, size_t bytes);
 int status_of(cudaError_t e, const char* where);
 
 int setup(Handle* h, const double* k_dev);
+// Keep the faster persistent GMRES form per level (tile-owned or slice-distributed).
+int autotune_gmres(Handle* h);
 int gmres_grid_want(int nx, int ny);
 size_t estimate_bytes(const hz_grid& g, const hz_config& cfg);
 void destroy(Handle* h);

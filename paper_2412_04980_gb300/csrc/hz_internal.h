@@ -159,6 +159,14 @@ struct GmresState {
 // Largest cooperative grid for the kernel variant used on a level of n nodes (0 if it cannot be
 // launched).
 int gmres_max_grid(int dt, int R, int cap, size_t n);
+// Tile-owned form of the persistent GMRES: tile shape (*TX, *TY) for an nx x ny level and the
+// number of CTAs (one per tile), 0 if no shape gives every co-resident CTA at most one tile.
+int gmres_tile_form(int dt, int R, int nx, int ny, int cap, int* TX, int* TY);
+// x += GMRES(M, b) for one right-hand side with the tile-owned form (grid = tiles; w0: n
+// elements; partA/partB: 2 (cap + 1) + 2 values per CTA; Rg, st as launch_gmres_persistent).
+cudaError_t launch_gmres_tile(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
+                              double* partA, double* partB, double* Rg, GmresState* st, int cap, double tol, int TX,
+                              int TY, double eta2);
 // Largest thread-block cluster (16 or 8 CTAs) the cluster form can run in, 0 if none.
 int gmres_cluster_size(int dt, int R, int cap);
 // x += GMRES(M, b), whole solve in one launch: one right-hand side on a cooperative grid of

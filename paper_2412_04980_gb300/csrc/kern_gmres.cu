@@ -30,7 +30,6 @@ namespace {
 
 constexpr int NT = 512;
 constexpr int NW = NT / 32;
-constexpr int CV = 8;
 constexpr int kWred = NW * 2 * 16 + NW;  // warp partials of up to 16 complex values, then NW norms
 // Operator tiles of the grid form: TS = 0 -> 32 x 16 nodes, TS = 1 -> 64 x 32 (large FP32 levels,
 // where fewer, fuller tiles per CTA cut the per-tile synchronisation; measured on GB300 at
@@ -297,75 +296,6 @@ __device__ void dots_warp(const cx<T>* V, size_t n, int nv, const cx<T>* w, doub
         part[(size_t)(2 * i + 1) * G + bid] = double(ai);
       }
     }
-  }
-}
-
-// Element-parallel variant for large slices: every thread takes 4 elements of the slice and
-// accumulates 8 vectors per pass; a warp transpose-reduction and one block combine per pass.
-template <typename T>
-__device__ void dots_elem(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
-                          double* wred, unsigned bid, unsigned G) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  size_t s0, s1;
-  my_slice(n, bid, G, s0, s1);
-  const int passes = nv > 0 ? nv : (with_norm ? 1 : 0);
-  for (int c0 = 0; c0 < passes; c0 += CV) {
-    const int cnt = max(0, min(CV, nv - c0));
-    T ar[CV], ai[CV];
-    T wn = T(0);
-#pragma unroll
-    for (int i = 0; i < CV; ++i) ar[i] = ai[i] = T(0);
-    const bool nrm = with_norm && c0 == 0;
-    for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += 4 * NT) {
-      cx<T> we[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const size_t e = e0 + k * NT;
-        we[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
-        if (nrm) wn += we[k].re * we[k].re + we[k].im * we[k].im;
-      }
-#pragma unroll
-      for (int i = 0; i < CV; ++i)
-        if (i < cnt) {
-          const cx<T>* Vi = V + (size_t)(c0 + i) * n;
-          cx<T> v[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const size_t e = e0 + k * NT;
-            v[k] = e < s1 ? ldcg(Vi + e) : mk<T>(T(0), T(0));
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            ar[i] += v[k].re * we[k].re + v[k].im * we[k].im;
-            ai[i] += v[k].re * we[k].im - v[k].im * we[k].re;
-          }
-        }
-    }
-    T vals[2 * CV];
-#pragma unroll
-    for (int i = 0; i < CV; ++i) {
-      vals[2 * i] = ar[i];
-      vals[2 * i + 1] = ai[i];
-    }
-    const T ws = warp_tsum<T, 2 * CV>(vals);
-    if (lane < 2 * CV) wred[wid * 2 * CV + lane] = double(ws);
-    if (nrm) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
-      if (lane == 0) wred[NW * 2 * CV + wid] = double(wn);
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * CV && (threadIdx.x >> 1) < cnt) {
-      double t = 0;
-      for (int q = 0; q < NW; ++q) t += wred[q * 2 * CV + threadIdx.x];
-      part[(size_t)(2 * c0 + threadIdx.x) * G + bid] = t;
-    }
-    if (nrm && threadIdx.x == 0) {
-      double t = 0;
-      for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CV + q];
-      part[(size_t)(2 * nv) * G + bid] = t;
-    }
-    __syncthreads();
   }
 }
 
@@ -841,6 +771,280 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   for (size_t e = s0 + threadIdx.x; e < s1; e += NT) x[e] = axpy_all<T, false>(x[e], V, n, jstop, sc, e);
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Tile-owned form (levels whose tiling fits the grid): CTA b owns tile b of a tiling in which
+// the last tile column / row absorbs the remainder (2^k + 1 grids split evenly).  The CTA
+// keeps M_l V_j of its own nodes in shared memory, so the Gram-Schmidt dots, a second pass and
+// the update touch only its own nodes: one grid barrier for the reduction and one after the
+// update (halo exchange through the vector in global memory) per iteration.
+
+__host__ __device__ inline int tiles_along(int n, int t) { return n > 1 ? (n - 1 + t - 1) / t : 1; }
+
+struct TileGrid {
+  int TX, TY, ntx, nty;
+};
+
+template <typename T>
+struct ScaledSrc {
+  const cx<T>* x;
+  int nx;
+  T s;
+  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const { return s * ldcg(x + (size_t)gy * nx + gx); }
+};
+
+struct OwnNodes {  // own node q (row-major in the tile) -> grid index
+  int OX, OY, ox0, oy0, nx;
+  __device__ __forceinline__ size_t operator()(int q) const {
+    const int oy = q / OX, ox = q - oy * OX;
+    return (size_t)(oy0 + oy) * nx + (ox0 + ox);
+  }
+  __device__ __forceinline__ int count() const { return OX * OY; }
+};
+
+// Partials of h_i = V_i^H w (i < nv) and ||w||^2 over the CTA's own nodes, w in shared memory;
+// 8 vectors per chunk, one warp transpose-reduction and a fixed-order block combine per chunk.
+template <typename T>
+__device__ void dots_own(const cx<T>* V, size_t n, int nv, const cx<T>* Wt, const OwnNodes& on, double* part,
+                         unsigned bid, unsigned G, double* wred) {
+  constexpr int CH = 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nown = on.count();
+  const int chunks = nv > 0 ? (nv + CH - 1) / CH : 1;
+  for (int c = 0; c < chunks; ++c) {
+    const int c0 = c * CH;
+    const int cnt = max(0, min(CH, nv - c0));
+    T acc[2 * CH];
+#pragma unroll
+    for (int q = 0; q < 2 * CH; ++q) acc[q] = T(0);
+    T wn = T(0);
+    for (int q = threadIdx.x; q < nown; q += NT) {
+      const cx<T> wq = Wt[q];
+      const size_t node = on(q);
+      if (c == 0) wn += wq.re * wq.re + wq.im * wq.im;
+      cx<T> v[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+        if (i < cnt) v[i] = ldcg(V + (size_t)(c0 + i) * n + node);
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+        if (i < cnt) {
+          acc[2 * i] += v[i].re * wq.re + v[i].im * wq.im;
+          acc[2 * i + 1] += v[i].re * wq.im - v[i].im * wq.re;
+        }
+    }
+    const T ws = warp_tsum<T, 2 * CH>(acc);
+    if (lane < 2 * CH) wred[wid * 2 * CH + lane] = double(ws);  // lanes l and l + 2 CH hold the same sum
+    if (c == 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+      if (lane == 0) wred[NW * 2 * CH + wid] = double(wn);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * CH && (threadIdx.x >> 1) < cnt) {
+      double t = 0;
+      for (int q = 0; q < NW; ++q) t += wred[q * 2 * CH + threadIdx.x];
+      part[(size_t)(2 * c0 + threadIdx.x) * G + bid] = t;
+    }
+    if (c == 0 && threadIdx.x == 0) {
+      double t = 0;
+      for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CH + q];
+      part[(size_t)(2 * nv) * G + bid] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const cx<T>* __restrict__ b,
+                                                   cx<T>* __restrict__ x, cx<T>* V, cx<T>* wbuf, double* partA,
+                                                   double* partB, double* Rg, hz::GmresState* st, int cap,
+                                                   double tol, double eta2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t n = (size_t)P.nx * P.ny;
+  const unsigned bid = blockIdx.x, G = gridDim.x;
+  const int tx = (int)bid % tg.ntx, ty = (int)bid / tg.ntx;
+  OwnNodes on;
+  on.ox0 = tx * tg.TX;
+  on.oy0 = ty * tg.TY;
+  on.OX = (tx == tg.ntx - 1) ? P.nx - on.ox0 : tg.TX;
+  on.OY = (ty == tg.nty - 1) ? P.ny - on.oy0 : tg.TY;
+  on.nx = P.nx;
+  const int nown = on.count();
+  // shared memory: tile (room for (TX + 1) x (TY + 1) outputs) | W_own | Krylov scratch
+  cx<T>* Wt = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(tg.TX + 1, tg.TY + 1));
+  unsigned char* kp = reinterpret_cast<unsigned char*>(Wt + (size_t)(tg.TX + 1) * (tg.TY + 1));
+  KShared K;
+  K.h = reinterpret_cast<double*>(kp);
+  K.h1 = K.h + 2 * (cap + 1) + 2;
+  K.gc = K.h1 + 2 * (cap + 1) + 2;
+  K.gs = K.gc + cap;
+  K.g = K.gs + 2 * cap;
+  K.wred = K.g + 2 * (cap + 1);
+  K.scal = K.wred + kWred;
+  K.flags = reinterpret_cast<int*>(K.scal + 4);
+  T* sc = reinterpret_cast<T*>(K.flags + 4);
+  T* gcT = reinterpret_cast<T*>(K.gc);
+  T* gsT = reinterpret_cast<T*>(K.gs);
+  T* gT = reinterpret_cast<T*>(K.g);
+  T* colT = sc + 2 * (cap + 1);
+  T* hT = colT + 2 * (cap + 1);
+  T* h1T = hT + 2 * (cap + 1) + 2;
+
+  // beta = ||b|| over the own nodes, reduced over the grid
+  for (int q = threadIdx.x; q < nown; q += NT) Wt[q] = ldcg(b + on(q));
+  __syncthreads();
+  dots_own<T>(V, n, 0, Wt, on, partA, bid, G, K.wred);
+  if (!grid_reduce(st, G, partA, 0, 1, nullptr, K.scal + 1)) return;
+  const double beta = sqrt(K.scal[1]);
+  if (!(beta > 0)) {
+    if (bid == 0 && threadIdx.x == 0) {
+      st->its = 0;
+      st->est = 0;
+    }
+    return;
+  }
+  const double tol_abs = tol * beta;
+  if (threadIdx.x == 0) {
+    gT[0] = T(beta);
+    gT[1] = T(0);
+  }
+  const cx<T>* src = b;
+  double s = 1.0 / beta;
+  int jstop = 0;
+  double est = beta;
+  // algorithmic bytes in units of one vector: ||b|| reads b once
+  const double eb = (double)sizeof(cx<T>), ekb = (double)sizeof(T);
+  double vec_units = 1.0, k_units = 0.0;
+  int reorths = 0;
+  const TileView<T, R> tv = make_tile<T, R>(smem, on.OX, on.OY, on.ox0, on.oy0);
+  for (int j = 0; j < cap; ++j) {
+    // op: V_j = s * src at the own nodes, W_own = M_l V_j
+    cx<T>* Vj = V + (size_t)j * n;
+    tile_fill<T, R>(tv, P, ScaledSrc<T>{src, P.nx, T(s)});
+    for (int it = threadIdx.x; it < on.OX * ((on.OY + 3) / 4); it += NT) {
+      const int ox = it % on.OX, sy = (it / on.OX) * 4;
+      const int cnt = min(4, on.OY - sy);
+      cx<T> v[4];
+      tile_op_seg<T, R>(tv, P, ox, sy, cnt, v);
+      for (int k = 0; k < cnt; ++k) {
+        const int q = (sy + k) * on.OX + ox;
+        Wt[q] = v[k];
+        Vj[on(q)] = tv.u(ox + R, sy + k + R);
+      }
+    }
+    __syncthreads();
+    vec_units += 2.0;  // read the previous vector, write V_j (M_l V_j stays on chip)
+    k_units += 1.0;
+    const int nv = j + 1;
+    vec_units += nv;  // V_0..V_j
+    dots_own<T>(V, n, nv, Wt, on, partA, bid, G, K.wred);
+    if (!grid_reduce(st, G, partA, 0, 2 * nv + 1, nullptr, K.h)) return;
+    {
+      const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
+      if (threadIdx.x == 0) {
+        const double wn2 = K.h[2 * nv];
+        const double hp = wn2 - double(hs);
+        K.scal[3] = hp;
+        K.flags[1] = !(hp >= eta2 * wn2);
+        if (!K.flags[1])
+          givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
+                         K.scal);
+      }
+    }
+    __syncthreads();
+    if (K.flags[1]) {  // second classical pass on the own nodes (w stays in shared memory)
+      ++reorths;
+      vec_units += 2 * nv;
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) {
+        sc[i] = T(K.h[i]);
+        h1T[i] = hT[i];
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < nown; q += NT) Wt[q] = axpy_all<T, true>(Wt[q], V, n, nv, sc, on(q));
+      __syncthreads();
+      dots_own<T>(V, n, nv, Wt, on, partB, bid, G, K.wred);
+      if (!grid_reduce(st, G, partB, 0, 2 * nv + 1, nullptr, K.h)) return;
+      const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
+      if (threadIdx.x == 0) {
+        const double hp = K.h[2 * nv] - double(hs);
+        givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags, K.scal);
+      }
+      __syncthreads();
+    }
+    if (bid == 0) {  // CTA 0 keeps the rotated column j (FP64) for the final triangular solve
+      double* Rc = Rg + 2 * (size_t)j * (cap + 1);
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) Rc[i] = double(colT[i]);
+    }
+    if (!K.flags[0]) {  // w' = w - V h at the own nodes, to global memory for the neighbours' halos
+      vec_units += nv + 1;
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
+      __syncthreads();
+      for (int q = threadIdx.x; q < nown; q += NT) {
+        const size_t node = on(q);
+        wbuf[node] = axpy_all<T, true>(Wt[q], V, n, nv, sc, node);
+      }
+      if (!grid_sync(st, G)) return;
+    }
+    est = K.scal[2];
+    if (K.flags[0]) {
+      jstop = j + 1;
+      break;
+    }
+    s = K.scal[0];
+    src = wbuf;
+  }
+  // y = R^-1 g by warp 0 of CTA 0, then x += V y at the own nodes
+  double* y = Rg + 2 * (size_t)cap * (cap + 1);
+  if (bid == 0 && threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double* gw = K.h;
+    double* dinv = K.h1;
+    for (int i = lane; i < 2 * jstop; i += 32) gw[i] = double(gT[i]);
+    for (int i = lane; i < jstop; i += 32) {
+      const double dr = Rg[2 * ((size_t)i * (cap + 1) + i)], di = Rg[2 * ((size_t)i * (cap + 1) + i) + 1];
+      const double d = dr * dr + di * di;
+      dinv[2 * i] = dr / d;
+      dinv[2 * i + 1] = -di / d;
+    }
+    __syncwarp();
+    for (int i = jstop - 1; i >= 0; --i) {
+      const double* Ri = Rg + 2 * (size_t)i * (cap + 1);
+      double yr = 0, yi = 0;
+      if (lane == 0) {
+        const double sr = gw[2 * i], si = gw[2 * i + 1];
+        const double ir = dinv[2 * i], ii = dinv[2 * i + 1];
+        yr = sr * ir - si * ii;
+        yi = sr * ii + si * ir;
+        y[2 * i] = yr;
+        y[2 * i + 1] = yi;
+      }
+      yr = __shfl_sync(0xffffffffu, yr, 0);
+      yi = __shfl_sync(0xffffffffu, yi, 0);
+      for (int k = lane; k < i; k += 32) {
+        const double rr = Ri[2 * k], ri = Ri[2 * k + 1];
+        gw[2 * k] -= rr * yr - ri * yi;
+        gw[2 * k + 1] -= rr * yi + ri * yr;
+      }
+      __syncwarp();
+    }
+  }
+  if (bid == 0 && threadIdx.x == 0) {
+    st->its = jstop;
+    st->est = est;
+    st->total_its += jstop;
+    st->total_reorth += reorths;
+    st->total_bytes += (vec_units + jstop + 2) * eb * (double)n + k_units * ekb * (double)n;
+  }
+  if (!grid_sync(st, G)) return;
+  for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(__ldcg(y + i));
+  __syncthreads();
+  for (int q = threadIdx.x; q < nown; q += NT) {
+    const size_t node = on(q);
+    x[node] = axpy_all<T, false>(x[node], V, n, jstop, sc, node);
+  }
+}
+
 template <typename T>
 OpP<T> mkop(const hz::OpDesc& d) {
   OpP<T> p;
@@ -864,11 +1068,76 @@ OpP<T> mkop(const hz::OpDesc& d) {
   return p;
 }
 
+template <typename T>
+size_t krylov_smem_bytes(int cap) {
+  return sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) + kWred + 4) + sizeof(int) * 4 +
+         sizeof(T) * (8 * (cap + 1) + 4) + 64;
+}
+
 template <typename T, int R, int TS = 0>
 size_t kshared_bytes(int cap) {
-  return tile_smem_bytes<T, R>(TileShape<TS>::X, TileShape<TS>::Y) + sizeof(double) * (2 * (2 * (cap + 1) + 2) + cap + 2 * cap + 2 * (cap + 1) +
-                                                             kWred + 4) +
-         sizeof(int) * 4 + sizeof(T) * (8 * (cap + 1) + 4) + 64;
+  return tile_smem_bytes<T, R>(TileShape<TS>::X, TileShape<TS>::Y) + krylov_smem_bytes<T>(cap);
+}
+
+template <typename T, int R>
+size_t tile_form_smem(int TX, int TY, int cap) {
+  return tile_smem_bytes<T, R>(TX + 1, TY + 1) + sizeof(cx<T>) * (size_t)(TX + 1) * (TY + 1) + krylov_smem_bytes<T>(cap);
+}
+
+// Tile shape of the tile-owned form for an nx x ny level: the candidate with the most tiles that
+// still gives every CTA its own tile (at most the co-resident CTAs of that shape), tiles of at
+// least 256 nodes.  Returns the tile count (0: the form does not fit this level).
+template <typename T, int R>
+int tile_form_choice(int nx, int ny, int cap, int* TXo, int* TYo) {
+  static const int cand[4][2] = {{64, 32}, {32, 32}, {32, 16}, {16, 16}};
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  int best = 0;
+  for (const auto& c : cand) {
+    const int TX = c[0], TY = c[1];
+    const size_t sm = tile_form_smem<T, R>(TX, TY, cap);
+    if (sm > (size_t)optin) continue;
+    const int nt = tiles_along(nx, TX) * tiles_along(ny, TY);
+    if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile<T, R>), sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres_tile<T, R>, NT, sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (nt > per * sms || nt <= best) continue;
+    best = nt;
+    *TXo = TX;
+    *TYo = TY;
+  }
+  return best;
+}
+
+template <typename T, int R>
+cudaError_t gmres_tile_t(hz::Ctx& c, const hz::OpDesc& d, const void* b, void* x, void* V, void* w0, double* partA,
+                         double* partB, double* Rg, hz::GmresState* st, int cap, double tol, int TX, int TY,
+                         double eta2) {
+  TileGrid tg;
+  tg.TX = TX;
+  tg.TY = TY;
+  tg.ntx = tiles_along(d.nx, TX);
+  tg.nty = tiles_along(d.ny, TY);
+  const int grid = tg.ntx * tg.nty;
+  const size_t sm = tile_form_smem<T, R>(TX, TY, cap);
+  cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile<T, R>), sm);
+  if (e != cudaSuccess) return e;
+  OpP<T> P = mkop<T>(d);
+  const cx<T>* bb = reinterpret_cast<const cx<T>*>(b);
+  cx<T>* xx = reinterpret_cast<cx<T>*>(x);
+  cx<T>* VV = reinterpret_cast<cx<T>*>(V);
+  cx<T>* wb = reinterpret_cast<cx<T>*>(w0);
+  void* args[] = {&P, &tg, &bb, &xx, &VV, &wb, &partA, &partB, &Rg, &st, &cap, &tol, &eta2};
+  hz::ProfScope ps(c, hz::F_GMRES, 0.0);
+  return cudaLaunchCooperativeKernel((const void*)k_gmres_tile<T, R>, dim3(grid), dim3(NT), args, sm, c.s);
 }
 
 // The grid form uses 64 x 32 tiles on FP32 levels of at least 2^18 nodes with the radius-3
@@ -1010,6 +1279,36 @@ int gmres_cluster_size(int dt, int R, int cap) {
     if (R == 3) return cluster_size_t<float, 3>(cap);
   }
   return 0;
+}
+
+int gmres_tile_form(int dt, int R, int nx, int ny, int cap, int* TX, int* TY) {
+  if (dt == C128) {
+    if (R == 1) return tile_form_choice<double, 1>(nx, ny, cap, TX, TY);
+    if (R == 2) return tile_form_choice<double, 2>(nx, ny, cap, TX, TY);
+    if (R == 3) return tile_form_choice<double, 3>(nx, ny, cap, TX, TY);
+  } else {
+    if (R == 1) return tile_form_choice<float, 1>(nx, ny, cap, TX, TY);
+    if (R == 2) return tile_form_choice<float, 2>(nx, ny, cap, TX, TY);
+    if (R == 3) return tile_form_choice<float, 3>(nx, ny, cap, TX, TY);
+  }
+  return 0;
+}
+
+cudaError_t launch_gmres_tile(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
+                              double* partA, double* partB, double* Rg, GmresState* st, int cap, double tol, int TX,
+                              int TY, double eta2) {
+#define HZ_GT(T_, R_) return gmres_tile_t<T_, R_>(c, M, b, x, V, w0, partA, partB, Rg, st, cap, tol, TX, TY, eta2)
+  if (dt == C128) {
+    if (M.R == 1) HZ_GT(double, 1);
+    if (M.R == 2) HZ_GT(double, 2);
+    if (M.R == 3) HZ_GT(double, 3);
+  } else {
+    if (M.R == 1) HZ_GT(float, 1);
+    if (M.R == 2) HZ_GT(float, 2);
+    if (M.R == 3) HZ_GT(float, 3);
+  }
+#undef HZ_GT
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gmres_persistent(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,

@@ -208,16 +208,24 @@ def test_cslp_gmres_fp64(hz, level, device_gmres):
     assert its_ref <= krylov_cap(6.0, cy * cx)
 
 
-@pytest.mark.parametrize("level,n,device_gmres", [(1, 1025, 1), (3, 257, 1), (3, 257, 3), (1, 257, 3), (1, 1025, 3),
-                                                  (3, 2049, 1)])
+@pytest.mark.parametrize("level,n,device_gmres", [(1, 1025, 1), (3, 257, 1), (3, 257, 3), (3, 257, 4), (1, 257, 3),
+                                                  (1, 1025, 3), (3, 2049, 1), (3, 2049, 4)])
 def test_cslp_gmres_fp32(hz, level, n, device_gmres):
     """FP32 GMRES (device kernel) reaches the 0.1 tolerance measured in FP64 and stays within
-    two iterations of the FP64 oracle; level 1 runs GMRES on the finest grid (mg_max_level = 0),
-    as a cooperative grid (1) and in one cluster with large per-CTA slices (3); level 3 of a
-    2049^2 grid (513^2 nodes) takes the 64 x 32 operator tiles of large levels."""
+    two iterations of the FP64 oracle.  Level 1 runs GMRES on the finest grid (mg_max_level = 0):
+    1025^2 as the slice-distributed grid (1), 257^2 and 1025^2 in one cluster (3).  Level 3 of
+    257^2 (65^2 nodes) and of 2049^2 (513^2 nodes): tile-owned grid (1) and slice-distributed
+    grid (4, with 64 x 32 operator tiles at 513^2)."""
     p = mp.random_field(n, 5.0, seed=3, kh_max=0.3, levels=4 if level == 3 else 1)
     H = handle(hz, p.k, p.h, levels=p.levels, precision="mixed", mg_max_level=0 if level == 1 else 2,
-               device_gmres=device_gmres)
+               device_gmres=device_gmres, autotune=0)
+    form = H.gmres_form(level)["form"]
+    if device_gmres == 3:
+        assert form == "cluster"
+    elif device_gmres == 4 or (level, n) == (1, 1025):
+        assert form == "slice"
+    else:
+        assert form == "tile"
     cy, cx = H.level_size(level)
     kl = T.inject(p.k, 2 ** (level - 1))
     b = round32(mp.random_complex((cy, cx), seed=25))

@@ -92,3 +92,23 @@ def test_solve_host_matches_device(hz):
     ud, _ = H.solve(dev(p.b[0]))
     uh, st = H.solve_host(p.b[0])
     assert np.array_equal(host(ud), uh)
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_autotuned_forms_solve_alike(hz, autotune):
+    """The tile-owned GMRES form (taken wherever it fits with autotune = 0) and whatever the
+    timing autotuner picks give solutions that agree with the slice-distributed form to the
+    solve tolerance and with the same outer iteration count within one."""
+    p = mp.named("wedge_289x481")
+    base = hz.Helmholtz(dev(p.k), p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="mixed",
+                        device_gmres=4)
+    u4, st4 = base.solve(dev(p.b[0]), tol=1e-6)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="mixed",
+                     autotune=autotune)
+    forms = [H.gmres_form(l)["form"] for l in range(3, p.levels + 1)]
+    if autotune == 0:
+        assert all(f == "tile" for f in forms)
+    u, st = H.solve(dev(p.b[0]), tol=1e-6)
+    assert st[0]["status"] == 0 and st[0]["true_relres"] <= 1e-6
+    assert abs(st[0]["outer_iterations"] - st4[0]["outer_iterations"]) <= 1
+    assert rel2(host(u), host(u4)) <= 1e-5
