@@ -42,6 +42,8 @@ WORKLOADS = {
     "mp1b_129": "129x129 constant k = 20, point source at the centre, 2-level, tol 1e-6",
     "random_1025": "1025x1025 seeded random-velocity model, k_max h = 0.3, 4-level MADP, tol 1e-6",
     "random_513": "513x513 seeded random-velocity model, k_max h = 0.3, 3-level MADP, tol 1e-6",
+    "wedge_2049_64rhs": "2049x2049 square version of the synthetic wedge (1000 x 1000 m), k_max h = 0.3, 64 unit "
+                        "point sources evenly spaced along the top row, 6-level MADP, tol 1e-6 per right-hand side",
 }
 METRIC = "solves/s at a 1e-6 relative residual (time-to-solution = ms_per_step)"
 # Iteration counts of one solve of each workload at tol 1e-6, mixed precision, as the GPU
@@ -75,6 +77,8 @@ def parse():
                     help="time one building block on the workload's finest grid instead of a solve")
     ap.add_argument("--repeat", type=int, default=20)
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per call in --micro mode")
+    ap.add_argument("--batch", type=int, default=16,
+                    help="right-hand sides per lockstep sub-batch for multi-source workloads")
     ap.add_argument("--serve", action="store_true",
                     help="serving trace: mixed requests with Poisson arrivals through hz_server_*")
     ap.add_argument("--requests", type=int, default=32)
@@ -381,6 +385,120 @@ def serve(args):
     print(json.dumps(line))
 
 
+def batched(args, p):
+    """Multi-source workload: every step solves all of the workload's right-hand sides, in
+    lockstep sub-batches of --batch (each right-hand side keeps its own Krylov state and
+    stopping test); value = right-hand sides solved per second."""
+    import torch
+
+    import paper_2412_04980_gb300 as hz
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B = args.batch
+    k = torch.from_numpy(p.k).to(dev)
+    b_all = torch.from_numpy(p.b).to(dev)
+    u_all = torch.empty_like(b_all)
+    stream = torch.cuda.current_stream(dev)
+    H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision,
+                     max_rhs=B)
+    mem_gb = H.memory_bytes() / 1e9
+    nr = p.nrhs
+
+    def step():
+        sts = []
+        for i in range(0, nr, B):
+            _, st = H.solve(b_all[i:i + B], u_all[i:i + B], tol=1e-6)
+            sts += st
+        return sts
+
+    for _ in range(args.warmup):
+        step()
+    fams = H.kernel_families()
+    for f in range(len(fams)):
+        H.profile_enable(f, True)
+    step()
+    fam_ms = {}
+    for f in range(len(fams)):
+        fam_ms[fams[f]] = H.profile_read(f)
+        H.profile_enable(f, False)
+    dom = max(fam_ms, key=lambda x: fam_ms[x][1])
+    dom_id = fams.index(dom)
+    H.profile_enable(dom_id, True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = H.launch_count()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    stats = []
+    for s_ in range(args.steps):
+        stats = step()
+        ev[s_ + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = H.launch_count() - l0
+    clk = clocks.stop()
+    n_dom, ms_dom, by_dom = H.profile_read(dom_id)
+    H.profile_enable(dom_id, False)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    assert all(x["status"] == 0 and x["true_relres"] <= 1e-6 for x in stats)
+    # end to end: host right-hand sides in, host solutions out, through hz_solve_host
+    b_host = p.b
+    t0 = time.perf_counter()
+    for i in range(0, nr, B):
+        H.solve_host(b_host[i:i + B], tol=1e-6)
+    e2e_s = time.perf_counter() - t0
+    H.close()
+    del u_all
+    torch.cuda.empty_cache()
+    fp64 = None
+    if not args.no_fp64:  # plain FP64 on one sub-batch of 8, scaled per right-hand side
+        B64 = min(8, nr)
+        H64 = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="fp64",
+                           max_rhs=B64)
+        u64 = torch.empty_like(b_all[:B64])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st64 = H64.solve(b_all[:B64], u64, tol=1e-6)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64 = {"rhs_per_s": B64 / (e0.elapsed_time(e1) / 1e3), "batch": B64, "s": e0.elapsed_time(e1) / 1e3,
+                "max_outer": max(x["outer_iterations"] for x in st64)}
+        H64.close()
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as f:
+            peaks = json.load(f)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    total_s = sum(step_ms) / 1e3
+    achieved = (by_dom / 1e9) / (ms_dom / 1e3) if ms_dom > 0 else None
+    nbytes = p.nx * p.ny * 16 * nr
+    line = {
+        "metric": "right-hand sides solved per second at a 1e-6 relative residual each", "mode": "batched",
+        "value": args.steps * nr / total_s, "unit": "rhs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (FP32 preconditioner, FP64 outer FGMRES)" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
+                   "levels": p.levels, "nrhs": nr, "batch": B, "precision": args.precision,
+                   "workspace_gb": mem_gb},
+        "outer_iterations": {"min": min(x["outer_iterations"] for x in stats),
+                             "max": max(x["outer_iterations"] for x in stats)},
+        "max_true_relres": max(x["true_relres"] for x in stats),
+        "fp64_gpu": fp64,
+        "e2e": {"value": nr / e2e_s, "unit": "rhs/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                     "share_of_step": ms_dom / max(sum(step_ms), 1e-9),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "kernel_ms_per_step": {f: round(v[1], 3) for f, v in fam_ms.items()},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -437,6 +555,8 @@ def main():
     dev = torch.device("cuda", local)
 
     p = mp.named(args.workload)
+    if p.nrhs > 1:
+        return batched(args, p)
     k = torch.from_numpy(p.k).to(dev)
     b = torch.from_numpy(p.b[0]).to(dev)
     stream = torch.cuda.current_stream(dev)
