@@ -77,6 +77,9 @@ def parse():
                     help="time one building block on the workload's finest grid instead of a solve")
     ap.add_argument("--repeat", type=int, default=20)
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per call in --micro mode")
+    ap.add_argument("--level", type=int, default=1,
+                    help="--micro gmres: deflation level whose CSLP GMRES runs (>= 3 keeps the level's own "
+                         "radius-3 operator; the levels above get minimal Krylov workspace)")
     ap.add_argument("--batch", type=int, default=16,
                     help="right-hand sides per lockstep sub-batch for multi-source workloads")
     ap.add_argument("--serve", action="store_true",
@@ -264,13 +267,20 @@ def micro(args):
     extra = {"mg_max_level": 0} if args.micro == "gmres" else {}
     if args.device_gmres is not None:
         extra["device_gmres"] = args.device_gmres
-    H = hz.Helmholtz(k, p.h, levels=1, precision=prec, max_rhs=args.nrhs, **extra)
-    shape = (p.ny, p.nx) if args.nrhs == 1 else (args.nrhs, p.ny, p.nx)
+    lev = args.level if args.micro == "gmres" else 1
+    if lev > 1:  # GMRES on a coarse level: default multigrid on levels 1-2, small bases above
+        extra = {k_: v for k_, v in extra.items() if k_ != "mg_max_level"}
+        H = hz.Helmholtz(k, p.h, levels=lev, precision=prec, max_rhs=args.nrhs, restart=1, l2_maxit=1,
+                         negdef_from_level=p.negdef_from_level, **extra)
+    else:
+        H = hz.Helmholtz(k, p.h, levels=1, precision=prec, max_rhs=args.nrhs, **extra)
+    ny_, nx_ = H.level_size(lev)
+    shape = (ny_, nx_) if args.nrhs == 1 else (args.nrhs, ny_, nx_)
     f = torch.from_numpy(mp.random_complex(shape, seed=7)).to(dev)
     if args.micro != "apply":
         f = f.to(cdt)
     fams = H.kernel_families()
-    run = {"gmres": lambda: H.cslp_gmres(1, f), "vcycle": lambda: H.mg_vcycle(1, f),
+    run = {"gmres": lambda: H.cslp_gmres(lev, f), "vcycle": lambda: H.mg_vcycle(1, f),
            "apply": lambda: H.apply(f)}[args.micro]
     for _ in range(args.warmup):
         out = run()
@@ -283,7 +293,7 @@ def micro(args):
         out = run()
     e1.record()
     torch.cuda.synchronize()
-    res = {"micro": args.micro, "workload": args.workload, "precision": prec, "repeat": args.repeat,
+    res = {"micro": args.micro, "workload": args.workload, "level": lev, "precision": prec, "repeat": args.repeat,
            "nrhs": args.nrhs, "device_gmres": H.cfg.device_gmres,
            "ms_per_call": e0.elapsed_time(e1) / args.repeat}
     if args.micro == "gmres":

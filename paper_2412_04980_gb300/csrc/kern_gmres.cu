@@ -428,30 +428,48 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
   my_slice(n, bid, G, s0, s1);
   T acc = T(0);
   if (s1 - s0 > kLargeSlice) {
-    for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += 4 * NT) {
-      cx<T> x[4];
+    // 8 elements per thread, two basis vectors per step (16 loads in flight), downwards: the
+    // last-read vectors are still in L2; each element's updates keep the order V_{nv-1} .. V_0
+    constexpr int E = 8;
+    for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += E * NT) {
+      cx<T> x[E];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < E; ++k) {
         const size_t e = e0 + k * NT;
         x[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
       }
-      for (int i = nv - 1; i >= 0; --i) {  // downwards: the last-read vectors are in L2
-        const cx<T>* Vi = V + (size_t)i * n;
-        const T cr = sc[2 * i], ci = sc[2 * i + 1];
-        cx<T> v[4];
+      int i = nv - 1;
+      for (; i >= 1; i -= 2) {
+        const cx<T>* Va = V + (size_t)i * n;
+        const cx<T>* Vb = V + (size_t)(i - 1) * n;
+        cx<T> va[E], vb[E];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < E; ++k) {
           const size_t e = e0 + k * NT;
-          v[k] = e < s1 ? ldcg(Vi + e) : mk<T>(T(0), T(0));
+          va[k] = e < s1 ? ldcg(Va + e) : mk<T>(T(0), T(0));
+          vb[k] = e < s1 ? ldcg(Vb + e) : mk<T>(T(0), T(0));
         }
+        const T ar = sc[2 * i], ai = sc[2 * i + 1], br = sc[2 * i - 2], bi = sc[2 * i - 1];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          x[k].re -= cr * v[k].re - ci * v[k].im;
-          x[k].im -= cr * v[k].im + ci * v[k].re;
+        for (int k = 0; k < E; ++k) {
+          x[k].re -= ar * va[k].re - ai * va[k].im;
+          x[k].im -= ar * va[k].im + ai * va[k].re;
+          x[k].re -= br * vb[k].re - bi * vb[k].im;
+          x[k].im -= br * vb[k].im + bi * vb[k].re;
+        }
+      }
+      if (i == 0) {
+        const T cr = sc[0], ci = sc[1];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const size_t e = e0 + k * NT;
+          const cx<T> v = e < s1 ? ldcg(V + e) : mk<T>(T(0), T(0));
+          x[k].re -= cr * v.re - ci * v.im;
+          x[k].im -= cr * v.im + ci * v.re;
         }
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < E; ++k) {
         const size_t e = e0 + k * NT;
         if (e < s1) {
           w[e] = x[k];
