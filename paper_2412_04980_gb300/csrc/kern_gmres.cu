@@ -418,24 +418,23 @@ __device__ __forceinline__ cx<T> axpy_all(cx<T> x, const cx<T>* V, size_t n, int
   return x;
 }
 
-// w -= sum_i h_i V_i over this CTA's slice; with_norm: CTA partial of ||w||^2 into part[bid]
+// w -= sum_i h_i V_i over this CTA's slice with coefficients sc (typed), by threads
+// t0 = 0 .. nthr - 1 of the CTA (no CTA-wide synchronisation inside, so a subset of the warps can
+// run it while others do something else).
 template <typename T>
-__device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T* sc, cx<T>* w, double* part,
-                            int pstride, double* wred, bool with_norm, unsigned bid, unsigned G) {
-  for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(h[i]);
-  __syncthreads();
+__device__ __forceinline__ void update_slice(const cx<T>* V, size_t n, int nv, const T* sc, cx<T>* w, unsigned bid,
+                                             unsigned G, int t0, int nthr) {
   size_t s0, s1;
   my_slice(n, bid, G, s0, s1);
-  T acc = T(0);
   if (s1 - s0 > kLargeSlice) {
     // 8 elements per thread, two basis vectors per step (16 loads in flight), downwards: the
     // last-read vectors are still in L2; each element's updates keep the order V_{nv-1} .. V_0
     constexpr int E = 8;
-    for (size_t e0 = s0 + threadIdx.x; e0 < s1; e0 += E * NT) {
+    for (size_t e0 = s0 + t0; e0 < s1; e0 += (size_t)E * nthr) {
       cx<T> x[E];
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        const size_t e = e0 + k * NT;
+        const size_t e = e0 + (size_t)k * nthr;
         x[k] = e < s1 ? ldcg(w + e) : mk<T>(T(0), T(0));
       }
       int i = nv - 1;
@@ -445,7 +444,7 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
         cx<T> va[E], vb[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-          const size_t e = e0 + k * NT;
+          const size_t e = e0 + (size_t)k * nthr;
           va[k] = e < s1 ? ldcg(Va + e) : mk<T>(T(0), T(0));
           vb[k] = e < s1 ? ldcg(Vb + e) : mk<T>(T(0), T(0));
         }
@@ -462,7 +461,7 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
         const T cr = sc[0], ci = sc[1];
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-          const size_t e = e0 + k * NT;
+          const size_t e = e0 + (size_t)k * nthr;
           const cx<T> v = e < s1 ? ldcg(V + e) : mk<T>(T(0), T(0));
           x[k].re -= cr * v.re - ci * v.im;
           x[k].im -= cr * v.im + ci * v.re;
@@ -470,30 +469,22 @@ __device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T
       }
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        const size_t e = e0 + k * NT;
-        if (e < s1) {
-          w[e] = x[k];
-          acc += x[k].re * x[k].re + x[k].im * x[k].im;
-        }
+        const size_t e = e0 + (size_t)k * nthr;
+        if (e < s1) w[e] = x[k];
       }
     }
   } else {
-    for (size_t e = s0 + threadIdx.x; e < s1; e += NT) {
-      const cx<T> x = axpy_all<T, true>(ldcg(w + e), V, n, nv, sc, e);
-      w[e] = x;
-      acc += x.re * x.re + x.im * x.im;
-    }
+    for (size_t e = s0 + t0; e < s1; e += nthr) w[e] = axpy_all<T, true>(ldcg(w + e), V, n, nv, sc, e);
   }
-  if (!with_norm) return;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = double(acc);
+}
+
+// w -= sum_i h_i V_i over this CTA's slice (h in FP64 shared memory), all threads
+template <typename T>
+__device__ void update_pass(const cx<T>* V, size_t n, int nv, const double* h, T* sc, cx<T>* w, unsigned bid,
+                            unsigned G) {
+  for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(h[i]);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int q = 0; q < NT / 32; ++q) t += wred[q];
-    part[bid] = t;
-  }
+  update_slice<T>(V, n, nv, sc, w, bid, G, threadIdx.x, NT);
 }
 
 // One Givens step on Hessenberg column j (entries h[0..2j+1] plus, with h2, a second-pass
@@ -689,23 +680,38 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     vec_units += nv + 1;  // read V_0..V_j and w
     dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
     if (!reduce_all<CL>(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
+    bool updated = false;
     {
+      // every thread holds the same reduced values, so every thread takes the same decision
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
-      if (threadIdx.x == 0) {
-        const double wn2 = K.h[2 * nv];
-        const double hp = wn2 - double(hs);
+      const double wn2 = K.h[2 * nv];
+      const double hp = wn2 - double(hs);
+      if (hp >= eta2 * wn2) {
+        // one pass suffices: warp 0 runs the Givens step while the other warps already apply
+        // w' = w - V h (not needed if the solve stops here; it is then simply unused)
+        for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          if (threadIdx.x == 0) {
+            K.scal[3] = hp;
+            K.flags[1] = 0;
+            givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
+                           K.scal);
+          }
+        } else {
+          update_slice<T>(V, n, nv, sc, wnext, bid, G, threadIdx.x - 32, NT - 32);
+        }
+        updated = true;
+      } else if (threadIdx.x == 0) {
         K.scal[3] = hp;
-        K.flags[1] = !(hp >= eta2 * wn2);
-        if (!K.flags[1])
-          givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
-                         K.scal);
+        K.flags[1] = 1;
       }
     }
     __syncthreads();
     if (K.flags[1]) {  // second classical pass
       ++reorths;
       vec_units += (nv + 2) + (nv + 1);  // w -= V h (read V, w; write w), then V^H w again
-      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false, bid, G);
+      update_pass<T>(V, n, nv, K.h, sc, wnext, bid, G);
       if (!bar_all<CL>(st, G)) return;
       for (int i = threadIdx.x; i < 2 * nv; i += NT) h1T[i] = hT[i];
       dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
@@ -723,7 +729,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     }
     if (!K.flags[0]) {  // w' = w - V h (with the last pass's coefficients); the next op needs it complete
       vec_units += nv + 2;
-      update_pass<T>(V, n, nv, K.h, sc, wnext, partB, pstride, K.wred, false, bid, G);
+      if (!updated) update_pass<T>(V, n, nv, K.h, sc, wnext, bid, G);
       if (!bar_all<CL>(st, G)) return;
     }
     est = K.scal[2];
@@ -958,16 +964,31 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
     vec_units += nv;  // V_0..V_j
     dots_own<T>(V, n, nv, Wt, on, partA, bid, G, K.wred);
     if (!grid_reduce(st, G, partA, 0, 2 * nv + 1, nullptr, K.h)) return;
+    bool updated = false;
     {
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
-      if (threadIdx.x == 0) {
-        const double wn2 = K.h[2 * nv];
-        const double hp = wn2 - double(hs);
+      const double wn2 = K.h[2 * nv];
+      const double hp = wn2 - double(hs);
+      if (hp >= eta2 * wn2) {  // one pass: warp 0 rotates while the other warps update the own nodes
+        for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          if (threadIdx.x == 0) {
+            K.scal[3] = hp;
+            K.flags[1] = 0;
+            givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
+                           K.scal);
+          }
+        } else {
+          for (int q = threadIdx.x - 32; q < nown; q += NT - 32) {
+            const size_t node = on(q);
+            wbuf[node] = axpy_all<T, true>(Wt[q], V, n, nv, sc, node);
+          }
+        }
+        updated = true;
+      } else if (threadIdx.x == 0) {
         K.scal[3] = hp;
-        K.flags[1] = !(hp >= eta2 * wn2);
-        if (!K.flags[1])
-          givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
-                         K.scal);
+        K.flags[1] = 1;
       }
     }
     __syncthreads();
@@ -996,11 +1017,13 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
     }
     if (!K.flags[0]) {  // w' = w - V h at the own nodes, to global memory for the neighbours' halos
       vec_units += nv + 1;
-      for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
-      __syncthreads();
-      for (int q = threadIdx.x; q < nown; q += NT) {
-        const size_t node = on(q);
-        wbuf[node] = axpy_all<T, true>(Wt[q], V, n, nv, sc, node);
+      if (!updated) {
+        for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nown; q += NT) {
+          const size_t node = on(q);
+          wbuf[node] = axpy_all<T, true>(Wt[q], V, n, nv, sc, node);
+        }
       }
       if (!grid_sync(st, G)) return;
     }
