@@ -343,6 +343,7 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
     cap = std::max(cap, 1);
     maxnv = std::max(maxnv, (size_t)cap + 1);
     total += (cap + 1) * bn * eb + cap * bn * ex + bn * eb + 3 * bn * ep + (l >= 2 ? 2 * bn * eb : 0) + scal(cap);
+    if (l >= 2 && cap == 1) total += sizeof(int) * 2 * (size_t)nb;  // one-iteration counters
     if (l <= cfg.mg_max_level) {
       int mx = nx, my = ny;
       const bool general = !(cfg.mg_nu1 == 1 && cfg.mg_nu2 == 1);
@@ -377,7 +378,7 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       ny = (ny + 1) / 2;
     }
   }
-  total += dot_ws_bytes((int)maxnv, nb) + scal(1) + (size_t)nb * g.nx * g.ny * 16;
+  total += dot_ws_bytes((int)maxnv, nb) + scal(1) + (size_t)nb * g.nx * g.ny * 16 + sizeof(int);
   return total;
 }
 
@@ -450,6 +451,12 @@ int setup(Handle* h, const double* k_dev) {
       CS(dalloc(h, &L.x, bn * eb));
     }
     CS(alloc_scalars(h, L.sc, L.cap, nb));
+    if (l >= 2 && L.cap == 1) {  // one-iteration cycles run without a host round trip
+      void* p;
+      CS(dalloc(h, &p, sizeof(int) * 2 * (size_t)nb));
+      L.m1cnt = (int*)p;
+      CK(cudaMemsetAsync(L.m1cnt, 0, sizeof(int) * 2 * (size_t)nb, h->ctx.s));
+    }
     if (l <= cfg.mg_max_level) {
       // multigrid CSLP hierarchy (level 0 = this deflation level)
       MGLevel m0;
@@ -547,6 +554,12 @@ int setup(Handle* h, const double* k_dev) {
   CS(dalloc(h, &h->ws, h->ws_bytes));
   CS(alloc_scalars(h, h->outer_sc, 1, nb));
   CS(dalloc(h, &h->rres, (size_t)nb * h->lv[0].n * 16));
+  {
+    void* p;
+    CS(dalloc(h, &p, sizeof(int)));
+    h->derr = (int*)p;
+    CK(cudaMemsetAsync(h->derr, 0, sizeof(int), h->ctx.s));
+  }
   h->st.assign(nb, RhsStats());
   CK(cudaStreamSynchronize(h->ctx.s));
   if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_gmres(h));
@@ -898,6 +911,27 @@ static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, voi
 
 int collect_gmres_stats(Handle* h, int nb) {
   for (auto& L : h->lv) {
+    if (!L.m1cnt) continue;
+    std::vector<int> cnt(2 * (size_t)nb);
+    CK(cudaMemcpyAsync(cnt.data(), L.m1cnt, sizeof(int) * 2 * (size_t)nb, cudaMemcpyDeviceToHost, h->ctx.s));
+    CK(cudaMemsetAsync(L.m1cnt, 0, sizeof(int) * 2 * (size_t)nb, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    for (int q = 0; q < nb; ++q) {
+      h->st[q].lev_it[L.l - 1] += cnt[q];
+      h->st[q].lev_calls[L.l - 1] += cnt[nb + q];
+    }
+  }
+  {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->ctx.s));
+    CK(cudaMemsetAsync(h->derr, 0, sizeof(int), h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    if (err) {
+      set_error("non-finite value in a one-iteration coarse-level cycle");
+      return HZ_EBREAKDOWN;
+    }
+  }
+  for (auto& L : h->lv) {
     if (!L.gst) continue;
     std::vector<GmresState> gs(nb);
     CK(cudaMemcpyAsync(gs.data(), L.gst, sizeof(GmresState) * nb, cudaMemcpyDeviceToHost, h->ctx.s));
@@ -1008,6 +1042,40 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
 }
 
 // v_til ~ A_l^-1 b on level l >= 2 with the MADP schedule; reads lv[l-1].b, writes .x
+// One-iteration (F)GMRES cycle of a coarse level (levels 3..ml-1, and the coarsest level when it
+// is treated as negative definite) with every scalar step on the device: the same Arnoldi step
+// as cycle() with m = 1, no host round trip.  Iteration counts and breakdowns are collected at
+// the end of the solve.  r0 = L.b, solution L.x (zero on entry) += X_0 y.
+static int cycle_m1_device(Handle* h, Level& L, int nb, const std::function<int(const void*, void*)>& prec,
+                           const std::function<int(const void*, void*)>& op) {
+  Ctx& c = h->ctx;
+  Scalars& sc = L.sc;
+  const size_t n = L.n, bn = (size_t)nb * n;
+  const int nv = 1, ldA = 2 * nv + 1;
+  double* hA = sc.dev + sc.hA;
+  double* hB = hA + (size_t)nb * ldA;
+  double* n1 = hB + (size_t)nb * 2 * nv;
+  double* n2 = n1 + nb;
+  double* flag = n2 + nb;
+  double* beta = sc.dev + sc.nrm;
+  double* cs = sc.dev + sc.csc;
+  double* coef = sc.dev + sc.ccomb;
+  CK(launch_multidot(c, L.dvec, L.b, 0, 1, L.b, n, nb, hA, h->ws));
+  CK(launch_m1_begin(c, hA, nb, cs, beta, h->derr));
+  CK(launch_scale_dev(c, L.dvec, L.b, L.V, cs, 0, n, nb));
+  CS(prec(L.V, L.X));
+  CS(op(L.X, L.w));
+  const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
+  CK(launch_multidot(c, L.dvec, L.V, bn, nv, L.w, n, nb, hA, h->ws, 1));
+  CK(launch_update(c, L.dvec, L.V, bn, nv, hA, ldA, L.dvec, L.w, n, nb, n1, h->ws));
+  CK(launch_dgks_flag(c, hA + 2 * nv, ldA, n1, flag, nb, eta2));
+  CK(launch_multidot(c, L.dvec, L.V, bn, nv, L.w, n, nb, hB, h->ws, 0, flag));
+  CK(launch_update(c, L.dvec, L.V, bn, nv, hB, 2 * nv, L.dvec, L.w, n, nb, n2, h->ws, flag));
+  CK(launch_m1_finish(c, hA, ldA, hB, n1, n2, flag, beta, nb, coef, L.m1cnt, L.m1cnt + nb, h->derr));
+  CK(launch_combine(c, L.dx, L.X, bn, 1, coef, L.dvec, L.x, n, nb));
+  return HZ_OK;
+}
+
 int coarse_solve(Handle* h, int l, int nb) {
   LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
@@ -1027,6 +1095,7 @@ int coarse_solve(Handle* h, int l, int nb) {
     return HZ_OK;
   };
   auto prec = [&](const void* vj, void* xj) -> int { return precond(h, l, vj, L.dvec, xj, nb); };
+  if (L.cap == 1 && L.m1cnt) return cycle_m1_device(h, L, nb, prec, op);
   CycleOut co;
   CS(cycle(h, L.sc, L.dvec, L.dx, L.n, nb, L.V, L.X, L.w, L.cap, L.b, L.x, L.dvec, tol, nullptr, nullptr, prec, op,
            co));

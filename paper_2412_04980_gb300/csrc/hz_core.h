@@ -50,6 +50,7 @@ struct Level {
   void* rt = nullptr;                        // r_til, dpre
   void* r = nullptr;                         // general-path scratch, dpre
   Scalars sc;
+  int* m1cnt = nullptr;                      // one-iteration levels: per-rhs iterations, then calls (device)
   // GMRES CSLP inverse (l > mg_max_level)
   int capg = 0;
   void* Vg = nullptr;                        // (capg + 1) batches, dpre
@@ -91,6 +92,7 @@ struct Handle {
   std::vector<RhsStats> st;                  // per-rhs statistics of the running call
   Scalars outer_sc;                          // true-residual norms
   void* rres = nullptr;                      // level-1 true residual buffer (C128)
+  int* derr = nullptr;                       // device breakdown flag of the device-side cycles
 };
 
 // allocation helpers (track for hz_destroy)

@@ -192,6 +192,74 @@ __global__ void k_dgks(const double* __restrict__ wn, int ldw, const double* __r
   if (b < nb) flag[b] = (n1[b] >= eta2 * wn[(size_t)b * ldw]) ? 1.0 : 0.0;
 }
 
+// One-iteration FGMRES without a host round trip (levels whose cycle is exactly one iteration).
+// begin: beta_b = ||r0_b|| from the multidot output (||r0||^2 at nrm2[2 b]); cs_b = 1 / beta_b
+// (0 for a zero residual); a non-finite norm sets *err.
+__global__ void k_m1_begin(const double* __restrict__ nrm2, int nb, double* __restrict__ cs, double* __restrict__ beta,
+                           int* __restrict__ err) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double s = nrm2[2 * b];
+  double be = s > 0 ? sqrt(s) : 0.0;
+  if (!isfinite(be)) {
+    atomicExch(err, 1);
+    be = 0.0;
+  }
+  beta[b] = be;
+  cs[2 * b] = be > 0 ? 1.0 / be : 0.0;
+  cs[2 * b + 1] = 0.0;
+}
+
+// finish: the 2 x 1 Hessenberg column [h_00 (+ second-pass correction); ||w'||], one Givens
+// rotation, y = c beta / R_00 into coef[2 b] (0 for a zero residual); per-rhs iteration and call
+// counters; non-finite values set *err.
+__global__ void k_m1_finish(const double* __restrict__ hA, int ldA, const double* __restrict__ hB,
+                            const double* __restrict__ n1, const double* __restrict__ n2,
+                            const double* __restrict__ flag, const double* __restrict__ beta, int nb,
+                            double* __restrict__ coef, int* __restrict__ its, int* __restrict__ calls,
+                            int* __restrict__ err) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double be = beta[b];
+  coef[2 * b] = 0.0;
+  coef[2 * b + 1] = 0.0;
+  if (!(be > 0)) return;
+  const bool second = flag[b] == 0.0;
+  const double ar = hA[(size_t)b * ldA] + (second ? hB[2 * b] : 0.0);
+  const double ai = hA[(size_t)b * ldA + 1] + (second ? hB[2 * b + 1] : 0.0);
+  const double nr = flag[b] != 0.0 ? n1[b] : n2[b];
+  const double hn = nr > 0 ? sqrt(nr) : 0.0;
+  const double aa = hypot(ar, ai);
+  const double t = sqrt((ar * ar + ai * ai) + hn * hn);
+  double c, sr, si;
+  if (t == 0) {
+    c = 1;
+    sr = si = 0;
+  } else if (aa == 0) {
+    c = 0;
+    sr = 1;
+    si = 0;
+  } else {
+    c = aa / t;
+    sr = (ar / aa) * hn / t;
+    si = (ai / aa) * hn / t;
+  }
+  const double Rr = c * ar + sr * hn, Ri = c * ai + si * hn;  // rotated R_00
+  const double est = hypot(sr, si) * be;
+  if (!isfinite(est) || !isfinite(hn)) {
+    atomicExch(err, 1);
+    return;
+  }
+  const double g0 = c * be;
+  const double d = Rr * Rr + Ri * Ri;
+  if (d > 0) {
+    coef[2 * b] = g0 * Rr / d;
+    coef[2 * b + 1] = -g0 * Ri / d;
+  }
+  its[b] += 1;
+  calls[b] += 1;
+}
+
 // u += sum_i coef_i X_i
 template <typename TX, typename TU>
 __global__ void __launch_bounds__(NT) k_combine(const cx<TX>* __restrict__ X, size_t ldx, int nv,
@@ -340,6 +408,20 @@ cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, co
 cudaError_t launch_dgks_flag(Ctx& c, const double* wn, int ldw, const double* n1, double* flag, int nb, double eta2) {
   ProfScope ps(c, F_REDUCE, (double)nb * 24);
   k_dgks<<<(nb + 127) / 128, 128, 0, c.s>>>(wn, ldw, n1, flag, nb, eta2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m1_begin(Ctx& c, const double* nrm2, int nb, double* cs, double* beta, int* err) {
+  ProfScope ps(c, F_REDUCE, (double)nb * 40);
+  k_m1_begin<<<(nb + 127) / 128, 128, 0, c.s>>>(nrm2, nb, cs, beta, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m1_finish(Ctx& c, const double* hA, int ldA, const double* hB, const double* n1, const double* n2,
+                             const double* flag, const double* beta, int nb, double* coef, int* its, int* calls,
+                             int* err) {
+  ProfScope ps(c, F_REDUCE, (double)nb * 96);
+  k_m1_finish<<<(nb + 127) / 128, 128, 0, c.s>>>(hA, ldA, hB, n1, n2, flag, beta, nb, coef, its, calls, err);
   return cudaGetLastError();
 }
 
