@@ -1041,7 +1041,6 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
   return cslp_inverse(h, l, L.rt, xout, L.t, nb);                                  // lines 14-15
 }
 
-// v_til ~ A_l^-1 b on level l >= 2 with the MADP schedule; reads lv[l-1].b, writes .x
 // One-iteration (F)GMRES cycle of a coarse level (levels 3..ml-1, and the coarsest level when it
 // is treated as negative definite) with every scalar step on the device: the same Arnoldi step
 // as cycle() with m = 1, no host round trip.  Iteration counts and breakdowns are collected at
@@ -1076,6 +1075,7 @@ static int cycle_m1_device(Handle* h, Level& L, int nb, const std::function<int(
   return HZ_OK;
 }
 
+// v_til ~ A_l^-1 b on level l >= 2 with the MADP schedule; reads lv[l-1].b, writes .x
 int coarse_solve(Handle* h, int l, int nb) {
   LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
