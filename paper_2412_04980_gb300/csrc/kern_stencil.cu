@@ -64,25 +64,6 @@ struct JacZeroSrc {
   }
 };
 
-// Z vtil from a coarse tile held in shared memory
-template <typename T>
-struct ZSrc {
-  const cx<T>* Cs;
-  int CW, Imin, Jmin;
-  __device__ __forceinline__ cx<T> operator()(int gx, int gy) const {
-    int I0 = floordiv2(gx - 1), I1 = floordiv2(gx + 2);
-    int J0 = floordiv2(gy - 1), J1 = floordiv2(gy + 2);
-    cx<T> acc = mk<T>(T(0), T(0));
-    for (int J = J0; J <= J1; ++J) {
-      T wy = pw<T>(gy - 2 * J);
-      cx<T> row = mk<T>(T(0), T(0));
-      for (int I = I0; I <= I1; ++I) row = row + pw<T>(gx - 2 * I) * Cs[(J - Jmin) * CW + (I - Imin)];
-      acc = acc + wy * row;
-    }
-    return acc;
-  }
-};
-
 // omega f / D + bilinear(ec) from a coarse tile in shared memory
 template <typename T, int R>
 struct UpSrc {
@@ -186,7 +167,39 @@ __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const c
     Cs[idx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? vtil[offc + (size_t)J * ncx + I] : mk<T>(T(0), T(0));
   }
   __syncthreads();
-  tile_fill<T, R>(t, P, ZSrc<T>{Cs, CW, Imin, Jmin});
+  // t = Z vtil on the tile window, separably: the 1-D weights are 1/8, 3/4, 1/8 at even fine
+  // nodes (coarse I-1, I, I+1) and 1/2, 1/2 at odd ones (I, I+1).  First every coarse row is
+  // interpolated to the fine columns (Xs), then the columns to the fine rows (zero outside the grid).
+  {
+    constexpr int WX = OXT + 2 * R, WY = OYT + 2 * R;
+    constexpr int CWM = (OXT + 2 * R + 6) / 2 + 2, CHM = (OYT + 2 * R + 6) / 2 + 2;
+    cx<T>* Xs = Cs + CWM * CHM;
+    const int gx0 = ox0 - R, gy0 = oy0 - R;
+    for (int idx = tid; idx < CH * WX; idx += BX * BY) {
+      const int cj = idx / WX, cxx = idx - cj * WX;
+      const int gx = gx0 + cxx;
+      const cx<T>* r = Cs + cj * CW + (floordiv2(gx) - Imin);
+      Xs[idx] = (gx & 1) ? T(0.5) * (r[0] + r[1]) : T(0.75) * r[0] + T(0.125) * (r[-1] + r[1]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < WX * WY; idx += BX * BY) {
+      const int cy = idx / WX, cxx = idx - cy * WX;
+      const int gx = gx0 + cxx, gy = gy0 + cy;
+      cx<T> u = mk<T>(T(0), T(0)), w = u;
+      if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) {
+        const cx<T>* c = Xs + (floordiv2(gy) - Jmin) * WX + cxx;
+        u = (gy & 1) ? T(0.5) * (c[0] + c[WX]) : T(0.75) * c[0] + T(0.125) * (c[-WX] + c[WX]);
+        if (R >= 2) {
+          const T k = P.k[(size_t)gy * P.nx + gx];
+          w = (k * k) * u;
+        }
+      }
+      t.U[idx] = u;
+      if (R >= 2) t.W[idx] = w;
+    }
+    __syncthreads();
+    tile_finish<T, R>(t, P);
+  }
   auto emit = [&](int ox, int oy, cx<T> s) {
     const size_t i = off + (size_t)(oy0 + oy) * P.nx + (ox0 + ox);
     rtil[i] = cvt<T>(v[i]) - s;
@@ -514,7 +527,7 @@ static cudaError_t dpr_r(Ctx& c, const OpDesc& d, const void* vtil, int ncx, int
   OpP<T> P = make_op<T>(d);
   dim3 grid((d.nx + OXT - 1) / OXT, (d.ny + OYT - 1) / OYT, nrhs), block(BX, BY);
   const int CW = (OXT + 2 * R + 6) / 2 + 2, CH = (OYT + 2 * R + 6) / 2 + 2;
-  size_t sm = tile_smem_bytes<T, R>(OXT, OYT) + sizeof(cx<T>) * CW * CH;
+  size_t sm = tile_smem_bytes<T, R>(OXT, OYT) + sizeof(cx<T>) * (CW * CH + CH * (OXT + 2 * R));
   cudaError_t e = set_smem(k_defl_prolong_resid<T, TV, R>, sm);
   if (e != cudaSuccess) return e;
   double bytes = (double)nrhs * d.n() * (sizeof(cx<TV>) + sizeof(cx<T>) * (t ? 2 : 1) + sizeof(T) + sizeof(cx<T>) / 4.0);
