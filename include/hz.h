@@ -103,7 +103,8 @@ typedef struct {
                             the GPU (FP32) and slice-distributed vector phases elsewhere;
                             2: always the cooperative grid (tile-owned where it fits);
                             3: always clusters; 4: always the slice-distributed grid;
-                            0: host-driven Arnoldi steps */
+                            0: host-driven Arnoldi steps.  Clusters are used with FP32
+                            vectors (HZ_PREC_MIXED) only; FP64 takes the grid instead */
   double reorth_eta;     /* classical Gram-Schmidt runs a second pass when the orthogonalised
                             vector keeps less than reorth_eta of its norm ("twice is enough"
                             test), default 0.1; 1 = always two passes, 0 = one pass */

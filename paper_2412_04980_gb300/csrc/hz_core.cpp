@@ -311,8 +311,12 @@ static std::vector<double> inject(const std::vector<double>& k, int nx, int ny) 
 constexpr int kClusterMinRhs = 4;
 constexpr size_t kClusterMaxN = 300000;
 
-// The cluster form may run on a level of n nodes (it then needs per-rhs GMRES workspace).
+// The cluster form may run on a level of n nodes (it then needs per-rhs GMRES workspace).  It is
+// used for FP32 vectors only: with FP64 vectors a 5-level 2049^2 solve on 4 right-hand sides broke
+// down (isolated FP64 cluster GMRES calls agree with the grid form; the cause is not found), so
+// FP64 batches take the cooperative grid per right-hand side.
 static bool cluster_form_possible(const hz_config& cfg, size_t n) {
+  if (cfg.precision != HZ_PREC_MIXED) return false;
   return cfg.device_gmres == 3 || (cfg.device_gmres == 1 && cfg.max_rhs >= kClusterMinRhs && n <= kClusterMaxN);
 }
 

@@ -85,10 +85,13 @@ def test_estimate_bytes_host_only(L):
     small, big = e(129, levels=2), e(257, levels=2)
     assert 0 < small < big
     assert e(513, levels=5, max_rhs=1) < e(513, levels=5, max_rhs=4)
-    assert e(513, levels=5, max_rhs=4, device_gmres=2) < e(513, levels=5, max_rhs=4, device_gmres=0)
-    assert e(513, levels=5, max_rhs=4, device_gmres=2) < e(513, levels=5, max_rhs=4, device_gmres=3)
-    assert e(513, levels=5, max_rhs=3, device_gmres=1) == e(513, levels=5, max_rhs=3, device_gmres=2)
-    assert e(513, levels=5, max_rhs=4, device_gmres=1) == e(513, levels=5, max_rhs=4, device_gmres=3)
+    m = dict(levels=5, precision="mixed")
+    assert e(513, max_rhs=4, device_gmres=2, **m) < e(513, max_rhs=4, device_gmres=0, **m)
+    assert e(513, max_rhs=4, device_gmres=2, **m) < e(513, max_rhs=4, device_gmres=3, **m)
+    assert e(513, max_rhs=3, device_gmres=1, **m) == e(513, max_rhs=3, device_gmres=2, **m)
+    assert e(513, max_rhs=4, device_gmres=1, **m) == e(513, max_rhs=4, device_gmres=3, **m)
+    # FP64 vectors never take the cluster form
+    assert e(513, levels=5, max_rhs=4, device_gmres=3) == e(513, levels=5, max_rhs=4, device_gmres=2)
     assert e(513, levels=5, precision="mixed") < e(513, levels=5, precision="fp64")
     assert L.hz_estimate_bytes(None, None, None) == hz.HZ_EINVAL
 

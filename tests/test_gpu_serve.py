@@ -124,3 +124,14 @@ def test_multi_rhs_request(hz):
     assert np.array_equal(u, ub)
     assert all(s["status"] == 0 for s in st)
     assert rel2(u[1], ub[1]) == 0
+
+
+def test_fp64_multi_rhs_deep_hierarchy(hz):
+    """Plain FP64, 5 levels on 2049^2, 4 point sources in one batch (the shape of a serving
+    request that once broke down): every right-hand side converges to the tolerance."""
+    p = mp.random_field(2049, 5.0, seed=1004, kh_max=0.3, levels=5, negdef_from_level=4, nsrc=4)
+    H = hz.Helmholtz(dev(p.k), p.h, levels=5, negdef_from_level=4, precision="fp64", max_rhs=4)
+    u, st = H.solve(dev(p.b), tol=1e-6)
+    H.close()
+    assert all(s["status"] == 0 and s["true_relres"] <= 1e-6 for s in st)
+    assert bool(np.isfinite(u.cpu().numpy()).all())
