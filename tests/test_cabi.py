@@ -134,3 +134,20 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_diagnostics_reject_null_handles(L):
+    import paper_2412_04980_gb300 as hz
+    f, c, cl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.hz_level_gmres_form(None, 1, ctypes.byref(f), ctypes.byref(c), ctypes.byref(cl)) == hz.HZ_EINVAL
+    n = ctypes.c_longlong()
+    assert L.hz_launch_count(None, ctypes.byref(n)) == hz.HZ_EINVAL
+
+
+def test_config_validation_of_new_fields(L):
+    import paper_2412_04980_gb300 as hz
+    h = ctypes.c_void_p()
+    g = hz.HzGrid(9, 9, 0.1, 0)
+    for bad in (dict(device_gmres=5), dict(device_gmres=-1), dict(autotune=2), dict(reorth_eta=1.5)):
+        c = hz.config(**bad)
+        assert L.hz_setup(ctypes.byref(g), ctypes.c_void_p(1), ctypes.byref(c), None, ctypes.byref(h)) == hz.HZ_EINVAL
