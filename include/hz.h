@@ -108,6 +108,9 @@ typedef struct {
   double reorth_eta;     /* classical Gram-Schmidt runs a second pass when the orthogonalised
                             vector keeps less than reorth_eta of its norm ("twice is enough"
                             test), default 0.1; 1 = always two passes, 0 = one pass */
+  int graphs;            /* 1 (default): the coarse solves below the first level whose whole
+                            subtree runs on the device (MADP: level 3) are captured once per
+                            batch size as a CUDA graph and replayed; 0: launched one by one */
   int autotune;          /* 1 (default): with device_gmres = 1, time the tile-owned and the
                             slice-distributed GMRES forms once per level shape (process-wide
                             cache, at hz_setup) and keep the faster; 0: take the tile-owned

@@ -51,7 +51,7 @@ class HzConfig(ctypes.Structure):
         ("mg_max_level", ctypes.c_int), ("mg_omega", ctypes.c_double), ("mg_nu1", ctypes.c_int),
         ("mg_nu2", ctypes.c_int), ("mg_coarsest_side", ctypes.c_int), ("max_rhs", ctypes.c_int),
         ("timeout_s", ctypes.c_double), ("device_gmres", ctypes.c_int), ("reorth_eta", ctypes.c_double),
-        ("autotune", ctypes.c_int),
+        ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
     ]
 
 

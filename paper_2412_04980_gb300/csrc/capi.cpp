@@ -65,6 +65,7 @@ int hz_config_init(hz_config* c) {
   c->device_gmres = 1;
   c->reorth_eta = 0.1;
   c->autotune = 1;
+  c->graphs = 1;
   return HZ_OK;
 }
 
@@ -85,6 +86,7 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (!(c.timeout_s > 0)) return bad("timeout_s must be positive");
   if (!(c.reorth_eta >= 0 && c.reorth_eta <= 1)) return bad("reorth_eta must be in [0, 1]");
   if (c.autotune != 0 && c.autotune != 1) return bad("autotune must be 0 or 1");
+  if (c.graphs != 0 && c.graphs != 1) return bad("graphs must be 0 or 1");
   if (c.device_gmres < 0 || c.device_gmres > 4) return bad("device_gmres must be 0, 1, 2, 3 or 4");
   if (g.bc == HZ_BC_DIRICHLET && c.levels != 1) return bad("Dirichlet grids support the level-1 operator only");
   int nx = g.nx, ny = g.ny;

@@ -567,6 +567,19 @@ int setup(Handle* h, const double* k_dev) {
   h->st.assign(nb, RhsStats());
   CK(cudaStreamSynchronize(h->ctx.s));
   if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_gmres(h));
+  // the first level >= 3 from which every level runs one-iteration device cycles and a device
+  // CSLP inverse (multigrid or persistent GMRES): its coarse solve issues no host decision
+  if (cfg.graphs) {
+    for (int l = ml; l >= 3; --l) {
+      const Level& L = h->lv[l - 1];
+      const bool dev_cslp = l <= cfg.mg_max_level || L.ggrid > 0 || L.gcl > 0 || L.gtiles > 0;
+      if (!(L.cap == 1 && L.m1cnt && dev_cslp)) break;
+      h->graph_level = l;
+    }
+    h->graph_exec.assign(nb, nullptr);
+    h->graph_launches.assign(nb, 0);
+    if (h->graph_level > 0) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+  }
   return HZ_OK;
 }
 
@@ -658,6 +671,11 @@ int autotune_gmres(Handle* h) {
 
 void destroy(Handle* h) {
   cudaStreamSynchronize(h->ctx.s);
+  for (auto g : h->graph_exec)
+    if (g) cudaGraphExecDestroy(g);
+  h->graph_exec.clear();
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  h->capture_stream = nullptr;
   for (auto& L : h->lv) {
     free_scalars(L.sc);
     free_scalars(L.scg);
@@ -1024,6 +1042,49 @@ int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add,
   return cslp_gmres(h, l, rtil, out, nb, nullptr);
 }
 
+// coarse_solve(l) through a CUDA graph when level l's whole subtree runs on the device: captured
+// on first use for this batch size, replayed afterwards.  Profiling runs it eagerly (the event
+// pairs of the per-family timers are host-side records).  A capture the runtime refuses falls
+// back to launching eagerly for the rest of the handle's life.
+static int coarse_solve_graph(Handle* h, int l, int nb) {
+  bool profiling = false;
+  for (int f = 0; f < F_COUNT; ++f) profiling |= h->prof.on[f];
+  if (l != h->graph_level || h->graph_failed || profiling || nb < 1 || nb > (int)h->graph_exec.size())
+    return coarse_solve(h, l, nb);
+  cudaGraphExec_t& ex = h->graph_exec[nb - 1];
+  if (!ex) {
+    // capture on the handle's private stream (the caller's stream may be the legacy default
+    // stream, which cannot be captured); nothing runs during the capture
+    cudaStream_t s = h->capture_stream;
+    const long long l0 = h->prof.total_launches;
+    cudaGraph_t g = nullptr;
+    if (!s || cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graph_failed = true;
+      return coarse_solve(h, l, nb);
+    }
+    const cudaStream_t user = h->ctx.s;
+    h->ctx.s = s;
+    const int st = coarse_solve(h, l, nb);
+    h->ctx.s = user;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != HZ_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      ex = nullptr;
+      h->graph_failed = true;
+      h->prof.total_launches = l0;
+      return coarse_solve(h, l, nb);
+    }
+    cudaGraphDestroy(g);
+    h->graph_launches[nb - 1] = h->prof.total_launches - l0;
+    h->prof.total_launches = l0;
+  }
+  CK(cudaGraphLaunch(ex, h->ctx.s));
+  h->prof.total_launches += h->graph_launches[nb - 1];
+  return HZ_OK;
+}
+
 // x = P v at level l (Algorithm 1 lines 5-15).  v has dtype dv; x has dtype lv[l-1].dx.
 int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
   LevelTag tag(h->ctx, l);
@@ -1040,7 +1101,7 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
   }
   Level& C = h->lv[l];
   CK(launch_defl_restrict(c, dv, C.dvec, L.nx, L.ny, v, C.b, nb));                 // line 5
-  CS(coarse_solve(h, l + 1, nb));                                                  // lines 6-10
+  CS(coarse_solve_graph(h, l + 1, nb));                                            // lines 6-10
   CK(launch_defl_prolong_resid(c, L.opA(L.dpre), L.dpre, dv, C.x, C.nx, C.ny, v, L.t, L.rt, nb));  // 11-13
   return cslp_inverse(h, l, L.rt, xout, L.t, nb);                                  // lines 14-15
 }

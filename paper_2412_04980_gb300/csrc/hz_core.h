@@ -93,6 +93,13 @@ struct Handle {
   Scalars outer_sc;                          // true-residual norms
   void* rres = nullptr;                      // level-1 true residual buffer (C128)
   int* derr = nullptr;                       // device breakdown flag of the device-side cycles
+  // CUDA graph of the coarse solve at level graph_level (every level from there down runs on the
+  // device without host decisions), one per batch size; launches it replays, for the counter
+  int graph_level = 0;
+  bool graph_failed = false;
+  cudaStream_t capture_stream = nullptr;     // private stream the graphs are captured on
+  std::vector<cudaGraphExec_t> graph_exec;   // index nb - 1
+  std::vector<long long> graph_launches;
 };
 
 // allocation helpers (track for hz_destroy)

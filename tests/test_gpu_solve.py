@@ -112,3 +112,24 @@ def test_autotuned_forms_solve_alike(hz, autotune):
     assert st[0]["status"] == 0 and st[0]["true_relres"] <= 1e-6
     assert abs(st[0]["outer_iterations"] - st4[0]["outer_iterations"]) <= 1
     assert rel2(host(u), host(u4)) <= 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_graph_replay_equals_eager(hz, nrhs):
+    """Levels 3-5 of a 513^2 hierarchy run one-iteration device cycles, so the level-3 coarse
+    solve is captured as a CUDA graph on first use and replayed afterwards: the solutions and
+    statistics equal the eagerly launched solve bitwise, on the capture call and on replays."""
+    p = mp.random_field(513, 5.0, seed=11, kh_max=0.3, levels=5, negdef_from_level=4, nsrc=nrhs)
+    cfg = dict(levels=5, negdef_from_level=4, precision="mixed", max_rhs=nrhs)
+    eager = hz.Helmholtz(dev(p.k), p.h, graphs=0, **cfg)
+    graph = hz.Helmholtz(dev(p.k), p.h, graphs=1, **cfg)
+    b = dev(p.b if nrhs > 1 else p.b[0])
+    ue, ste = eager.solve(b, tol=1e-6)
+    for _ in range(2):  # capture, then replay
+        ug, stg = graph.solve(b, tol=1e-6)
+        assert np.array_equal(host(ug), host(ue))
+        for a, c in zip(stg, ste):
+            assert a["outer_iterations"] == c["outer_iterations"]
+            assert a["level_iterations"] == c["level_iterations"]
+            assert a["cslp_gmres_iterations"] == c["cslp_gmres_iterations"]
+    assert all(s["status"] == 0 for s in ste)
