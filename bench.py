@@ -72,8 +72,8 @@ def parse():
                     help="capture the device-only coarse solves as CUDA graphs (library default if omitted)")
     ap.add_argument("--no-live-profile", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--device-gmres", type=int, default=None, choices=[0, 1, 2, 3, 4],
-                    help="GMRES CSLP form: 1 cluster/grid by level size, 2 cooperative grid, 3 cluster, "
-                         "0 host-driven")
+                    help="GMRES CSLP form: 1 automatic (cluster, tile-owned or slice grid by level "
+                         "and batch), 2 cooperative grid, 3 cluster, 4 slice grid, 0 host-driven")
     ap.add_argument("--reorth-eta", type=float, default=None,
                     help="Gram-Schmidt reorthogonalisation threshold (library default if omitted)")
     ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply", "levelop", "prolong"],
