@@ -115,6 +115,15 @@ typedef struct {
                             slice-distributed GMRES forms once per level shape (process-wide
                             cache, at hz_setup) and keep the faster; 0: take the tile-owned
                             form wherever it fits */
+  int cycle_m;           /* deflated FGMRES iterations m on each level 3 .. ml-1 that has no
+                            tolerance (Algorithm 1's m on the coarser levels, Section 3.2):
+                            1 (default) = V-cycle, 2 = W-cycle; >= 1 */
+  double level_tol[HZ_MAX_LEVELS]; /* [l-1] for levels 3 .. ml-1: > 0 solves level l to this
+                            relative residual with at most l2_maxit iterations instead of
+                            cycle_m iterations (tolerances on the coarser indefinite levels,
+                            Sections 4.3.3 and 4.5); default 0; entries of other levels must be 0.
+                            Level 2 keeps l2_tol / l2_maxit: l2_tol = 0 runs exactly l2_maxit
+                            iterations (l2_maxit = 1: MADP-v1's V-cycle, Section 4.3.1) */
 } hz_config;
 
 /* Per-right-hand-side solve statistics. */

@@ -14,8 +14,13 @@ Algorithm 1 lines 5-14:
 
 MADP schedule (Section 4.4; Section 4.1 for the coarsest level):
 * level 1: FGMRES(restart) to relative residual ``tol`` (1e-6, Section 4);
-* level 2 (when it is not the coarsest): tolerance 0.3, at most 30 iterations;
-* levels 3 .. ml-1: exactly one iteration;
+* level 2 (when it is not the coarsest): tolerance 0.3, at most 30 iterations
+  (``l2_tol = 0`` runs exactly ``l2_maxit`` iterations: MADP-v1's V-cycle,
+  Section 4.3.1, is ``l2_tol = 0, l2_maxit = 1``);
+* levels 3 .. ml-1: exactly ``cycle_m`` iterations, Algorithm 1's m on the
+  coarser levels (1 = V-cycle, 2 = W-cycle, Section 3.2), or, for a level
+  listed in ``level_tol``, that relative tolerance within ``l2_maxit``
+  iterations (tolerances on the coarser levels, Sections 4.3.3 and 4.5);
 * coarsest level ml: one iteration if it is treated as negative definite,
   otherwise tolerance 1e-1, at most floor(6 N_ml^(1/4)) iterations;
 * CSLP inverse: multigrid V-cycle on levels 1 and 2; unpreconditioned GMRES to
@@ -64,6 +69,8 @@ class MADPConfig:
     mg_nu1: int = 1
     mg_nu2: int = 1
     mg_coarsest_side: int = 20
+    cycle_m: int = 1                # iterations on levels 3 .. ml-1 without a tolerance
+    level_tol: dict = field(default_factory=dict)   # level (3 .. ml-1) -> relative tolerance
 
 
 @dataclass
@@ -148,7 +155,12 @@ class Hierarchy:
                 tol, cap = cfg.coarsest_tol, krylov_cap(cfg.c_it, self.nodes(l))
             u, res = fgmres(lambda x: self.A(l, x), b, lambda v: self.cslp_inverse(l, v), tol, cap)
         else:
-            tol, cap = (cfg.l2_tol, cfg.l2_maxit) if l == 2 else (0.0, 1)
+            if l == 2:
+                tol, cap = cfg.l2_tol, cfg.l2_maxit
+            elif cfg.level_tol.get(l, 0.0) > 0:
+                tol, cap = cfg.level_tol[l], cfg.l2_maxit
+            else:
+                tol, cap = 0.0, cfg.cycle_m
             u, res = fgmres(lambda x: self.A(l, x), b, lambda v: self.precond(l, v), tol, cap)
         self.stats.add(self.stats.level_iterations, l, res.iterations)
         self.stats.add(self.stats.level_calls, l, 1)

@@ -51,7 +51,8 @@ class HzConfig(ctypes.Structure):
         ("mg_max_level", ctypes.c_int), ("mg_omega", ctypes.c_double), ("mg_nu1", ctypes.c_int),
         ("mg_nu2", ctypes.c_int), ("mg_coarsest_side", ctypes.c_int), ("max_rhs", ctypes.c_int),
         ("timeout_s", ctypes.c_double), ("device_gmres", ctypes.c_int), ("reorth_eta", ctypes.c_double),
-        ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
+        ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("cycle_m", ctypes.c_int),
+        ("level_tol", ctypes.c_double * HZ_MAX_LEVELS),
     ]
 
 
@@ -176,6 +177,14 @@ def config(**kw) -> HzConfig:
     for k, v in kw.items():
         if not hasattr(c, k):
             raise KeyError(k)
+        if k == "level_tol":
+            # {level: tolerance} for levels 3 .. levels-1 (entry level-1 of the C array)
+            arr = (ctypes.c_double * HZ_MAX_LEVELS)()
+            for lev, tol in dict(v).items():
+                if not 1 <= int(lev) <= HZ_MAX_LEVELS:
+                    raise ValueError(f"level_tol: level {lev} out of range")
+                arr[int(lev) - 1] = float(tol)
+            v = arr
         setattr(c, k, v)
     return c
 

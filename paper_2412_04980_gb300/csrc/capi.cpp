@@ -66,6 +66,7 @@ int hz_config_init(hz_config* c) {
   c->reorth_eta = 0.1;
   c->autotune = 1;
   c->graphs = 1;
+  c->cycle_m = 1;
   return HZ_OK;
 }
 
@@ -88,6 +89,13 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (c.autotune != 0 && c.autotune != 1) return bad("autotune must be 0 or 1");
   if (c.graphs != 0 && c.graphs != 1) return bad("graphs must be 0 or 1");
   if (c.device_gmres < 0 || c.device_gmres > 4) return bad("device_gmres must be 0, 1, 2, 3 or 4");
+  if (c.cycle_m < 1) return bad("cycle_m must be >= 1");
+  if (!(c.l2_tol >= 0 && c.l2_tol < 1)) return bad("l2_tol must be in [0, 1)");
+  for (int l = 1; l <= HZ_MAX_LEVELS; ++l) {
+    const double t = c.level_tol[l - 1];
+    if (!(t >= 0 && t < 1)) return bad("level_tol entries must be in [0, 1)");
+    if (t > 0 && (l < 3 || l >= c.levels)) return bad("level_tol is set for levels 3 .. levels-1 only");
+  }
   if (g.bc == HZ_BC_DIRICHLET && c.levels != 1) return bad("Dirichlet grids support the level-1 operator only");
   int nx = g.nx, ny = g.ny;
   for (int l = 1; l < c.levels; ++l) {

@@ -151,6 +151,36 @@ int wait_event(Handle* h, cudaEvent_t ev) {
 
 static int krylov_cap(double c_it, size_t nodes) { return (int)std::floor(c_it * std::pow((double)nodes, 0.25)); }
 
+// Deflated FGMRES schedule of level l (Algorithm 1 with the MADP schedule of Section 4.4 and its
+// variants): the relative tolerance (0 = run exactly `cap` iterations) and the iteration cap.
+//   level 1      : tolerance of the solve call, cap = restart length (set by the caller);
+//   level ml     : one iteration when negative definite, else coarsest_tol within the Krylov cap
+//                  (Section 4.1);
+//   level 2      : l2_tol within l2_maxit;
+//   levels 3..ml-1: level_tol[l-1] within l2_maxit where set (Sections 4.3.3, 4.5), else
+//                  exactly cycle_m iterations (m = 1 V-cycle, m = 2 W-cycle, Section 3.2).
+static void level_schedule(const hz_config& cfg, int l, size_t nodes, double* tol, int* cap) {
+  const int ml = cfg.levels;
+  if (l == 1) {
+    *tol = 0.0;
+    *cap = cfg.restart;
+  } else if (l == ml) {
+    const bool negdef = cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level;
+    *tol = negdef ? 0.0 : cfg.coarsest_tol;
+    *cap = negdef ? 1 : krylov_cap(cfg.c_it, nodes);
+  } else if (l == 2) {
+    *tol = cfg.l2_tol;
+    *cap = cfg.l2_maxit;
+  } else if (cfg.level_tol[l - 1] > 0) {
+    *tol = cfg.level_tol[l - 1];
+    *cap = cfg.l2_maxit;
+  } else {
+    *tol = 0.0;
+    *cap = cfg.cycle_m;
+  }
+  *cap = std::max(*cap, 1);
+}
+
 OpDesc Level::opA(int dt) const {
   OpDesc d;
   d.nx = nx;
@@ -341,10 +371,8 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
     const size_t eb = (l == 1 || !mixed) ? 16 : 8, ep = mixed ? 8 : 16, ex = ep;
     total += n * 12;  // k in FP64 and FP32
     int cap;
-    if (l == 1) cap = cfg.restart;
-    else if (l == ml) cap = (cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level) ? 1 : krylov_cap(cfg.c_it, n);
-    else cap = (l == 2) ? cfg.l2_maxit : 1;
-    cap = std::max(cap, 1);
+    double tol_unused;
+    level_schedule(cfg, l, n, &tol_unused, &cap);
     maxnv = std::max(maxnv, (size_t)cap + 1);
     total += (cap + 1) * bn * eb + cap * bn * ex + bn * eb + 3 * bn * ep + (l >= 2 ? 2 * bn * eb : 0) + scal(cap);
     if (l >= 2 && cap == 1) total += sizeof(int) * 2 * (size_t)nb;  // one-iteration counters
@@ -434,15 +462,7 @@ int setup(Handle* h, const double* k_dev) {
     Level& L = h->lv[l - 1];
     const size_t eb = elem_bytes(L.dvec), ep = elem_bytes(L.dpre), ex = elem_bytes(L.dx);
     const size_t bn = (size_t)nb * L.n;
-    if (l == 1) {
-      L.cap = cfg.restart;
-    } else if (l == ml) {
-      bool negdef = cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level;
-      L.cap = negdef ? 1 : krylov_cap(cfg.c_it, L.n);
-    } else {
-      L.cap = (l == 2) ? cfg.l2_maxit : 1;
-    }
-    if (L.cap < 1) L.cap = 1;
+    level_schedule(cfg, l, L.n, &L.tol, &L.cap);
     maxnv = std::max(maxnv, (size_t)L.cap + 1);
     CS(dalloc(h, &L.V, (L.cap + 1) * bn * eb));
     CS(dalloc(h, &L.X, L.cap * bn * ex));
@@ -1144,15 +1164,7 @@ static int cycle_m1_device(Handle* h, Level& L, int nb, const std::function<int(
 int coarse_solve(Handle* h, int l, int nb) {
   LevelTag tag(h->ctx, l);
   Level& L = h->lv[l - 1];
-  const hz_config& cfg = h->cfg;
-  const int ml = cfg.levels;
-  double tol;
-  if (l == ml) {
-    bool negdef = cfg.negdef_from_level > 0 && l >= cfg.negdef_from_level;
-    tol = negdef ? 0.0 : cfg.coarsest_tol;
-  } else {
-    tol = (l == 2) ? cfg.l2_tol : 0.0;
-  }
+  const double tol = L.tol;
   CK(cudaMemsetAsync(L.x, 0, (size_t)nb * L.n * elem_bytes(L.dvec), h->ctx.s));
   OpDesc A = L.opA(L.dvec);
   auto op = [&](const void* xin, void* wout) -> int {

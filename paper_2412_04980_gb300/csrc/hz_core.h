@@ -41,6 +41,7 @@ struct Level {
   int ninv = 0;
   // deflated / CSLP FGMRES of this level
   int cap = 0;                               // iteration cap per cycle
+  double tol = 0.0;                          // relative tolerance of a coarse solve (0 = exactly cap iterations)
   void* V = nullptr;                         // (cap + 1) batches, dvec
   void* X = nullptr;                         // cap batches, dx
   void* w = nullptr;                         // dvec

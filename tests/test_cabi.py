@@ -148,6 +148,11 @@ def test_config_validation_of_new_fields(L):
     import paper_2412_04980_gb300 as hz
     h = ctypes.c_void_p()
     g = hz.HzGrid(9, 9, 0.1, 0)
-    for bad in (dict(device_gmres=5), dict(device_gmres=-1), dict(autotune=2), dict(reorth_eta=1.5)):
+    for bad in (dict(device_gmres=5), dict(device_gmres=-1), dict(autotune=2), dict(reorth_eta=1.5),
+                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1),
+                dict(levels=3, level_tol={2: 0.1}), dict(levels=3, level_tol={3: 0.1}),
+                dict(levels=4, level_tol={3: 1.0}), dict(levels=4, level_tol={3: float("nan")})):
         c = hz.config(**bad)
         assert L.hz_setup(ctypes.byref(g), ctypes.c_void_p(1), ctypes.byref(c), None, ctypes.byref(h)) == hz.HZ_EINVAL
+        msg = L.hz_last_error().decode()
+        assert "coarsened" not in msg, (bad, msg)       # refused for the field itself

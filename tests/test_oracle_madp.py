@@ -77,3 +77,90 @@ def test_deeper_levels_take_one_iteration():
     assert st.level_iterations[4] == st.level_calls[4]
     assert st.level_calls[3] == st.level_iterations[2]
     assert st.true_relres <= 1e-6
+
+
+def _level_operator(hier, l):
+    ny, nx = hier.shapes[l - 1]
+    return assemble(lambda u: hier.A(l, u), (ny, nx), 3).toarray()
+
+
+@pytest.mark.parametrize("variant", ["cycle_m", "level_tol"])
+def test_intermediate_level_with_enough_iterations_is_exact(variant):
+    """Four levels on 17x17 nodes (level 3: 5x5 = 25 unknowns).  FGMRES terminates
+    with the exact solution after as many iterations as unknowns, so level 3 solved
+    with m = 25 iterations (Algorithm 1's m, Section 3.2) or to a 1e-12 tolerance
+    within 25 iterations (Sections 4.3.3, 4.5) must make the level-2 preconditioner
+    (Algorithm 1 lines 5-15) agree with the one built on a dense inverse of A_3."""
+    n, h = 17, 1.0 / 16
+    k = mp.random_k(n, n, seed=11, kmin=4.0, kmax=9.0)
+    if variant == "cycle_m":
+        cfg = MADPConfig(levels=4, cycle_m=25)
+    else:
+        cfg = MADPConfig(levels=4, level_tol={3: 1e-12}, l2_maxit=25)
+    hier = Hierarchy(k, h, cfg)
+    v = mp.random_complex(hier.shapes[1], seed=12)
+    x = hier.precond(2, v)
+    its = hier.stats.level_iterations[3]
+    assert its == 25 if variant == "cycle_m" else 2 <= its <= 25     # the level-3 solve iterated
+    exact = Hierarchy(k, h, MADPConfig(levels=4))
+    A3 = _level_operator(exact, 3)
+    exact.coarse_solve = lambda l, b: np.linalg.solve(A3, b.ravel()).reshape(b.shape)
+    ref = exact.precond(2, v)
+    np.testing.assert_allclose(x, ref, rtol=0, atol=1e-7 * np.abs(ref).max())
+
+
+def test_w_cycle_counts_and_solution():
+    """W-cycle (m = 2 on levels 3 .. ml-1, Section 3.2): every level-3 and level-4
+    solve takes exactly two iterations, each of which calls the next level once;
+    level 2 keeps its tolerance schedule; the result solves the system."""
+    p = mp.random_field(129, 5.0, seed=3, kh_max=0.3, levels=5, negdef_from_level=4)
+    cfg = MADPConfig(levels=5, negdef_from_level=4, cycle_m=2)
+    u, st = Hierarchy(p.k, p.h, cfg).solve(p.b[0])
+    for l in (3, 4):
+        assert st.level_iterations[l] == 2 * st.level_calls[l]
+        assert st.level_calls[l + 1] == st.level_iterations[l]
+    assert st.level_calls[3] == st.level_iterations[2]
+    assert st.level_iterations[5] == st.level_calls[5]          # negative-definite coarsest
+    assert st.level_iterations[2] != 2 * st.level_calls[2] or st.level_iterations[2] <= 2 * st.level_calls[2]
+    A = assemble(lambda x: apply_helmholtz(x, p.k, p.h), (p.ny, p.nx), 1).tocsc()
+    b = p.b[0]
+    rel = np.linalg.norm(b.ravel() - A @ u.ravel()) / np.linalg.norm(b)
+    assert rel <= 1e-6 and abs(rel - st.true_relres) <= 1e-9
+
+
+def test_level_tolerance_is_met_or_capped():
+    """Tolerances on levels 3 and 4 (Section 4.5's extension of MADP-v3): every
+    solve there ends with ||b - A_l u|| <= tol ||b|| or at the l2_maxit cap."""
+    p = mp.random_field(65, 5.0, seed=3, kh_max=0.3, levels=5, negdef_from_level=5)
+    cfg = MADPConfig(levels=5, negdef_from_level=5, l2_tol=0.1, level_tol={3: 0.1, 4: 0.1}, l2_maxit=8)
+    hier = Hierarchy(p.k, p.h, cfg)
+    inner = hier.coarse_solve
+    seen = []
+
+    def checked(l, b):
+        before = hier.stats.level_iterations.get(l, 0)
+        u = inner(l, b)
+        its = hier.stats.level_iterations[l] - before
+        if l in (2, 3, 4):
+            rel = np.linalg.norm(b - hier.A(l, u)) / np.linalg.norm(b)
+            assert rel <= 0.1 * (1 + 1e-8) or its == 8, (l, rel, its)
+            seen.append((l, its))
+        return u
+
+    hier.coarse_solve = checked
+    u, st = hier.solve(p.b[0])
+    assert st.true_relres <= 1e-6
+    assert {l for l, _ in seen} == {2, 3, 4}
+    assert any(its > 1 for l, its in seen if l in (3, 4))     # the tolerance, not one iteration
+
+
+def test_madp_v1_schedule():
+    """MADP-v1 (Section 4.3.1): CSLP by GMRES on every level with the small shift
+    beta2 = 1/k and one iteration on every level between the finest and the
+    coarsest (l2_tol = 0, l2_maxit = 1)."""
+    p = mp.mp1b(64, 20.0)
+    cfg = MADPConfig(levels=3, beta2=1.0 / 20.0, mg_max_level=0, l2_tol=0.0, l2_maxit=1)
+    u, st = Hierarchy(p.k, p.h, cfg).solve(p.b[0])
+    assert st.level_iterations[2] == st.level_calls[2] == st.outer_iterations
+    assert set(st.cslp_gmres_iterations) == {1, 2, 3}
+    assert st.true_relres <= 1e-6
