@@ -55,6 +55,38 @@ SOLVE_COUNTS = {
                     "cslp_gmres_iterations": [0, 0, 13557, 11436, 20375, 27242, 0, 0, 0, 0]},
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# Coarse-level schedules (hz_config fields): the paper's final MADP and the variants it studies.
+SCHEDULES = {
+    "madp": "MADP (Section 4.4): multigrid CSLP on levels 1-2, level 2 to 0.3, one iteration below",
+    "madp_w": "MADP with a W-cycle: two iterations on every level between level 2 and the coarsest "
+              "(Algorithm 1's m = 2, Section 3.2)",
+    "madp_v3": "MADP-v3 (Section 4.4): as MADP with level 2 solved to 0.1",
+    "madp_v3_tol": "MADP-v3 with tolerance 0.1 on levels 3 and 4 as well (Section 4.5)",
+    "madp_v1": "MADP-v1 (Section 4.3.1): GMRES CSLP on every level, beta2 = 1/k_dim,max, one iteration "
+               "on every level between the finest and the coarsest",
+    "madp_v2": "MADP-v2 (Section 4.3.3): as MADP-v1 with level 2 solved to 0.1",
+}
+
+
+def schedule_config(name: str, p) -> dict:
+    """hz_config fields of a schedule for problem p; beta2 = 1/k_dim with the dimensionless
+    wavenumber k_dim = k_max sqrt(L_x L_y) (Section 4.3.2)."""
+    import numpy as np
+    ml = p.levels
+    kdim = float(np.max(p.k)) * math.sqrt((p.nx - 1) * p.h * (p.ny - 1) * p.h)
+    if name == "madp":
+        return {}
+    if name == "madp_w":
+        return {"cycle_m": 2}
+    if name == "madp_v3":
+        return {"l2_tol": 0.1}
+    if name == "madp_v3_tol":
+        return {"l2_tol": 0.1, "level_tol": {l: 0.1 for l in (3, 4) if l < ml}}
+    if name == "madp_v1":
+        return {"mg_max_level": 0, "beta2": 1.0 / kdim, "l2_tol": 0.0, "l2_maxit": 1}
+    if name == "madp_v2":
+        return {"mg_max_level": 0, "beta2": 1.0 / kdim, "l2_tol": 0.1}
+    raise ValueError(name)
 
 
 def parse():
@@ -70,6 +102,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--graphs", type=int, default=None, choices=[0, 1],
                     help="capture the device-only coarse solves as CUDA graphs (library default if omitted)")
+    ap.add_argument("--schedule", default="madp", choices=sorted(SCHEDULES),
+                    help="coarse-level schedule: " + "; ".join(f"{k}: {v}" for k, v in SCHEDULES.items()))
     ap.add_argument("--no-live-profile", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--device-gmres", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="GMRES CSLP form: 1 automatic (cluster, tile-owned or slice grid by level "
@@ -112,7 +146,9 @@ def oracle_sample(workload: str, counts: dict) -> dict:
     from oracle.multigrid import CSLPMultigrid
 
     p = mp.named(workload)
-    cfg = MADPConfig(levels=p.levels, negdef_from_level=p.negdef_from_level)
+    sched = schedule_config(counts.get("schedule", "madp"), p)
+    cfg = MADPConfig(levels=p.levels, negdef_from_level=p.negdef_from_level,
+                     mg_max_level=sched.get("mg_max_level", 2))
     ml = p.levels
     shift = complex(cfg.beta1, cfg.beta2)
     t_total = time.perf_counter()
@@ -540,10 +576,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        counts = load_counts(args.workload)
+        counts = load_counts(args.workload) if args.schedule == "madp" else None
         if counts is None:
             print(json.dumps({"impl": "reference", "unavailable": "no per-solve iteration counts recorded for "
-                                                                   f"{args.workload}"}))
+                                                                   f"{args.workload} ({args.schedule})"}))
             return
         times = []
         res = None
@@ -584,6 +620,7 @@ def main():
         extra["device_gmres"] = args.device_gmres
     if args.graphs is not None:
         extra["graphs"] = args.graphs
+    extra.update(schedule_config(args.schedule, p))
     H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision,
                      **extra)
     u = torch.empty_like(b)
@@ -675,7 +712,7 @@ def main():
     counts = {"outer": stats[-1]["outer_iterations"], "level_iterations": stats[-1]["level_iterations"],
               "level_calls": stats[-1]["level_calls"],
               "cslp_gmres_iterations": stats[-1]["cslp_gmres_iterations"],
-              "cslp_gmres_reorth": stats[-1]["cslp_gmres_reorth"]}
+              "cslp_gmres_reorth": stats[-1]["cslp_gmres_reorth"], "schedule": args.schedule}
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:
@@ -710,7 +747,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
                    "levels": p.levels, "nrhs": 1, "precision": args.precision, "reorth_eta": H.cfg.reorth_eta,
-                   "device_gmres": H.cfg.device_gmres,
+                   "device_gmres": H.cfg.device_gmres, "schedule": args.schedule,
                    "l2": f"inputs larger than L2: b is {nbytes / 1e6:.0f} MB and the solver touches "
                          f"{mem_gb:.1f} GB of workspace per solve",
                    "parallelism": f"replicas x{world}"},

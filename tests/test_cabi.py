@@ -93,6 +93,9 @@ def test_estimate_bytes_host_only(L):
     # FP64 vectors never take the cluster form
     assert e(513, levels=5, max_rhs=4, device_gmres=3) == e(513, levels=5, max_rhs=4, device_gmres=2)
     assert e(513, levels=5, precision="mixed") < e(513, levels=5, precision="fp64")
+    # a level with m iterations or a tolerance keeps a larger Krylov basis than a one-iteration level
+    assert e(513, levels=5) < e(513, levels=5, cycle_m=2) < e(513, levels=5, cycle_m=3)
+    assert e(513, levels=5, cycle_m=2) < e(513, levels=5, level_tol={3: 0.1})
     assert L.hz_estimate_bytes(None, None, None) == hz.HZ_EINVAL
 
 

@@ -133,3 +133,51 @@ def test_graph_replay_equals_eager(hz, nrhs):
             assert a["level_iterations"] == c["level_iterations"]
             assert a["cslp_gmres_iterations"] == c["cslp_gmres_iterations"]
     assert all(s["status"] == 0 for s in ste)
+
+
+# Coarse-level schedule variants (Algorithm 1's m and per-level tolerances, Sections 3.2, 4.3, 4.5).
+_VARIANTS = {
+    # W-cycle: two deflated FGMRES iterations on level 3 of four
+    "w_cycle": ("field257", dict(levels=4, negdef_from_level=4, cycle_m=2)),
+    # tolerance 0.1 on levels 2 and 3 instead of one iteration on level 3
+    "level_tol": ("field257", dict(levels=4, negdef_from_level=4, l2_tol=0.1, level_tol={3: 0.1})),
+    # MADP-v1: GMRES CSLP on every level, beta2 = 1/k, one iteration on level 2
+    "madp_v1": ("mp1b129", dict(levels=3, mg_max_level=0, beta2=1 / 20.0, l2_tol=0.0, l2_maxit=1)),
+    # MADP-v2: as v1 with tolerance 0.1 on level 2
+    "madp_v2": ("mp1b129", dict(levels=3, mg_max_level=0, beta2=1 / 20.0, l2_tol=0.1)),
+}
+
+
+def _variant_problem(name):
+    if name == "field257":
+        return mp.random_field(257, 5.0, seed=3, kh_max=0.3, levels=4, negdef_from_level=4)
+    return mp.mp1b(128, 20.0)
+
+
+@pytest.mark.parametrize("variant,precision", [("w_cycle", "fp64"), ("w_cycle", "mixed"), ("level_tol", "fp64"),
+                                               ("madp_v1", "mixed"), ("madp_v2", "mixed")])
+def test_solve_schedule_variants(hz, variant, precision):
+    """Each schedule variant reaches the 1e-6 residual with the oracle's solution, within one
+    outer iteration of it, and keeps the variant's per-level counts: m iterations per call on a
+    level without a tolerance, every call of level l+1 issued by one iteration of level l."""
+    pname, kw = _VARIANTS[variant]
+    p = _variant_problem(pname)
+    ref, rst = Hierarchy(p.k, p.h, MADPConfig(**kw)).solve(p.b[0])
+    H = hz.Helmholtz(dev(p.k), p.h, precision=precision, **kw)
+    u, st = H.solve(dev(p.b[0]), tol=1e-6)
+    st = st[0]
+    u = host(u)
+    r = p.b[0] - apply_helmholtz(u, p.k, p.h)
+    true_rel = np.linalg.norm(r) / np.linalg.norm(p.b[0])
+    assert st["status"] == 0 and true_rel <= 1e-6
+    assert rel2(u, ref) <= 1e-5
+    assert abs(st["outer_iterations"] - rst.outer_iterations) <= 1
+    lit, lca = st["level_iterations"], st["level_calls"]
+    ml = kw["levels"]
+    assert lca[1] == st["outer_iterations"] or ml == 1
+    for l in range(2, ml):
+        assert lca[l] == lit[l - 1]                       # level l+1 called once per level-l iteration
+    if variant == "w_cycle":
+        assert lit[2] == 2 * lca[2]
+    if variant == "madp_v1":
+        assert lit[1] == lca[1]
