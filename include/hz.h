@@ -111,10 +111,10 @@ typedef struct {
   int graphs;            /* 1 (default): the coarse solves below the first level whose whole
                             subtree runs on the device (MADP: level 3) are captured once per
                             batch size as a CUDA graph and replayed; 0: launched one by one */
-  int autotune;          /* 1 (default): with device_gmres = 1, time the tile-owned and the
-                            slice-distributed GMRES forms once per level shape (process-wide
-                            cache, at hz_setup) and keep the faster; 0: take the tile-owned
-                            form wherever it fits */
+  int autotune;          /* 1 (default): with device_gmres = 1, time the tile-owned GMRES form at
+                            each fitting tile shape and the slice-distributed form once per
+                            level shape (process-wide cache, at hz_setup) and keep the fastest;
+                            0: take the tile-owned form with the most tiles wherever it fits */
   int cycle_m;           /* deflated FGMRES iterations m on each level 3 .. ml-1 that has no
                             tolerance (Algorithm 1's m on the coarser levels, Section 3.2):
                             1 (default) = V-cycle, 2 = W-cycle; >= 1 */

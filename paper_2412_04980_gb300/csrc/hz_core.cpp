@@ -604,24 +604,39 @@ int setup(Handle* h, const double* k_dev) {
 }
 
 // ------------------------------------------------------------------------------ autotuning
-// Per level shape (nx, ny, precision, stencil radius, iteration cap) the faster of the
-// tile-owned and the slice-distributed GMRES forms, measured once per process: both run
+// Per level shape (nx, ny, precision, stencil radius, iteration cap) the fastest GMRES form among
+// the tile-owned form at every fitting tile shape (fewer, larger tiles mean fewer CTAs at each
+// grid barrier) and the slice-distributed grid, measured once per process: each runs
 // min(cap, 24) iterations (tolerance 0) on a fixed pseudo-random right-hand side, twice, and the
 // second run's event time decides.  The workspace of the level is reused; statistics are reset.
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, bool> g_tune;  // -> tile-owned form wins
+// (nx, ny, precision, radius, cap) -> fastest form: tile shape (TX, TY), or (0, 0) for the
+// slice-distributed grid
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune;
+
+// tiles along a side of n nodes for tile width t (the last tile takes the remainder node)
+static int tile_count(int n, int t) { return n > 1 ? (n - 1 + t - 1) / t : 1; }
 }  // namespace
 
 int autotune_gmres(Handle* h) {
   for (auto& L : h->lv) {
     if (L.gtiles <= 0 || L.ggrid <= 0) continue;
     const auto key = std::make_tuple(L.nx, L.ny, L.dpre, L.R, L.capg);
+    auto adopt = [&](int TX, int TY) {
+      if (TX <= 0) {
+        L.gtiles = 0;  // slice-distributed grid
+        return;
+      }
+      L.gtx = TX;
+      L.gty = TY;
+      L.gtiles = tile_count(L.nx, TX) * tile_count(L.ny, TY);
+    };
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune.find(key);
       if (it != g_tune.end()) {
-        if (!it->second) L.gtiles = 0;
+        adopt(it->second.first, it->second.second);
         continue;
       }
     }
@@ -645,19 +660,31 @@ int autotune_gmres(Handle* h) {
     OpDesc M = L.opM(L.dpre, h->cfg.beta1, h->cfg.beta2);
     const int K = std::min(L.capg, 24);
     const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
+    // candidates: every fitting tile shape (at most as many tiles as the setup's default, whose
+    // partial-sum buffers are sized for it), then the slice-distributed grid (TX = 0)
+    int tx[5], ty[5];
+    const int ntile = gmres_tile_forms(L.dpre, L.R, L.nx, L.ny, L.capg, tx, ty, 4);
+    int nc = 0;
+    for (int i = 0; i < ntile; ++i)
+      if (tile_count(L.nx, tx[i]) * tile_count(L.ny, ty[i]) <= L.gtiles) {
+        tx[nc] = tx[i];
+        ty[nc++] = ty[i];
+      }
+    tx[nc] = 0;
+    ty[nc++] = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float ms[2] = {0, 0};
+    std::vector<float> ms(nc, 0.0f);
     int st = HZ_OK;
-    for (int form = 0; form < 2 && st == HZ_OK; ++form) {
+    for (int c = 0; c < nc && st == HZ_OK; ++c) {
       for (int rep = 0; rep < 2 && st == HZ_OK; ++rep) {
         st = status_of(cudaMemsetAsync(L.rt, 0, L.n * eb, h->ctx.s), "autotune");
         if (st) break;
         st = status_of(cudaEventRecord(e0, h->ctx.s), "autotune");
         if (st) break;
-        cudaError_t e = form == 0 ? launch_gmres_tile(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.gpartA, L.gpartB,
-                                                      L.gR, L.gst, K, 0.0, L.gtx, L.gty, eta2)
+        cudaError_t e = tx[c] > 0 ? launch_gmres_tile(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.gpartA, L.gpartB,
+                                                      L.gR, L.gst, K, 0.0, tx[c], ty[c], eta2)
                                   : launch_gmres_persistent(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.wg2, L.gpartA,
                                                             L.gpartB, L.gpstride, L.gR, L.gst, K, 0.0, L.ggrid, false,
                                                             1, eta2);
@@ -667,7 +694,7 @@ int autotune_gmres(Handle* h) {
         if (st) break;
         st = wait_event(h, e1);
         if (st) break;
-        st = status_of(cudaEventElapsedTime(&ms[form], e0, e1), "autotune");
+        st = status_of(cudaEventElapsedTime(&ms[c], e0, e1), "autotune");  // the second run counts
       }
     }
     cudaEventDestroy(e0);
@@ -681,10 +708,12 @@ int autotune_gmres(Handle* h) {
       set_error("a grid barrier of the persistent GMRES kernel exceeded its wait budget");
       return HZ_ETIMEOUT;
     }
-    const bool tile_wins = ms[0] <= ms[1];
-    if (!tile_wins) L.gtiles = 0;
+    int best = 0;
+    for (int c = 1; c < nc; ++c)
+      if (ms[c] < ms[best]) best = c;
+    adopt(tx[best], ty[best]);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = tile_wins;
+    g_tune[key] = {tx[best], ty[best]};
   }
   return HZ_OK;
 }

@@ -168,6 +168,8 @@ int gmres_max_grid(int dt, int R, int cap, size_t n);
 // Tile-owned form of the persistent GMRES: tile shape (*TX, *TY) for an nx x ny level and the
 // number of CTAs (one per tile), 0 if no shape gives every co-resident CTA at most one tile.
 int gmres_tile_form(int dt, int R, int nx, int ny, int cap, int* TX, int* TY);
+// Every fitting tile shape of the tile-owned form, most tiles first; returns the count (<= maxc).
+int gmres_tile_forms(int dt, int R, int nx, int ny, int cap, int* TX, int* TY, int maxc);
 // x += GMRES(M, b) for one right-hand side with the tile-owned form (grid = tiles; w0: n
 // elements; partA/partB: 2 (cap + 1) + 2 values per CTA; Rg, st as launch_gmres_persistent).
 cudaError_t launch_gmres_tile(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,

@@ -1125,17 +1125,17 @@ size_t tile_form_smem(int TX, int TY, int cap) {
   return tile_smem_bytes<T, R>(TX + 1, TY + 1) + sizeof(cx<T>) * (size_t)(TX + 1) * (TY + 1) + krylov_smem_bytes<T>(cap);
 }
 
-// Tile shape of the tile-owned form for an nx x ny level: the candidate with the most tiles that
-// still gives every CTA its own tile (at most the co-resident CTAs of that shape), tiles of at
-// least 256 nodes.  Returns the tile count (0: the form does not fit this level).
+// Tile shapes of the tile-owned form that fit an nx x ny level: every CTA owns one tile and all
+// tiles are co-resident.  Written most tiles first (one shape per tile count, the larger tile on
+// a tie); returns how many were written (at most maxc).
 template <typename T, int R>
-int tile_form_choice(int nx, int ny, int cap, int* TXo, int* TYo) {
+int tile_form_list(int nx, int ny, int cap, int* TXo, int* TYo, int maxc) {
   static const int cand[4][2] = {{64, 32}, {32, 32}, {32, 16}, {16, 16}};
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-  int best = 0;
+  int m = 0, cnt[4];
   for (const auto& c : cand) {
     const int TX = c[0], TY = c[1];
     const size_t sm = tile_form_smem<T, R>(TX, TY, cap);
@@ -1150,12 +1150,32 @@ int tile_form_choice(int nx, int ny, int cap, int* TXo, int* TYo) {
       cudaGetLastError();
       continue;
     }
-    if (nt > per * sms || nt <= best) continue;
-    best = nt;
-    *TXo = TX;
-    *TYo = TY;
+    if (nt > per * sms) continue;
+    bool dup = false;
+    for (int i = 0; i < m; ++i) dup |= cnt[i] == nt;
+    if (dup || m == maxc) continue;
+    int i = m++;
+    for (; i > 0 && cnt[i - 1] < nt; --i) {  // insertion by decreasing tile count
+      cnt[i] = cnt[i - 1];
+      TXo[i] = TXo[i - 1];
+      TYo[i] = TYo[i - 1];
+    }
+    cnt[i] = nt;
+    TXo[i] = TX;
+    TYo[i] = TY;
   }
-  return best;
+  return m;
+}
+
+// Default tile shape of the tile-owned form: the fitting shape with the most tiles.  Returns the
+// tile count (0: the form does not fit this level).
+template <typename T, int R>
+int tile_form_choice(int nx, int ny, int cap, int* TXo, int* TYo) {
+  int tx[4], ty[4];
+  if (tile_form_list<T, R>(nx, ny, cap, tx, ty, 4) == 0) return 0;
+  *TXo = tx[0];
+  *TYo = ty[0];
+  return tiles_along(nx, tx[0]) * tiles_along(ny, ty[0]);
 }
 
 template <typename T, int R>
@@ -1331,6 +1351,19 @@ int gmres_tile_form(int dt, int R, int nx, int ny, int cap, int* TX, int* TY) {
     if (R == 1) return tile_form_choice<float, 1>(nx, ny, cap, TX, TY);
     if (R == 2) return tile_form_choice<float, 2>(nx, ny, cap, TX, TY);
     if (R == 3) return tile_form_choice<float, 3>(nx, ny, cap, TX, TY);
+  }
+  return 0;
+}
+
+int gmres_tile_forms(int dt, int R, int nx, int ny, int cap, int* TX, int* TY, int maxc) {
+  if (dt == C128) {
+    if (R == 1) return tile_form_list<double, 1>(nx, ny, cap, TX, TY, maxc);
+    if (R == 2) return tile_form_list<double, 2>(nx, ny, cap, TX, TY, maxc);
+    if (R == 3) return tile_form_list<double, 3>(nx, ny, cap, TX, TY, maxc);
+  } else {
+    if (R == 1) return tile_form_list<float, 1>(nx, ny, cap, TX, TY, maxc);
+    if (R == 2) return tile_form_list<float, 2>(nx, ny, cap, TX, TY, maxc);
+    if (R == 3) return tile_form_list<float, 3>(nx, ny, cap, TX, TY, maxc);
   }
   return 0;
 }
