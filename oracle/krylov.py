@@ -14,10 +14,16 @@ column is min_y ||beta e1 - H_j y|| computed by a dense least-squares solve
 (the definition, not an incremental Givens update), and the cycle stops as soon
 as it falls to ``tol_abs`` or the Hessenberg subdiagonal vanishes.
 
+Bi-CGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13(2), 1992), the Krylov
+solver the paper's earlier multilevel work used for the CSLP inverse (Section 3.2)
+and its own tolerance study used (Section 4.1), is :func:`bicgstab`.
+
 Pins (tests/test_oracle_krylov.py): the GMRES residual after j steps equals the
 minimum residual over the Krylov space computed from an independent basis;
 FGMRES with the exact inverse converges in one step; the Arnoldi relation
-A X_j = V_{j+1} H_j holds; restarted FGMRES reaches a direct solve.
+A X_j = V_{j+1} H_j holds; restarted FGMRES reaches a direct solve.  Bi-CGSTAB:
+one step on a multiple of the identity is exact, its recurred residual is the
+true residual, and it agrees with SciPy's independent implementation.
 """
 from __future__ import annotations
 
@@ -106,3 +112,58 @@ def fgmres_restarted(apply_a, b, precond, tol, restart, max_iters, u0=None):
         if cyc.iterations == 0:
             break
     return u, total, rel, history
+
+
+@dataclass
+class BicgResult:
+    iterations: int
+    residual: float          # recurred ||r|| / ||b|| at exit
+    converged: bool
+
+
+def bicgstab(apply_a, b, tol, maxit):
+    """Bi-CGSTAB with zero initial guess and shadow residual r_hat = b.
+
+    Each iteration: rho = r_hat^H r; p = r (first) or r + (rho/rho_old)(alpha/omega)(p - omega v);
+    v = A p; alpha = rho / (r_hat^H v); s = r - alpha v; t = A s; omega = t^H s / t^H t;
+    x += alpha p + omega s; r = s - omega t.  Stops when ||r|| <= tol ||b|| after an iteration,
+    after ``maxit`` iterations, or on a vanishing rho, r_hat^H v or t^H t (breakdown; t = 0
+    means s = 0, so x + alpha p is then exact).  Returns (x, BicgResult)."""
+    bn = float(np.linalg.norm(b))
+    x = np.zeros_like(b)
+    if bn == 0.0:
+        return x, BicgResult(0, 0.0, True)
+    r = b.copy()
+    rhat = b.copy()
+    p = v = None
+    rho_old = alpha = omega = 1.0
+    its = 0
+    for i in range(maxit):
+        rho = np.vdot(rhat, r)
+        if rho == 0:
+            break
+        if i == 0:
+            p = r.copy()
+        else:
+            p = r + (rho / rho_old) * (alpha / omega) * (p - omega * v)
+        v = apply_a(p)
+        rv = np.vdot(rhat, v)
+        if rv == 0:
+            break
+        alpha = rho / rv
+        s = r - alpha * v
+        t = apply_a(s)
+        tt = np.vdot(t, t).real
+        its = i + 1
+        if tt == 0:
+            x = x + alpha * p
+            r = s
+            break
+        omega = np.vdot(t, s) / tt
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho_old = rho
+        if float(np.linalg.norm(r)) <= tol * bn:
+            break
+    rel = float(np.linalg.norm(r)) / bn
+    return x, BicgResult(its, rel, rel <= tol)

@@ -25,7 +25,9 @@ MADP schedule (Section 4.4; Section 4.1 for the coarsest level):
   otherwise tolerance 1e-1, at most floor(6 N_ml^(1/4)) iterations;
 * CSLP inverse: multigrid V-cycle on levels 1 and 2; unpreconditioned GMRES to
   tolerance 1e-1, at most floor(6 N_l^(1/4)) iterations, on levels >= 3
-  (Section 4.2), with shift beta = (1, 0.5) (Section 4.3).
+  (Section 4.2), with shift beta = (1, 0.5) (Section 4.3); Bi-CGSTAB with the same
+  tolerance and cap instead of GMRES with ``cslp_solver = "bicgstab"`` (the solver
+  of the earlier multilevel work, Section 3.2).
 All inner solves start from a zero initial guess.
 
 Level l has (n_{l-1} + 1) / 2 nodes per side, spacing 2^(l-1) h and the
@@ -44,7 +46,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .krylov import fgmres, fgmres_restarted, gmres
+from .krylov import bicgstab, fgmres, fgmres_restarted, gmres
 from .multigrid import CSLPMultigrid
 from .operators import apply_level
 from .transfers import coarse_size, deflation_prolong, deflation_restrict, inject
@@ -71,6 +73,7 @@ class MADPConfig:
     mg_coarsest_side: int = 20
     cycle_m: int = 1                # iterations on levels 3 .. ml-1 without a tolerance
     level_tol: dict = field(default_factory=dict)   # level (3 .. ml-1) -> relative tolerance
+    cslp_solver: str = "gmres"      # Krylov solver of the CSLP inverse beyond mg_max_level: gmres | bicgstab
 
 
 @dataclass
@@ -126,7 +129,10 @@ class Hierarchy:
         if l in self.mg:
             return self.mg[l](r)
         cap = krylov_cap(self.cfg.c_it, self.nodes(l))
-        x, res = gmres(lambda u: self.M(l, u), r, self.cfg.cslp_tol, cap)
+        if self.cfg.cslp_solver == "bicgstab":
+            x, res = bicgstab(lambda u: self.M(l, u), r, self.cfg.cslp_tol, cap)
+        else:
+            x, res = gmres(lambda u: self.M(l, u), r, self.cfg.cslp_tol, cap)
         self.stats.add(self.stats.cslp_gmres_iterations, l, res.iterations)
         return x
 

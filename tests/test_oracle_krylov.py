@@ -71,3 +71,53 @@ def test_restarted_fgmres_reaches_direct_solve():
 def test_zero_rhs_returns_zero():
     x, res = gmres(lambda v: 2 * v, np.zeros(5, complex), 0.1, 4)
     assert res.iterations == 0 and not np.any(x)
+
+
+# ---- Bi-CGSTAB (van der Vorst 1992; the CSLP solver of Sections 3.2 and 4.1) --------------------
+def test_bicgstab_scaled_identity_is_exact_in_one_step():
+    """A = c I: v = c p, alpha = 1/c, s = 0, so the first iteration returns b / c."""
+    from oracle.krylov import bicgstab
+    b = mp.random_complex((40,), seed=3)
+    c = 2.5 - 1.5j
+    x, res = bicgstab(lambda u: c * u, b, 1e-12, 10)
+    assert res.iterations == 1 and res.converged
+    np.testing.assert_allclose(x, b / c, rtol=0, atol=1e-14 * np.abs(b / c).max())
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_bicgstab_matches_scipy_iterates(k):
+    """k iterations with no early stop give SciPy's independent Bi-CGSTAB iterate."""
+    import scipy.sparse.linalg as spla
+    from oracle.krylov import bicgstab
+    A = _matrix(30, seed=7)
+    b = mp.random_complex((30,), seed=8)
+    x, res = bicgstab(lambda u: A @ u, b, 0.0, k)
+    assert res.iterations == k
+    xs, info = spla.bicgstab(A, b, rtol=1e-300, atol=0.0, maxiter=k)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-10 * np.abs(xs).max())
+
+
+def test_bicgstab_recurred_residual_is_true_residual_and_solves():
+    """On a Helmholtz-type CSLP system the recurred residual at exit equals ||b - A x||
+    and the tolerance reached means the direct solution to that accuracy."""
+    from helpers import assemble
+    from oracle.krylov import bicgstab
+    from oracle.operators import apply_level
+    n = 17
+    k = mp.random_k(n, n, seed=4, kmin=3.0, kmax=6.0)
+    h = 1.0 / 16
+    M = lambda u: apply_level(u, k, 3, h, complex(1.0, 0.5))
+    b = mp.random_complex((n, n), seed=5)
+    x, res = bicgstab(M, b, 1e-10, 400)
+    assert res.converged and res.iterations > 3
+    true = np.linalg.norm(b - M(x)) / np.linalg.norm(b)
+    assert abs(true - res.residual) <= 1e-9
+    Md = assemble(M, (n, n), 3).toarray()
+    ref = np.linalg.solve(Md, b.ravel()).reshape(n, n)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-10 * np.linalg.cond(Md)
+
+
+def test_bicgstab_zero_rhs():
+    from oracle.krylov import bicgstab
+    x, res = bicgstab(lambda u: 2 * u, np.zeros(5, complex), 0.1, 5)
+    assert res.iterations == 0 and not x.any()

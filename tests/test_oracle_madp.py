@@ -164,3 +164,15 @@ def test_madp_v1_schedule():
     assert st.level_iterations[2] == st.level_calls[2] == st.outer_iterations
     assert set(st.cslp_gmres_iterations) == {1, 2, 3}
     assert st.true_relres <= 1e-6
+
+
+def test_bicgstab_cslp_solves():
+    """Bi-CGSTAB as the CSLP solver on levels >= 3 (Sections 3.2, 4.1): the solve still reaches
+    the 1e-6 residual of the assembled system and every CSLP call iterated."""
+    p = mp.random_field(129, 5.0, seed=3, kh_max=0.3, levels=4, negdef_from_level=4)
+    cfg = MADPConfig(levels=4, negdef_from_level=4, cslp_solver="bicgstab")
+    u, st = Hierarchy(p.k, p.h, cfg).solve(p.b[0])
+    A = assemble(lambda x: apply_helmholtz(x, p.k, p.h), (p.ny, p.nx), 1).tocsc()
+    rel = np.linalg.norm(p.b[0].ravel() - A @ u.ravel()) / np.linalg.norm(p.b[0])
+    assert rel <= 1e-6
+    assert st.cslp_gmres_iterations[3] >= st.level_iterations[2]
