@@ -65,6 +65,8 @@ SCHEDULES = {
     "madp_v1": "MADP-v1 (Section 4.3.1): GMRES CSLP on every level, beta2 = 1/k_dim,max, one iteration "
                "on every level between the finest and the coarsest",
     "madp_v2": "MADP-v2 (Section 4.3.3): as MADP-v1 with level 2 solved to 0.1",
+    "madp_bicgstab": "MADP with Bi-CGSTAB instead of GMRES for the CSLP inverse on levels >= 3 "
+                     "(the earlier multilevel work's solver, Sections 3.2 and 4.1)",
 }
 
 
@@ -86,6 +88,8 @@ def schedule_config(name: str, p) -> dict:
         return {"mg_max_level": 0, "beta2": 1.0 / kdim, "l2_tol": 0.0, "l2_maxit": 1}
     if name == "madp_v2":
         return {"mg_max_level": 0, "beta2": 1.0 / kdim, "l2_tol": 0.1}
+    if name == "madp_bicgstab":
+        return {"cslp_solver": "bicgstab"}
     raise ValueError(name)
 
 
@@ -192,8 +196,11 @@ def oracle_sample(workload: str, counts: dict) -> dict:
         est += its * per_it + calls * kk * (kk + 1) / 2 * unit[f"G{l}"]
         g = counts["cslp_gmres_iterations"][l - 1]
         if l > cfg.mg_max_level and its > 0:
-            kg = g / its
-            est += g * unit[f"A{l}"] + its * kg * (kg + 1) / 2 * unit[f"G{l}"]
+            if sched.get("cslp_solver") == "bicgstab":   # two applies and three dot/axpy pairs
+                est += g * (2 * unit[f"A{l}"] + 3 * unit[f"G{l}"])
+            else:
+                kg = g / its
+                est += g * unit[f"A{l}"] + its * kg * (kg + 1) / 2 * unit[f"G{l}"]
     est += unit["A1"]                                            # true residual
     return {"est_s_per_solve": est, "sample_s": sample_s, "unit_s": unit, "cores": 1}
 

@@ -61,6 +61,9 @@ extern "C" {
 #define HZ_OP_A 0          /* Helmholtz operator A_l (shift 1) */
 #define HZ_OP_M 1          /* CSLP operator M_l (shift beta1 + i beta2) */
 
+#define HZ_CSLP_GMRES    0 /* CSLP inverse on Krylov levels by GMRES */
+#define HZ_CSLP_BICGSTAB 1 /* CSLP inverse on Krylov levels by Bi-CGSTAB */
+
 #define HZ_MAX_LEVELS 10
 
 #define HZ_SOLVE_INITIAL_GUESS 1u  /* hz_solve flag: u holds the initial guess on entry */
@@ -124,6 +127,10 @@ typedef struct {
                             Sections 4.3.3 and 4.5); default 0; entries of other levels must be 0.
                             Level 2 keeps l2_tol / l2_maxit: l2_tol = 0 runs exactly l2_maxit
                             iterations (l2_maxit = 1: MADP-v1's V-cycle, Section 4.3.1) */
+  int cslp_solver;       /* Krylov solver of the CSLP inverse on levels > mg_max_level, same
+                            tolerance cslp_tol and cap: HZ_CSLP_GMRES (default, Section 4.2) or
+                            HZ_CSLP_BICGSTAB (the earlier multilevel work's choice, Sections 3.2
+                            and 4.1) */
 } hz_config;
 
 /* Per-right-hand-side solve statistics. */
@@ -236,6 +243,12 @@ int hz_mg_size(hz_handle h, int level, int mg_level, int* nx, int* ny);
  * b, x: dtype vectors on level l; iterations (host, nrhs entries) may be NULL. */
 int hz_cslp_gmres(hz_handle h, int level, int dtype, const void* b, void* x, int nrhs,
                   int* iterations);
+
+/* CSLP inverse by Bi-CGSTAB (van der Vorst 1992) on M_l with the same tolerance and cap as
+ * hz_cslp_gmres, zero initial guess, shadow residual b.  Needs a handle configured with
+ * cslp_solver = HZ_CSLP_BICGSTAB and level > mg_max_level (else HZ_EINVAL). */
+int hz_cslp_bicgstab(hz_handle h, int level, int dtype, const void* b, void* x, int nrhs,
+                     int* iterations);
 
 /* ---- allocation-free check -------------------------------------------------------- */
 

@@ -29,6 +29,7 @@ HZ_PREC_FP64, HZ_PREC_MIXED = 0, 1
 HZ_C128, HZ_C64 = 0, 1
 HZ_OP_A, HZ_OP_M = 0, 1
 HZ_MAX_LEVELS = 10
+HZ_CSLP_GMRES, HZ_CSLP_BICGSTAB = 0, 1
 HZ_SOLVE_INITIAL_GUESS = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -52,7 +53,7 @@ class HzConfig(ctypes.Structure):
         ("mg_nu2", ctypes.c_int), ("mg_coarsest_side", ctypes.c_int), ("max_rhs", ctypes.c_int),
         ("timeout_s", ctypes.c_double), ("device_gmres", ctypes.c_int), ("reorth_eta", ctypes.c_double),
         ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("cycle_m", ctypes.c_int),
-        ("level_tol", ctypes.c_double * HZ_MAX_LEVELS),
+        ("level_tol", ctypes.c_double * HZ_MAX_LEVELS), ("cslp_solver", ctypes.c_int),
     ]
 
 
@@ -119,6 +120,7 @@ _SIGS = {
     "hz_mg_vcycle": (_I, [_P, _I, _I, _P, _P, _I]),
     "hz_mg_size": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "hz_cslp_gmres": (_I, [_P, _I, _I, _P, _P, _I, ctypes.POINTER(_I)]),
+    "hz_cslp_bicgstab": (_I, [_P, _I, _I, _P, _P, _I, ctypes.POINTER(_I)]),
     "hz_strerror": (ctypes.c_char_p, [_I]),
     "hz_last_error": (ctypes.c_char_p, []),
     "hz_profile_enable": (_I, [_P, _I, _I]),
@@ -177,6 +179,8 @@ def config(**kw) -> HzConfig:
     for k, v in kw.items():
         if not hasattr(c, k):
             raise KeyError(k)
+        if k == "cslp_solver" and isinstance(v, str):
+            v = {"gmres": HZ_CSLP_GMRES, "bicgstab": HZ_CSLP_BICGSTAB}[v]
         if k == "level_tol":
             # {level: tolerance} for levels 3 .. levels-1 (entry level-1 of the C array)
             arr = (ctypes.c_double * HZ_MAX_LEVELS)()
@@ -378,6 +382,16 @@ class Helmholtz:
         x = torch.empty_like(b)
         its = (ctypes.c_int * n)()
         _check(lib().hz_cslp_gmres(self._h, level, self._dt(b), _ptr(b), _ptr(x), n, its), "hz_cslp_gmres")
+        return x, list(its)
+
+    def cslp_bicgstab(self, level: int, b):
+        """CSLP inverse by Bi-CGSTAB on level ``level`` (handle built with cslp_solver="bicgstab")."""
+        import torch
+        ny, nx = self.level_size(level)
+        n = self._nrhs(b, ny, nx)
+        x = torch.empty_like(b)
+        its = (ctypes.c_int * n)()
+        _check(lib().hz_cslp_bicgstab(self._h, level, self._dt(b), _ptr(b), _ptr(x), n, its), "hz_cslp_bicgstab")
         return x, list(its)
 
     def launch_count(self) -> int:

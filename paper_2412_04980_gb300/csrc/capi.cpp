@@ -90,6 +90,7 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (c.graphs != 0 && c.graphs != 1) return bad("graphs must be 0 or 1");
   if (c.device_gmres < 0 || c.device_gmres > 4) return bad("device_gmres must be 0, 1, 2, 3 or 4");
   if (c.cycle_m < 1) return bad("cycle_m must be >= 1");
+  if (c.cslp_solver != HZ_CSLP_GMRES && c.cslp_solver != HZ_CSLP_BICGSTAB) return bad("unknown cslp_solver");
   if (!(c.l2_tol >= 0 && c.l2_tol < 1)) return bad("l2_tol must be in [0, 1)");
   for (int l = 1; l <= HZ_MAX_LEVELS; ++l) {
     const double t = c.level_tol[l - 1];
@@ -369,6 +370,20 @@ int hz_cslp_gmres(hz_handle hp, int level, int dtype, const void* b, void* x, in
   if (st) return st;
   st = cslp_gmres(H_, level, b, x, nrhs, iterations);
   return st ? st : collect_gmres_stats(H_, nrhs);
+}
+
+int hz_cslp_bicgstab(hz_handle hp, int level, int dtype, const void* b, void* x, int nrhs, int* iterations) {
+  GUARD_HANDLE(hp);
+  if (int s = check_level(H_, level)) return s;
+  if (int s = check_nrhs(H_, nrhs, true)) return s;
+  if (!b || !x) return bad("null vector");
+  Level& L = H_->lv[level - 1];
+  if (!L.bcg) return bad("level has no Bi-CGSTAB CSLP solver (cslp_solver or level <= mg_max_level)");
+  if (dtype != L.dpre) return bad("dtype must match the handle's preconditioner precision on this level");
+  for (int q = 0; q < nrhs; ++q) H_->st[q] = RhsStats();
+  int st = status_of(cudaMemsetAsync(x, 0, (size_t)nrhs * L.n * elem_bytes(dtype), H_->ctx.s), "hz_cslp_bicgstab");
+  if (st) return st;
+  return cslp_bicgstab(H_, level, b, x, nrhs, iterations);
 }
 
 const char* hz_strerror(int s) {

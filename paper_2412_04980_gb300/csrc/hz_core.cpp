@@ -346,7 +346,7 @@ constexpr size_t kClusterMaxN = 300000;
 // down (isolated FP64 cluster GMRES calls agree with the grid form; the cause is not found), so
 // FP64 batches take the cooperative grid per right-hand side.
 static bool cluster_form_possible(const hz_config& cfg, size_t n) {
-  if (cfg.precision != HZ_PREC_MIXED) return false;
+  if (cfg.precision != HZ_PREC_MIXED || cfg.cslp_solver != HZ_CSLP_GMRES) return false;
   return cfg.device_gmres == 3 || (cfg.device_gmres == 1 && cfg.max_rhs >= kClusterMinRhs && n <= kClusterMaxN);
 }
 
@@ -392,7 +392,9 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
     } else {
       const int capg = std::max(1, krylov_cap(cfg.c_it, n));
       maxnv = std::max(maxnv, (size_t)capg + 1);
-      const bool dev = cfg.device_gmres != 0;
+      const bool bicg = cfg.cslp_solver == HZ_CSLP_BICGSTAB;
+      const bool dev = cfg.device_gmres != 0 && !bicg;
+      if (bicg) total += 5 * bn * ep + sizeof(BicgState) * (size_t)nb + bicg_part_bytes(n, nb);
       // upper bound: the cluster form keeps per-rhs workspace
       const bool clus = cluster_form_possible(cfg, n);
       const size_t gbr = (dev && !clus) ? n : bn;
@@ -536,7 +538,14 @@ int setup(Handle* h, const double* k_dev) {
     } else {
       L.capg = std::max(1, krylov_cap(cfg.c_it, L.n));
       maxnv = std::max(maxnv, (size_t)L.capg + 1);
-      if (cfg.device_gmres) {
+      if (cfg.cslp_solver == HZ_CSLP_BICGSTAB) {
+        void* p;
+        CS(dalloc(h, &L.bcg, 5 * bn * ep));
+        CS(dalloc(h, &p, sizeof(BicgState) * (size_t)nb));
+        L.bst = (BicgState*)p;
+        CS(dalloc(h, &p, bicg_part_bytes(L.n, nb)));
+        L.bpart = (double*)p;
+      } else if (cfg.device_gmres) {
         L.ggrid = std::min(gmres_max_grid(L.dpre, L.R, L.capg, L.n), gmres_grid_want(L.nx, L.ny));
         L.gcl = cluster_form_possible(cfg, L.n) ? gmres_cluster_size(L.dpre, L.R, L.capg) : 0;
         // one right-hand side at a time on levels whose tiling fits the grid: tile-owned form
@@ -1081,6 +1090,65 @@ int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
   return HZ_OK;
 }
 
+// CSLP inverse by Bi-CGSTAB on M_l (levels > mg_max_level, cslp_solver = HZ_CSLP_BICGSTAB):
+// x += BiCGSTAB(b), tolerance cslp_tol, at most capg iterations.  Scalars stay on the device;
+// the host looks at the stop flags every kBicgCheck iterations and after the last one.
+constexpr int kBicgCheck = 4;
+int cslp_bicgstab(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
+  LevelTag tag(h->ctx, l);
+  Level& L = h->lv[l - 1];
+  if (!L.bcg) {
+    set_error("the level has no Bi-CGSTAB workspace (cslp_solver is not HZ_CSLP_BICGSTAB)");
+    return HZ_EINVAL;
+  }
+  Ctx& c = h->ctx;
+  const int dt = L.dpre;
+  const size_t n = L.n, bn = (size_t)nb * n, eb = elem_bytes(dt);
+  char* base = (char*)L.bcg;
+  const size_t stride = (size_t)h->nbmax * n * eb;
+  void *r = base, *p = base + stride, *v = base + 2 * stride, *s = base + 3 * stride, *t = base + 4 * stride;
+  OpDesc M = L.opM(dt, h->cfg.beta1, h->cfg.beta2);
+  CK(cudaMemcpyAsync(r, b, bn * eb, cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemsetAsync(p, 0, bn * eb, c.s));
+  CK(cudaMemsetAsync(v, 0, bn * eb, c.s));
+  CK(launch_bicg_start(c, dt, b, n, nb, h->cfg.cslp_tol, L.bpart, L.bst));
+  // stop flags come back through the level's pinned scalar buffer under the handle's timeout
+  if (sizeof(BicgState) * (size_t)nb > L.scg.total * sizeof(double)) {
+    set_error("Bi-CGSTAB state does not fit the level's host scalar buffer");
+    return HZ_EINVAL;
+  }
+  const BicgState* hs = reinterpret_cast<const BicgState*>(L.scg.host);
+  auto fetch = [&]() -> int {
+    CK(cudaMemcpyAsync(L.scg.host, L.bst, sizeof(BicgState) * nb, cudaMemcpyDeviceToHost, c.s));
+    return wait_event(h, L.scg.ev);
+  };
+  for (int it = 0; it < L.capg; ++it) {
+    CK(launch_bicg_p(c, dt, r, p, v, n, nb, L.bst));
+    CK(launch_level_op(c, M, 0, dt, dt, dt, p, nullptr, v, 0.0, nb));
+    CK(launch_bicg_dots(c, dt, 0, b, v, nullptr, nullptr, n, nb, L.bpart, L.bst));
+    CK(launch_bicg_s(c, dt, r, v, s, n, nb, L.bst));
+    CK(launch_level_op(c, M, 0, dt, dt, dt, s, nullptr, t, 0.0, nb));
+    CK(launch_bicg_dots(c, dt, 1, t, s, t, t, n, nb, L.bpart, L.bst));
+    CK(launch_bicg_xr(c, dt, x, p, s, t, r, b, n, nb, L.bpart, L.bst));
+    if ((it + 1) % kBicgCheck == 0 || it + 1 == L.capg) {
+      CS(fetch());
+      bool all = true;
+      for (int q = 0; q < nb; ++q) all &= hs[q].done != 0.0;
+      if (all) break;
+    }
+  }
+  if (L.capg < 1) CS(fetch());
+  for (int q = 0; q < nb; ++q) {
+    if (!std::isfinite(hs[q].rn2)) {
+      set_error("non-finite residual in the Bi-CGSTAB CSLP solve");
+      return HZ_EBREAKDOWN;
+    }
+    h->st[q].cslp_it[l - 1] += (int)hs[q].its;
+    if (its_out) its_out[q] = (int)hs[q].its;
+  }
+  return HZ_OK;
+}
+
 // out = M_l^-1 rtil [+ add]  (Algorithm 1 line 14; with add = t also line 15)
 int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add, int nb) {
   Level& L = h->lv[l - 1];
@@ -1088,6 +1156,7 @@ int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add,
   const size_t bytes = (size_t)nb * L.n * elem_bytes(L.dpre);
   if (add) CK(cudaMemcpyAsync(out, add, bytes, cudaMemcpyDeviceToDevice, h->ctx.s));
   else CK(cudaMemsetAsync(out, 0, bytes, h->ctx.s));
+  if (h->cfg.cslp_solver == HZ_CSLP_BICGSTAB) return cslp_bicgstab(h, l, rtil, out, nb, nullptr);
   return cslp_gmres(h, l, rtil, out, nb, nullptr);
 }
 

@@ -64,6 +64,10 @@ struct Level {
   int gpstride = 0;
   double* gR = nullptr;
   GmresState* gst = nullptr;                 // nbmax control blocks
+  // Bi-CGSTAB CSLP solver (cslp_solver = HZ_CSLP_BICGSTAB): r, p, v, s, t batches, scalars, partials
+  void* bcg = nullptr;
+  BicgState* bst = nullptr;
+  double* bpart = nullptr;
   int ggrid = 0;                             // CTAs of the cooperative-grid form (0: host-driven GMRES)
   int gcl = 0;                               // CTAs per cluster of the cluster form (0: not used)
   int gtiles = 0, gtx = 0, gty = 0;          // tile-owned form: CTAs (= tiles) and tile shape (0: not used)
@@ -118,6 +122,7 @@ void destroy(Handle* h);
 int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, int nb);
 int cslp_inverse(Handle* h, int l, const void* rtil, void* out, const void* add, int nb);
 int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out);
+int cslp_bicgstab(Handle* h, int l, const void* b, void* x, int nb, int* its_out);
 int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb);
 int coarse_solve(Handle* h, int l, int nb);
 int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags);

@@ -147,6 +147,32 @@ cudaError_t launch_combine(Ctx& c, int dtx, const void* X, size_t ldx, int nv, c
 cudaError_t launch_scale_dev(Ctx& c, int dt, const void* x, void* y, const double* alpha_dev, int recip, size_t n,
                              int nb);
 
+// ---- Bi-CGSTAB CSLP solver (kern_bicgstab.cu) ---------------------------------------------
+// Scalars of one right-hand side, in device memory (complex values as re, im).
+struct BicgState {
+  double rho[2], alpha[2], omega[2], beta[2];
+  double bn2, rn2, tol2;  // ||b||^2, ||r||^2, (tol ||b||)^2
+  double done;            // 0 running, 1 converged, 2 stopped by a breakdown
+  double its;             // completed iterations
+  double pad[3];
+};
+int bicg_parts(size_t n);                  // CTAs per right-hand side of the reduction passes
+size_t bicg_part_bytes(size_t n, int nb);  // partial-sum buffer
+// rho = ||b||^2 and the stop test's reference (r = r_hat = b is the caller's copy)
+cudaError_t launch_bicg_start(Ctx& c, int dt, const void* b, size_t n, int nb, double tol, double* part,
+                              BicgState* st);
+// which 0: alpha = rho / (a0^H b0) with a0 = r_hat, b0 = v; which 1: omega = a0^H b0 / a1^H b1 with
+// a0 = a1 = t, b0 = s, b1 = t
+cudaError_t launch_bicg_dots(Ctx& c, int dt, int which, const void* a0, const void* b0, const void* a1,
+                             const void* b1, size_t n, int nb, double* part, BicgState* st);
+cudaError_t launch_bicg_p(Ctx& c, int dt, const void* r, void* p, const void* v, size_t n, int nb,
+                          const BicgState* st);
+cudaError_t launch_bicg_s(Ctx& c, int dt, const void* r, const void* v, void* s, size_t n, int nb,
+                          const BicgState* st);
+// x += alpha p + omega s; r = s - omega t; then rho, ||r||, the stop test and beta
+cudaError_t launch_bicg_xr(Ctx& c, int dt, void* x, const void* p, const void* s, const void* t, void* r,
+                           const void* rhat, size_t n, int nb, double* part, BicgState* st);
+
 // ---- persistent GMRES (kern_gmres.cu) ---------------------------------------------------
 // Per-right-hand-side control block of the cooperative GMRES kernel (device memory, zeroed).
 struct GmresState {

@@ -96,6 +96,8 @@ def test_estimate_bytes_host_only(L):
     # a level with m iterations or a tolerance keeps a larger Krylov basis than a one-iteration level
     assert e(513, levels=5) < e(513, levels=5, cycle_m=2) < e(513, levels=5, cycle_m=3)
     assert e(513, levels=5, cycle_m=2) < e(513, levels=5, level_tol={3: 0.1})
+    # Bi-CGSTAB keeps five vectors per Krylov level in place of the persistent GMRES workspace
+    assert e(513, levels=5, cslp_solver="bicgstab") != e(513, levels=5)
     assert L.hz_estimate_bytes(None, None, None) == hz.HZ_EINVAL
 
 
@@ -152,7 +154,7 @@ def test_config_validation_of_new_fields(L):
     h = ctypes.c_void_p()
     g = hz.HzGrid(9, 9, 0.1, 0)
     for bad in (dict(device_gmres=5), dict(device_gmres=-1), dict(autotune=2), dict(reorth_eta=1.5),
-                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1),
+                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1), dict(cslp_solver=2),
                 dict(levels=3, level_tol={2: 0.1}), dict(levels=3, level_tol={3: 0.1}),
                 dict(levels=4, level_tol={3: 1.0}), dict(levels=4, level_tol={3: float("nan")})):
         c = hz.config(**bad)

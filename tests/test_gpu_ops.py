@@ -236,3 +236,46 @@ def test_cslp_gmres_fp32(hz, level, n, device_gmres):
     hier = Hierarchy(p.k, p.h, MADPConfig(levels=max(p.levels, level), mg_max_level=0 if level == 1 else 2))
     hier.cslp_inverse(level, b)
     assert abs(its[0] - hier.stats.cslp_gmres_iterations[level]) <= 2
+
+
+# ---- Bi-CGSTAB as the CSLP solver (van der Vorst 1992; Sections 3.2, 4.1) ------------------------
+@pytest.mark.parametrize("level", [3, 4])
+def test_cslp_bicgstab_fp64(hz, level):
+    """FP64 Bi-CGSTAB on M_l follows the oracle's iterates: the same iteration count (the stop
+    test is ||r|| <= 0.1 ||b|| after a full iteration) and the same x, and x meets the tolerance."""
+    p = mp.random_field(257, 5.0, seed=3, kh_max=0.3, levels=4)
+    H = handle(hz, p.k, p.h, levels=4, cslp_solver="bicgstab")
+    cy, cx = H.level_size(level)
+    kl = T.inject(p.k, 2 ** (level - 1))
+    b = mp.random_complex((cy, cx), seed=26)
+    hier = Hierarchy(p.k, p.h, MADPConfig(levels=4, cslp_solver="bicgstab"))
+    x_ref = hier.cslp_inverse(level, b)
+    its_ref = hier.stats.cslp_gmres_iterations[level]
+    x, its = H.cslp_bicgstab(level, dev(b))
+    x = host(x)
+    r = b - O.apply_level(x, kl, level, p.h, SHIFT)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 0.1 * (1 + 1e-9) or its[0] == krylov_cap(6.0, cy * cx)
+    assert abs(its[0] - its_ref) <= 1
+    if its[0] == its_ref:
+        assert rel_inf(x, x_ref) <= 1e-8
+
+
+def test_cslp_bicgstab_fp32_batch(hz):
+    """FP32 Bi-CGSTAB on three right-hand sides in one batch: each meets the tolerance measured
+    in FP64, stays within three iterations of the oracle, and equals its own solve alone."""
+    p = mp.random_field(257, 5.0, seed=3, kh_max=0.3, levels=4)
+    H = handle(hz, p.k, p.h, levels=4, precision="mixed", cslp_solver="bicgstab", max_rhs=3)
+    cy, cx = H.level_size(3)
+    kl = round32r(T.inject(p.k, 4))
+    b = round32(mp.random_complex((3, cy, cx), seed=27))
+    xb, itb = H.cslp_bicgstab(3, dev(b, torch.complex64))
+    xb = host(xb).astype(np.complex128)
+    hier = Hierarchy(p.k, p.h, MADPConfig(levels=4, cslp_solver="bicgstab"))
+    for q in range(3):
+        r = b[q] - O.apply_level(xb[q], kl, 3, p.h, SHIFT)
+        assert np.linalg.norm(r) / np.linalg.norm(b[q]) <= 0.1 * (1 + 1e-3)
+        before = hier.stats.cslp_gmres_iterations.get(3, 0)
+        hier.cslp_inverse(3, b[q])
+        assert abs(itb[q] - (hier.stats.cslp_gmres_iterations[3] - before)) <= 3
+        x1, it1 = H.cslp_bicgstab(3, dev(b[q], torch.complex64))
+        assert np.array_equal(host(x1), xb[q].astype(np.complex64)) and it1[0] == itb[q]

@@ -145,6 +145,8 @@ _VARIANTS = {
     "madp_v1": ("mp1b129", dict(levels=3, mg_max_level=0, beta2=1 / 20.0, l2_tol=0.0, l2_maxit=1)),
     # MADP-v2: as v1 with tolerance 0.1 on level 2
     "madp_v2": ("mp1b129", dict(levels=3, mg_max_level=0, beta2=1 / 20.0, l2_tol=0.1)),
+    # MADP with Bi-CGSTAB instead of GMRES for the CSLP inverse on levels 3 and 4
+    "bicgstab": ("field257", dict(levels=4, negdef_from_level=4, cslp_solver="bicgstab")),
 }
 
 
@@ -155,7 +157,8 @@ def _variant_problem(name):
 
 
 @pytest.mark.parametrize("variant,precision", [("w_cycle", "fp64"), ("w_cycle", "mixed"), ("level_tol", "fp64"),
-                                               ("madp_v1", "mixed"), ("madp_v2", "mixed")])
+                                               ("madp_v1", "mixed"), ("madp_v2", "mixed"), ("bicgstab", "fp64"),
+                                               ("bicgstab", "mixed")])
 def test_solve_schedule_variants(hz, variant, precision):
     """Each schedule variant reaches the 1e-6 residual with the oracle's solution, within one
     outer iteration of it, and keeps the variant's per-level counts: m iterations per call on a
