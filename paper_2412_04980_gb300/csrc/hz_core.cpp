@@ -399,7 +399,7 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       const bool clus = cluster_form_possible(cfg, n);
       const size_t gbr = (dev && !clus) ? n : bn;
       const size_t gq = clus ? (size_t)nb : 1;
-      total += (capg + 1) * gbr * ep + gbr * ep + scal(capg);
+      total += (capg + 1) * gbr * ep + gbr * ep + scal(bicg ? std::max(capg, 2) : capg);
       if (dev) {
         const size_t ps = 2 * (size_t)(capg + 1) + 2;
         total += gq * n * ep + 2 * sizeof(double) * std::max<size_t>(152, 16 * gq) * ps +
@@ -564,7 +564,8 @@ int setup(Handle* h, const double* k_dev) {
       const size_t gq = L.gcl ? (size_t)nb : 1;
       CS(dalloc(h, &L.Vg, (L.capg + 1) * gb_rhs * ep));
       CS(dalloc(h, &L.wg, gb_rhs * ep));
-      CS(alloc_scalars(h, L.scg, L.capg, nb));
+      // (the Bi-CGSTAB stop flags come back through this buffer: at least two columns' worth)
+      CS(alloc_scalars(h, L.scg, cfg.cslp_solver == HZ_CSLP_BICGSTAB ? std::max(L.capg, 2) : L.capg, nb));
       if (dev) {
         void* p;
         CS(dalloc(h, &L.wg2, gq * L.n * ep));
