@@ -232,6 +232,33 @@ def cpu_line(workload, res, steps_note):
             "est_s_per_solve": est}
 
 
+# ------------------------------------------------------------------------------- replicas
+# `--gpus N` under torchrun runs N independent replicas of the solve (the method has no exchange
+# step on one GPU per solve): the only collectives are the barriers around the timed region and
+# the maximum of the timed seconds over the replicas.
+def rank_barrier():
+    """Barrier over the replicas of a torchrun launch (nothing for a single process)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over the replicas: the job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, total_s: float) -> float:
+    """Whole-job solves/s: every replica solves `steps` times within the slowest one's time."""
+    return world * steps / total_s
+
+
 # ------------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -632,9 +659,7 @@ def main():
                      **extra)
     u = torch.empty_like(b)
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    barrier = rank_barrier
 
     mem_gb = H.memory_bytes() / 1e9
     gmres_forms = {str(l): H.gmres_form(l) for l in range(1, p.levels + 1) if H.gmres_form(l)["form"] != "none"}
@@ -677,10 +702,7 @@ def main():
     clk = clocks.stop()
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, dev)
     if args.no_live_profile:
         ms_dom, n_dom, by_dom = fam_ms[dom]
     else:
@@ -745,7 +767,7 @@ def main():
         if ent and ent.get("kernel_hash") == kernel_source_hash() and ent.get("workload") == args.workload:
             traffic = ent.get("bytes_per_launch")
     t_sorted = sorted(step_ms)
-    value = world * args.steps / total_s
+    value = job_throughput(world, args.steps, total_s)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
