@@ -139,7 +139,8 @@ typedef struct {
   int outer_iterations;                        /* level-1 FGMRES iterations, all cycles */
   int level_iterations[HZ_MAX_LEVELS];         /* [l-1]: deflated FGMRES iterations on level l */
   int level_calls[HZ_MAX_LEVELS];              /* [l-1]: number of level-l coarse solves */
-  int cslp_gmres_iterations[HZ_MAX_LEVELS];    /* [l-1]: GMRES iterations of CSLP inverses */
+  int cslp_gmres_iterations[HZ_MAX_LEVELS];    /* [l-1]: Krylov iterations of CSLP inverses
+                                                  (GMRES, or Bi-CGSTAB with cslp_solver) */
   double true_relres;                          /* ||b - A_h u|| / ||b|| in FP64 */
   double est_relres;                           /* last Arnoldi least-squares estimate */
   double ms;                                   /* wall time of the solve in milliseconds */
