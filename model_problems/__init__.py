@@ -89,6 +89,19 @@ def mp1b(n_interior: int = 128, k: float = 20.0) -> Problem:
                    meta={"k": k, "source": (c, c)})
 
 
+def mp1a(n_interior: int = 128, k: float = 20.0, levels: int = 2) -> Problem:
+    """Constant wavenumber on [0,1]^2 with homogeneous Dirichlet boundary (MP-1a): the
+    (n_interior-1)^2 interior nodes are the unknowns, h = 1/n_interior, unit point source at
+    (0.5, 0.5) (interior index n_interior/2 - 1)."""
+    n = n_interior - 1
+    h = 1.0 / n_interior
+    kk = np.full((n, n), float(k))
+    c = n_interior // 2 - 1
+    b = point_source(n, n, c, c, h)[None]
+    return Problem("mp1a", n, n, h, kk, b, levels=levels, negdef_from_level=0,
+                   meta={"k": k, "source": (c, c), "bc": "dirichlet"})
+
+
 def _wedge_velocity(x: np.ndarray, y: np.ndarray, width: float) -> np.ndarray:
     """Three-layer wedge velocity.  Interface 1 runs from (0, -350) to (600, -150),
     interface 2 from (0, -700) to (600, -550); both are extended linearly beyond

@@ -31,7 +31,9 @@ MADP schedule (Section 4.4; Section 4.1 for the coarsest level):
 All inner solves start from a zero initial guess.
 
 Level l has (n_{l-1} + 1) / 2 nodes per side, spacing 2^(l-1) h and the
-wavenumber injected at coincident nodes.
+wavenumber injected at coincident nodes.  With ``bc = "dirichlet"`` (MP-1a,
+Section 2.2) the grids hold interior unknowns only: (n_{l-1} - 1) / 2 per side,
+the Dirichlet transfers and level operators of ``transfers`` / ``operators``.
 
 Pins (tests/test_oracle_madp.py): with the exact Galerkin coarse inverse the
 A-DEF1 operator maps A Z y to Z y; the solver's result solves the assembled
@@ -48,8 +50,9 @@ import numpy as np
 
 from .krylov import bicgstab, fgmres, fgmres_restarted, gmres
 from .multigrid import CSLPMultigrid
-from .operators import apply_level
-from .transfers import coarse_size, deflation_prolong, deflation_restrict, inject
+from .operators import DIRICHLET, SOMMERFELD, apply_level, apply_level_dirichlet
+from .transfers import (coarse_size, coarse_size_dirichlet, deflation_prolong, deflation_prolong_dirichlet,
+                        deflation_restrict, deflation_restrict_dirichlet, inject, inject_dirichlet)
 
 
 @dataclass
@@ -74,6 +77,7 @@ class MADPConfig:
     cycle_m: int = 1                # iterations on levels 3 .. ml-1 without a tolerance
     level_tol: dict = field(default_factory=dict)   # level (3 .. ml-1) -> relative tolerance
     cslp_solver: str = "gmres"      # Krylov solver of the CSLP inverse beyond mg_max_level: gmres | bicgstab
+    bc: str = SOMMERFELD            # "dirichlet": interior unknowns of a zero-boundary grid (MP-1a)
 
 
 @dataclass
@@ -102,24 +106,29 @@ class Hierarchy:
         self.h = float(h)
         self.shift = complex(cfg.beta1, cfg.beta2)
         ny, nx = k.shape
+        self.dirichlet = cfg.bc == DIRICHLET
+        csize = coarse_size_dirichlet if self.dirichlet else coarse_size
+        injector = inject_dirichlet if self.dirichlet else inject
         self.shapes = [(ny, nx)]
         for _ in range(cfg.levels - 1):
-            ny, nx = coarse_size(ny), coarse_size(nx)
+            ny, nx = csize(ny), csize(nx)
             self.shapes.append((ny, nx))
-        self.k = [inject(np.asarray(k, np.float64), 2 ** l) for l in range(cfg.levels)]
+        self.k = [injector(np.asarray(k, np.float64), 2 ** l) for l in range(cfg.levels)]
         self.mg = {}
         for l in range(1, cfg.levels + 1):
             if l <= cfg.mg_max_level:
                 self.mg[l] = CSLPMultigrid(self.k[l - 1], l, self.h, self.shift, cfg.mg_omega,
-                                           cfg.mg_nu1, cfg.mg_nu2, cfg.mg_coarsest_side)
+                                           cfg.mg_nu1, cfg.mg_nu2, cfg.mg_coarsest_side, cfg.bc)
         self.stats = Stats()
 
     # operators of level l (1-based)
     def A(self, l, u):
-        return apply_level(u, self.k[l - 1], l, self.h, 1.0)
+        op = apply_level_dirichlet if self.dirichlet else apply_level
+        return op(u, self.k[l - 1], l, self.h, 1.0)
 
     def M(self, l, u):
-        return apply_level(u, self.k[l - 1], l, self.h, self.shift)
+        op = apply_level_dirichlet if self.dirichlet else apply_level
+        return op(u, self.k[l - 1], l, self.h, self.shift)
 
     def nodes(self, l):
         return self.shapes[l - 1][0] * self.shapes[l - 1][1]
@@ -141,9 +150,14 @@ class Hierarchy:
         ml = self.cfg.levels
         if ml == 1:
             return self.cslp_inverse(1, v)
-        vhat = deflation_restrict(v)
-        vtil = self.coarse_solve(l + 1, vhat)
-        t = deflation_prolong(vtil, self.shapes[l - 1])
+        if self.dirichlet:
+            vhat = deflation_restrict_dirichlet(v)
+            vtil = self.coarse_solve(l + 1, vhat)
+            t = deflation_prolong_dirichlet(vtil, self.shapes[l - 1])
+        else:
+            vhat = deflation_restrict(v)
+            vtil = self.coarse_solve(l + 1, vhat)
+            t = deflation_prolong(vtil, self.shapes[l - 1])
         s = self.A(l, t)
         rtil = v - s
         r = self.cslp_inverse(l, rtil)

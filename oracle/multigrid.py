@@ -15,9 +15,14 @@ it takes from its earlier matrix-free CSLP work.  The reading used here:
 * coarsening stops once a side has at most ``coarsest_side`` nodes (or cannot be
   halved); that level is solved exactly by a dense LU factorisation built once.
 
+On a homogeneous Dirichlet grid (interior unknowns, ``bc = "dirichlet"``) the same
+cycle runs with the Dirichlet operators, transfers and injection of
+``operators`` / ``transfers`` (coarse unknown I at fine unknown 2I + 1).
+
 Pins (tests/test_oracle_multigrid.py): for the Poisson operator (k = 0) the
-V(1,1) convergence factor lies in the textbook range; the exact solution is a
-fixed point of every Jacobi sweep; a single-level hierarchy is an exact solve.
+V(1,1) convergence factor lies in the textbook range (both boundary types); the
+exact solution is a fixed point of every Jacobi sweep; a single-level hierarchy
+is an exact solve.
 """
 from __future__ import annotations
 
@@ -26,8 +31,10 @@ from dataclasses import dataclass
 import numpy as np
 import scipy.linalg as sla
 
-from .operators import apply_5pt, apply_level, diag_5pt, diag_level, jacobi, level_scale, level_spacing
-from .transfers import bilinear_prolong, fw_restrict, inject
+from .operators import (DIRICHLET, SOMMERFELD, apply_5pt, apply_level, apply_level_dirichlet, diag_5pt, diag_level,
+                        diag_level_dirichlet, jacobi, level_scale, level_spacing)
+from .transfers import (bilinear_prolong, bilinear_prolong_dirichlet, fw_restrict, fw_restrict_dirichlet, inject,
+                        inject_dirichlet)
 
 
 @dataclass
@@ -53,26 +60,33 @@ def _dense_matrix(apply, shape) -> np.ndarray:
 class CSLPMultigrid:
     """V-cycle approximation of M_l^-1 for deflation level ``level``."""
 
-    def __init__(self, k_level, level, h, shift, omega=0.8, nu1=1, nu2=1, coarsest_side=20):
+    def __init__(self, k_level, level, h, shift, omega=0.8, nu1=1, nu2=1, coarsest_side=20, bc=SOMMERFELD):
         self.omega, self.nu1, self.nu2 = omega, nu1, nu2
+        self.bc = bc
         ks = level_scale(level)
         H = level_spacing(level, h)
         sh = complex(shift)
         k0 = np.asarray(k_level, dtype=np.float64)
-        self.levels = [MGLevel(k0.shape, k0,
-                               (lambda u, kk=k0: apply_level(u, kk, level, h, sh)),
-                               diag_level(k0, level, h, sh))]
+        if bc == DIRICHLET:
+            top = MGLevel(k0.shape, k0, (lambda u, kk=k0: apply_level_dirichlet(u, kk, level, h, sh)),
+                          diag_level_dirichlet(k0, level, h, sh))
+            min_side, injector = 3, inject_dirichlet
+        else:
+            top = MGLevel(k0.shape, k0, (lambda u, kk=k0: apply_level(u, kk, level, h, sh)),
+                          diag_level(k0, level, h, sh))
+            min_side, injector = 5, inject
+        self.levels = [top]
         Hm = H
         while True:
             ny, nx = self.levels[-1].shape
-            if min(ny, nx) <= coarsest_side or (ny - 1) % 2 or (nx - 1) % 2 or min(ny, nx) < 5:
+            if min(ny, nx) <= coarsest_side or (ny - 1) % 2 or (nx - 1) % 2 or min(ny, nx) < min_side:
                 break
             Hm = 2.0 * Hm
-            km = inject(self.levels[-1].k, 2)
+            km = injector(self.levels[-1].k, 2)
             c = ks / (Hm * Hm)
             self.levels.append(MGLevel(km.shape, km,
-                                       (lambda u, kk=km, c=c, Hm=Hm: apply_5pt(u, kk, c, Hm, sh, ks)),
-                                       diag_5pt(km, c, Hm, sh, ks)))
+                                       (lambda u, kk=km, c=c, Hm=Hm: apply_5pt(u, kk, c, Hm, sh, ks, bc)),
+                                       diag_5pt(km, c, Hm, sh, ks, bc)))
         last = self.levels[-1]
         self.lu = sla.lu_factor(_dense_matrix(last.apply, last.shape))
 
@@ -84,8 +98,12 @@ class CSLPMultigrid:
         for _ in range(self.nu1):
             u = jacobi(u, f, lv.apply, lv.diag, self.omega)
         r = f - lv.apply(u)
-        ec = self.vcycle(fw_restrict(r), m + 1)
-        u = u + bilinear_prolong(ec, lv.shape)
+        if self.bc == DIRICHLET:
+            ec = self.vcycle(fw_restrict_dirichlet(r), m + 1)
+            u = u + bilinear_prolong_dirichlet(ec, lv.shape)
+        else:
+            ec = self.vcycle(fw_restrict(r), m + 1)
+            u = u + bilinear_prolong(ec, lv.shape)
         for _ in range(self.nu2):
             u = jacobi(u, f, lv.apply, lv.diag, self.omega)
         return u

@@ -29,6 +29,14 @@ reduction of ``apply_level`` at level 1 to ``apply_5pt``, Galerkin triple
 products for the interior rows of levels 2-3, and brute-force diagonals.
 Parity unpinned: the near-boundary rows of levels >= 2 (ghost layer and zero
 padding), which the paper calls an open problem and fixes only in words.
+
+* ``apply_level_dirichlet`` / ``diag_level_dirichlet``   the level-l operator on a
+                    homogeneous Dirichlet grid (MP-1a): the Galerkin stencil at every
+                    interior unknown, zero outside.  Pins: level 1 equals the
+                    Dirichlet ``apply_5pt``; interior rows equal the Dirichlet Galerkin
+                    triple product; rows that reach the boundary differ from it (zero
+                    padding is this reading, not the exact product), parity there is
+                    pinned to the oracle only.
 """
 from __future__ import annotations
 
@@ -161,6 +169,37 @@ def diag_level(k, level, h, shift=1.0):
     d[:, 0] = db[:, 0]
     d[:, -1] = db[:, -1]
     return d
+
+
+def apply_level_dirichlet(u, k, level, h, shift=1.0):
+    """Level-l operator on a homogeneous Dirichlet grid (interior unknowns only): the
+    Galerkin stencil of Section 3.3 at every unknown, with zero values outside the grid
+    (the boundary values are zero and no boundary rows exist).  Level 1 is the 5-point
+    operator of Section 2.1 with Dirichlet data."""
+    lap, kk = stencils_2d(level, h)
+    R = lap.shape[0] // 2
+    ny, nx = u.shape
+    ue = np.zeros((ny + 2 * R, nx + 2 * R), dtype=np.complex128)
+    ue[R:R + ny, R:R + nx] = u
+    we = np.zeros_like(ue)
+    we[R:R + ny, R:R + nx] = k * k * u
+    v = np.zeros((ny, nx), dtype=np.complex128)
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            a = lap[dy + R, dx + R]
+            b = kk[dy + R, dx + R]
+            if a != 0.0:
+                v += a * ue[R + dy:R + dy + ny, R + dx:R + dx + nx]
+            if b != 0.0:
+                v -= shift * b * we[R + dy:R + dy + ny, R + dx:R + dx + nx]
+    return v
+
+
+def diag_level_dirichlet(k, level, h, shift=1.0):
+    """Diagonal of ``apply_level_dirichlet``: the stencil centre at every unknown."""
+    lap, kk = stencils_2d(level, h)
+    R = lap.shape[0] // 2
+    return lap[R, R] - shift * kk[R, R] * k * k + 0j
 
 
 def jacobi(u, f, apply_m, diag, omega):

@@ -15,10 +15,18 @@ matrices written from their definitions; 2-D application is A_y @ v @ A_x^T.
   and bilinear prolongation (coincident nodes copied, edge midpoints averaged
   from 2 coarse nodes, cell centres from 4).
 
+Homogeneous Dirichlet grids (MP-1a, Section 2.2) hold only the interior nodes: a
+grid of n unknowns is the interior of a vertex grid of n + 2 nodes whose boundary
+values are zero.  Its transfers are the ones above on that vertex grid, applied to
+the zero-extended vector and restricted to interior nodes (``*_dirichlet``):
+coarse unknown I coincides with fine unknown 2I + 1, n_coarse = (n_fine - 1) / 2.
+
 Pins (tests/test_oracle_transfers.py): Z reproduces constants and linear
 functions in the interior, <Z^T v, w> = <v, Z w>, bilinear interpolation is
 exact for bilinear functions, FW equals one quarter of the bilinear transpose,
-and Z^T A Z reproduces the printed coarse stencils.
+and Z^T A Z reproduces the printed coarse stencils; the Dirichlet variants
+reproduce constants and linear functions away from the boundary and keep the
+transpose relations.
 """
 from __future__ import annotations
 
@@ -106,3 +114,57 @@ def bilinear_prolong(e: np.ndarray, fine_shape) -> np.ndarray:
 def inject(k: np.ndarray, stride: int) -> np.ndarray:
     """Coarse-grid values at coincident nodes (used for the coarse wavenumbers)."""
     return np.ascontiguousarray(k[::stride, ::stride])
+
+
+# ---- homogeneous Dirichlet grids (interior unknowns only) ---------------------------------
+def coarse_size_dirichlet(n_fine: int) -> int:
+    if n_fine < 3 or (n_fine - 1) % 2 != 0:
+        raise ValueError(f"Dirichlet grid of {n_fine} unknowns cannot be coarsened (needs odd n >= 3)")
+    return (n_fine - 1) // 2
+
+
+def _interior(m: sp.csr_matrix) -> sp.csr_matrix:
+    """Drop the first and last row and column (the zero boundary nodes)."""
+    return sp.csr_matrix(m[1:-1, :][:, 1:-1])
+
+
+def zt_1d_dirichlet(n_fine: int) -> sp.csr_matrix:
+    """Z^T between interior unknowns: the vertex-grid rows of coarse interior nodes,
+    restricted to fine interior columns: (Z^T)[I, 2I + 1 + a] = p_a."""
+    coarse_size_dirichlet(n_fine)
+    return _interior(zt_1d(n_fine + 2))
+
+
+def fw_1d_dirichlet(n_fine: int) -> sp.csr_matrix:
+    coarse_size_dirichlet(n_fine)
+    return _interior(fw_1d(n_fine + 2))
+
+
+def bilinear_1d_dirichlet(n_fine: int) -> sp.csr_matrix:
+    coarse_size_dirichlet(n_fine)
+    return _interior(bilinear_1d(n_fine + 2))
+
+
+def deflation_restrict_dirichlet(v: np.ndarray) -> np.ndarray:
+    ny, nx = v.shape
+    return zt_1d_dirichlet(ny) @ v @ zt_1d_dirichlet(nx).T
+
+
+def deflation_prolong_dirichlet(w: np.ndarray, fine_shape) -> np.ndarray:
+    ny, nx = fine_shape
+    return (zt_1d_dirichlet(ny).T @ w) @ zt_1d_dirichlet(nx)
+
+
+def fw_restrict_dirichlet(r: np.ndarray) -> np.ndarray:
+    ny, nx = r.shape
+    return fw_1d_dirichlet(ny) @ r @ fw_1d_dirichlet(nx).T
+
+
+def bilinear_prolong_dirichlet(e: np.ndarray, fine_shape) -> np.ndarray:
+    ny, nx = fine_shape
+    return (bilinear_1d_dirichlet(ny) @ e) @ bilinear_1d_dirichlet(nx).T
+
+
+def inject_dirichlet(k: np.ndarray, stride: int) -> np.ndarray:
+    """Values at the fine unknowns that coincide with coarse unknowns: stride (I + 1) - 1."""
+    return np.ascontiguousarray(k[stride - 1::stride, stride - 1::stride])
