@@ -35,11 +35,16 @@ wavenumber injected at coincident nodes.  With ``bc = "dirichlet"`` (MP-1a,
 Section 2.2) the grids hold interior unknowns only: (n_{l-1} - 1) / 2 per side,
 the Dirichlet transfers and level operators of ``transfers`` / ``operators``.
 
-Pins (tests/test_oracle_madp.py): with the exact Galerkin coarse inverse the
-A-DEF1 operator maps A Z y to Z y; the solver's result solves the assembled
-system (dense LU) to the requested residual on small grids.  Iteration counts
-against the paper's tables: parity unpinned (setup details live in other
-papers, and the wedge geometry is synthetic).
+Pins (tests/test_oracle_madp.py, tests/test_oracle_dirichlet.py): with the exact
+Galerkin coarse inverse the A-DEF1 operator maps A Z y to Z y (both boundary
+types); the solver's result solves the assembled system (dense LU) to the
+requested residual on small grids; a level solved with as many iterations as
+unknowns (or to 1e-12) reproduces the preconditioner built on a dense inverse of
+that level; W-cycle and per-level-tolerance runs keep their call and iteration
+counts.  Iteration counts against the paper's tables: the three-level k = 100
+constant-wavenumber entries of Section 4.3.1 within one iteration; the four-
+and five-level entries differ by 2-3 iterations (setup details live in other
+papers), and the wedge geometry is synthetic: parity unpinned there.
 """
 from __future__ import annotations
 
