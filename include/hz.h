@@ -48,7 +48,9 @@ extern "C" {
 
 /* ---- enumerations ---------------------------------------------------------------- */
 #define HZ_BC_SOMMERFELD 0 /* first-order Sommerfeld rows, ghost equation of Section 2.1 */
-#define HZ_BC_DIRICHLET  1 /* homogeneous Dirichlet; only level-1 operator applies */
+#define HZ_BC_DIRICHLET  1 /* homogeneous Dirichlet (MP-1a): nx * ny interior unknowns; coarse
+                              unknown I sits at fine unknown 2I + 1, a side of n coarsens to
+                              (n - 1) / 2; every level applies its stencil with zeros outside */
 
 #define HZ_PREC_FP64   0   /* every vector and scalar in complex FP64 */
 #define HZ_PREC_MIXED  1   /* preconditioner (lines 5-14 of Algorithm 1) and inner levels in
@@ -159,6 +161,7 @@ int hz_config_init(hz_config* cfg);
  * sub-hierarchies with an FP64 dense coarsest inverse, and all workspace for nrhs <=
  * cfg->max_rhs.  k_dev: nx*ny real FP64 wavenumbers, device, read during the call only.
  * stream: cudaStream_t used by every later call on the handle.
+ * (Dirichlet grids: n_l = (n_{l-1} - 1) / 2, wavenumber injected at fine unknown 2I + 1.)
  * Errors: HZ_EINVAL (sizes not coarsenable, h <= 0, non-finite or non-positive k,
  * bad config), HZ_ENOMEM, HZ_ECUDA. */
 int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, void* stream,

@@ -1,6 +1,7 @@
 // extern "C" entry points declared in include/hz.h: argument validation, status codes,
 // and dispatch to the runtime in hz_core.cpp.
 #include <chrono>
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -97,12 +98,15 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
     if (!(t >= 0 && t < 1)) return bad("level_tol entries must be in [0, 1)");
     if (t > 0 && (l < 3 || l >= c.levels)) return bad("level_tol is set for levels 3 .. levels-1 only");
   }
-  if (g.bc == HZ_BC_DIRICHLET && c.levels != 1) return bad("Dirichlet grids support the level-1 operator only");
   int nx = g.nx, ny = g.ny;
+  const bool dir = g.bc == HZ_BC_DIRICHLET;
   for (int l = 1; l < c.levels; ++l) {
-    if ((nx - 1) % 2 || (ny - 1) % 2 || nx < 5 || ny < 5) return bad("grid cannot be coarsened levels-1 times (needs odd sizes >= 5)");
-    nx = (nx + 1) / 2;
-    ny = (ny + 1) / 2;
+    // vertex grids: coarse node I at fine node 2I; Dirichlet grids (interior unknowns): 2I + 1
+    if ((nx - 1) % 2 || (ny - 1) % 2 || std::min(nx, ny) < (dir ? 3 : 5))
+      return bad(dir ? "Dirichlet grid cannot be coarsened levels-1 times (needs odd sizes >= 3)"
+                     : "grid cannot be coarsened levels-1 times (needs odd sizes >= 5)");
+    nx = dir ? (nx - 1) / 2 : (nx + 1) / 2;
+    ny = dir ? (ny - 1) / 2 : (ny + 1) / 2;
   }
   hz_handle_s* hs = new (std::nothrow) hz_handle_s();
   if (!hs) return HZ_ENOMEM;
@@ -111,39 +115,7 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   H->cfg = c;
   H->ctx.s = reinterpret_cast<cudaStream_t>(stream);
   H->ctx.prof = &H->prof;
-  int st = HZ_OK;
-  if (g.bc == HZ_BC_DIRICHLET) {
-    // level-1 operator only: keep k and the geometry
-    H->lv.resize(1);
-    Level& L = H->lv[0];
-    L.l = 1;
-    L.nx = g.nx;
-    L.ny = g.ny;
-    L.n = (size_t)g.nx * g.ny;
-    L.H = g.h;
-    L.ks = 1;
-    galerkin_masks(1, &L.R, L.m, L.L);
-    std::vector<double> k(L.n);
-    cudaError_t e = cudaMemcpy(k.data(), k_dev, L.n * 8, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) st = status_of(e, "hz_setup");
-    for (size_t i = 0; !st && i < k.size(); ++i)
-      if (!(std::isfinite(k[i]) && k[i] > 0)) st = bad("wavenumber field must be finite and positive");
-    void* p = nullptr;
-    if (!st) st = dalloc(H, &p, L.n * 8);
-    if (!st) {
-      L.k_d = (double*)p;
-      st = status_of(cudaMemcpy(p, k.data(), L.n * 8, cudaMemcpyHostToDevice), "hz_setup");
-    }
-    std::vector<float> kf(k.begin(), k.end());
-    if (!st) st = dalloc(H, &p, L.n * 4);
-    if (!st) {
-      L.k_f = (float*)p;
-      st = status_of(cudaMemcpy(p, kf.data(), L.n * 4, cudaMemcpyHostToDevice), "hz_setup");
-    }
-    H->nbmax = c.max_rhs;
-  } else {
-    st = setup(H, k_dev);
-  }
+  const int st = setup(H, k_dev);
   if (st) {
     destroy(H);
     delete hs;
@@ -308,7 +280,7 @@ int hz_defl_restrict(hz_handle hp, int level, int dtype, const void* v, void* vh
   if (int s = check_nrhs(H_, nrhs, false)) return s;
   if (!v || !vhat) return bad("null vector");
   Level& L = H_->lv[level - 1];
-  return status_of(launch_defl_restrict(H_->ctx, dtype, dtype, L.nx, L.ny, v, vhat, nrhs), "hz_defl_restrict");
+  return status_of(launch_defl_restrict(H_->ctx, dtype, dtype, L.nx, L.ny, v, vhat, nrhs, L.bc), "hz_defl_restrict");
 }
 
 int hz_defl_prolong(hz_handle hp, int level, int dtype, const void* w, void* t, int nrhs) {
@@ -319,7 +291,7 @@ int hz_defl_prolong(hz_handle hp, int level, int dtype, const void* w, void* t, 
   if (int s = check_nrhs(H_, nrhs, false)) return s;
   if (!w || !t) return bad("null vector");
   Level& L = H_->lv[level - 1];
-  return status_of(launch_defl_prolong(H_->ctx, dtype, L.nx, L.ny, w, t, nrhs), "hz_defl_prolong");
+  return status_of(launch_defl_prolong(H_->ctx, dtype, L.nx, L.ny, w, t, nrhs, L.bc), "hz_defl_prolong");
 }
 
 int hz_defl_prolong_residual(hz_handle hp, int level, int dtype, const void* vtil, const void* v, void* t, void* rtil,

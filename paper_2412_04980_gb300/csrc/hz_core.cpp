@@ -186,7 +186,7 @@ OpDesc Level::opA(int dt) const {
   d.nx = nx;
   d.ny = ny;
   d.R = R;
-  d.bc = 0;
+  d.bc = bc;
   d.H = H;
   d.ks = ks;
   d.c = ks / (H * H);  // = 1 / h^2 on every level (Galerkin scale 4^(l-1) over H_l^2)
@@ -322,11 +322,24 @@ static int upload_k(Handle* h, const std::vector<double>& k, double** kd, float*
   return HZ_OK;
 }
 
-static std::vector<double> inject(const std::vector<double>& k, int nx, int ny) {
-  int cx = (nx + 1) / 2, cy = (ny + 1) / 2;
+// Nodes per side of the next coarser grid: vertex grids keep their boundary nodes (coarse node I
+// at fine node 2I), homogeneous Dirichlet grids hold interior unknowns only (coarse unknown I at
+// fine unknown 2I + 1).
+static int coarse_side(int n, int bc) { return bc == HZ_BC_DIRICHLET ? (n - 1) / 2 : (n + 1) / 2; }
+
+// The multigrid CSLP coarsens while both sides are odd, above the coarsest side and large enough
+// to halve (a vertex grid keeps at least 3 nodes, a Dirichlet grid at least 1 unknown).
+static bool mg_coarsens(int mx, int my, int coarsest_side, int bc) {
+  if (std::min(mx, my) <= coarsest_side || (mx - 1) % 2 || (my - 1) % 2) return false;
+  return std::min(mx, my) >= (bc == HZ_BC_DIRICHLET ? 3 : 5);
+}
+
+// Wavenumbers of the next coarser grid: injection at the coincident nodes.
+static std::vector<double> inject(const std::vector<double>& k, int nx, int ny, int bc) {
+  const int cx = coarse_side(nx, bc), cy = coarse_side(ny, bc), o = bc == HZ_BC_DIRICHLET ? 1 : 0;
   std::vector<double> out((size_t)cx * cy);
   for (int j = 0; j < cy; ++j)
-    for (int i = 0; i < cx; ++i) out[(size_t)j * cx + i] = k[(size_t)(2 * j) * nx + 2 * i];
+    for (int i = 0; i < cx; ++i) out[(size_t)j * cx + i] = k[(size_t)(2 * j + o) * nx + 2 * i + o];
   return out;
 }
 
@@ -381,9 +394,9 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       const bool general = !(cfg.mg_nu1 == 1 && cfg.mg_nu2 == 1);
       if (general) total += 2 * bn * ep;
       for (;;) {
-        if (std::min(mx, my) <= cfg.mg_coarsest_side || (mx - 1) % 2 || (my - 1) % 2 || std::min(mx, my) < 5) break;
-        mx = (mx + 1) / 2;
-        my = (my + 1) / 2;
+        if (!mg_coarsens(mx, my, cfg.mg_coarsest_side, g.bc)) break;
+        mx = coarse_side(mx, g.bc);
+        my = coarse_side(my, g.bc);
         const size_t m = (size_t)mx * my;
         total += m * 12 + 2 * (size_t)nb * m * ep + (general ? 2 * (size_t)nb * m * ep : 0);
       }
@@ -408,8 +421,8 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       }
     }
     if (l < ml) {
-      nx = (nx + 1) / 2;
-      ny = (ny + 1) / 2;
+      nx = coarse_side(nx, g.bc);
+      ny = coarse_side(ny, g.bc);
     }
   }
   total += dot_ws_bytes((int)maxnv, nb) + scal(1) + (size_t)nb * g.nx * g.ny * 16 + sizeof(int);
@@ -438,6 +451,7 @@ int setup(Handle* h, const double* k_dev) {
   for (int l = 1; l <= ml; ++l) {
     Level& L = h->lv[l - 1];
     L.l = l;
+    L.bc = g.bc;
     L.nx = nx;
     L.ny = ny;
     L.n = (size_t)nx * ny;
@@ -453,9 +467,9 @@ int setup(Handle* h, const double* k_dev) {
       L.dvec = L.dpre = L.dx = mixed ? C64 : C128;
     }
     if (l < ml) {
-      kl = inject(kl, nx, ny);
-      nx = (nx + 1) / 2;
-      ny = (ny + 1) / 2;
+      kl = inject(kl, nx, ny, g.bc);
+      nx = coarse_side(nx, g.bc);
+      ny = coarse_side(ny, g.bc);
     }
   }
   // per-level workspace
@@ -494,25 +508,25 @@ int setup(Handle* h, const double* k_dev) {
       {
         int fx = g.nx, fy = g.ny;
         for (int q = 1; q < l; ++q) {
-          km = inject(km, fx, fy);
-          fx = (fx + 1) / 2;
-          fy = (fy + 1) / 2;
+          km = inject(km, fx, fy, g.bc);
+          fx = coarse_side(fx, g.bc);
+          fy = coarse_side(fy, g.bc);
         }
       }
       int mx = L.nx, my = L.ny;
       double Hm = L.H;
       const bool general = !(cfg.mg_nu1 == 1 && cfg.mg_nu2 == 1);
       for (;;) {
-        if (std::min(mx, my) <= cfg.mg_coarsest_side || (mx - 1) % 2 || (my - 1) % 2 || std::min(mx, my) < 5) break;
-        km = inject(km, mx, my);
-        mx = (mx + 1) / 2;
-        my = (my + 1) / 2;
+        if (!mg_coarsens(mx, my, cfg.mg_coarsest_side, g.bc)) break;
+        km = inject(km, mx, my, g.bc);
+        mx = coarse_side(mx, g.bc);
+        my = coarse_side(my, g.bc);
         Hm *= 2.0;
         MGLevel q;
         q.op.nx = mx;
         q.op.ny = my;
         q.op.R = 1;
-        q.op.bc = 0;
+        q.op.bc = g.bc;
         q.op.c = L.ks / (Hm * Hm);
         q.op.H = Hm;
         q.op.ks = L.ks;
@@ -800,9 +814,9 @@ int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, 
       CK(cudaMemsetAsync(a, 0, nn * eb, c.s));
     }
     CK(launch_level_op(c, q.op, 1, dt, dt, dt, a, fm, q.tmp, 0.0, nb));
-    CK(launch_fw(c, dt, q.op.nx, q.op.ny, q.tmp, L.mg[m + 1].f, nb));
+    CK(launch_fw(c, dt, q.op.nx, q.op.ny, q.tmp, L.mg[m + 1].f, nb, q.op.bc));
     CS(rec(m + 1, L.mg[m + 1].f, L.mg[m + 1].e));
-    CK(launch_prolong_add(c, dt, q.op.nx, q.op.ny, L.mg[m + 1].e, a, nb));
+    CK(launch_prolong_add(c, dt, q.op.nx, q.op.ny, L.mg[m + 1].e, a, nb, q.op.bc));
     for (int s = 0; s < h->cfg.mg_nu2; ++s) {
       CK(launch_level_op(c, q.op, 2, dt, dt, dt, a, fm, b, om, nb));
       std::swap(a, b);
@@ -1219,7 +1233,7 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
     return cslp_inverse(h, l, src, xout, nullptr, nb);
   }
   Level& C = h->lv[l];
-  CK(launch_defl_restrict(c, dv, C.dvec, L.nx, L.ny, v, C.b, nb));                 // line 5
+  CK(launch_defl_restrict(c, dv, C.dvec, L.nx, L.ny, v, C.b, nb, L.bc));           // line 5
   CS(coarse_solve_graph(h, l + 1, nb));                                            // lines 6-10
   CK(launch_defl_prolong_resid(c, L.opA(L.dpre), L.dpre, dv, C.x, C.nx, C.ny, v, L.t, L.rt, nb));  // 11-13
   return cslp_inverse(h, l, L.rt, xout, L.t, nb);                                  // lines 14-15

@@ -28,6 +28,7 @@ struct Scalars {
 
 struct Level {
   int l = 1, nx = 0, ny = 0;
+  int bc = 0;  // HZ_BC_* of the grid: Dirichlet levels hold interior unknowns only
   size_t n = 0;
   int R = 1;
   double H = 0, ks = 1;

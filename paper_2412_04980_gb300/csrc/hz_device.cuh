@@ -14,7 +14,9 @@
 //           the 5-point row at the level spacing (Section 3.3, "Boundary").
 // Cells of the extended tile outside the grid are zero except the first ghost layer
 // (one coordinate outside by exactly one); ghost wavenumbers are zero, so the
-// wavenumber part sees zeros outside the grid.
+// wavenumber part sees zeros outside the grid.  Homogeneous Dirichlet grids (bc = 1,
+// interior unknowns only) have no ghost layer and no boundary rows: the level's stencil
+// applies at every node with zeros outside.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,8 +75,11 @@ struct OpP {
   const T* k;       // wavenumber, nx*ny
 };
 
+// Physical boundary sides a node touches.  Dirichlet grids hold interior unknowns only, so
+// none of their nodes takes a boundary row: every node uses the level's stencil, zero outside.
 template <typename T>
 __device__ __forceinline__ int bsides(const OpP<T>& P, int gx, int gy) {
+  if (P.bc != 0) return 0;
   return (gx == 0) + (gx == P.nx - 1) + (gy == 0) + (gy == P.ny - 1);
 }
 
@@ -91,9 +96,11 @@ __device__ __forceinline__ cx<T> op_diag(const OpP<T>& P, int gx, int gy) {
     return mk<T>(dre, dim);
   } else {
     T lap = P.c * T(2) * P.l[R] * P.m[R];
-    T extra = P.c * (P.l[R] * P.m[R + 2] + P.m[R] * P.l[R + 2]);
-    int near = (gx == 1) + (gx == P.nx - 2) + (gy == 1) + (gy == P.ny - 2);
-    lap += extra * T(near);
+    if (P.bc == 0) {  // a Sommerfeld ghost two steps away holds this node with coefficient 1
+      T extra = P.c * (P.l[R] * P.m[R + 2] + P.m[R] * P.l[R + 2]);
+      int near = (gx == 1) + (gx == P.nx - 2) + (gy == 1) + (gy == P.ny - 2);
+      lap += extra * T(near);
+    }
     T kc = P.m[R] * P.m[R] * k2;
     return mk<T>(lap - P.sr * kc, -P.si * kc);
   }

@@ -98,11 +98,13 @@ cudaError_t launch_jacobi_zero(Ctx& c, const OpDesc& op, int dt, const void* f, 
 // t = Z vtil (coarse vtil, dtype tcomp), rtil = v - A t.  v has dtype tv; t, rtil dtype tcomp.
 cudaError_t launch_defl_prolong_resid(Ctx& c, const OpDesc& op, int tcomp, int tv, const void* vtil,
                                       int ncx, int ncy, const void* v, void* t, void* rtil, int nrhs);
+// Transfers take the grid's boundary type: vertex grids (bc 0) put coarse node I at fine node 2I,
+// Dirichlet grids (bc 1, interior unknowns) at fine unknown 2I + 1.
 // t = Z w (plain prolongation), same dtype.
-cudaError_t launch_defl_prolong(Ctx& c, int dt, int nx, int ny, const void* w, void* t, int nrhs);
+cudaError_t launch_defl_prolong(Ctx& c, int dt, int nx, int ny, const void* w, void* t, int nrhs, int bc = 0);
 // vhat = Z^T v; v dtype tin, vhat dtype tout (arithmetic in tout).
 cudaError_t launch_defl_restrict(Ctx& c, int tin, int tout, int nx, int ny, const void* v, void* vhat,
-                                 int nrhs);
+                                 int nrhs, int bc = 0);
 // Fused multigrid kernels, V(1,1) with zero initial guess.
 // down: fc = FW(f - Op(omega f / D)) on the next coarser grid (ncx x ncy)
 cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void* fc, double omega, int nrhs);
@@ -110,8 +112,8 @@ cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void
 cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const void* ec, void* y,
                          double omega, const void* add, int tadd, void* yout2, int tout2, int nrhs);
 // General multigrid pieces: fc = FW(r); u += P ec.
-cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs);
-cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs);
+cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs, int bc = 0);
+cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs, int bc = 0);
 
 // ---- vector launchers (kern_vec.cu) -------------------------------------------------
 // Dense FP64 complex matvec y = A x with dtype conversions (coarsest multigrid solve).

@@ -18,6 +18,10 @@ constexpr int OXT = 32, OYT = 16;       // output tile of the fine-grid kernels
 
 __host__ __device__ inline int floordiv2(int a) { return (a >= 0) ? (a >> 1) : -((-a + 1) >> 1); }
 
+// Coarse nodes per side: vertex grids keep both boundary nodes, (n + 1) / 2; Dirichlet grids hold
+// interior unknowns only, (n - 1) / 2.
+inline int coarse_n(int n, int bc) { return bc != 0 ? (n - 1) / 2 : (n + 1) / 2; }
+
 template <typename T>
 OpP<T> make_op(const hz::OpDesc& d) {
   OpP<T> p;
@@ -71,11 +75,11 @@ struct UpSrc {
   OpP<T> P;
   T omega;
   const cx<T>* Es;
-  int EW, Imin, Jmin;
+  int EW, Imin, Jmin, dof;  // dof = 1 on Dirichlet grids (coarse unknown I at fine unknown 2I + 1)
   __device__ __forceinline__ cx<T> operator()(int gx, int gy) const {
     cx<T> u = omega * cdiv(f[(size_t)gy * P.nx + gx], op_diag<T, R>(P, gx, gy));
-    int I = floordiv2(gx), J = floordiv2(gy);
-    int ex = gx - 2 * I, ey = gy - 2 * J;
+    int I = floordiv2(gx + dof), J = floordiv2(gy + dof);
+    int ex = gx + dof - 2 * I, ey = gy + dof - 2 * J;
     const cx<T>* e = Es + (J - Jmin) * EW + (I - Imin);
     cx<T> a = e[0];
     if (ex) a = T(0.5) * (a + e[1]);
@@ -155,15 +159,18 @@ __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const c
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny;
   const size_t offc = (size_t)blockIdx.z * ncx * ncy;
   const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
-  const int Imin = floordiv2(ox0 - R - 1), Imax = floordiv2(ox0 + OXT + R + 1);
-  const int Jmin = floordiv2(oy0 - R - 1), Jmax = floordiv2(oy0 + OYT + R + 1);
+  // coarse indices below are those of the vertex grid; on a Dirichlet grid (dof = 1) fine unknown
+  // g is vertex g + 1 and coarse unknown I is vertex I + 1 (its boundary vertices hold zero)
+  const int dof = P.bc != 0;
+  const int Imin = floordiv2(ox0 + dof - R - 1), Imax = floordiv2(ox0 + dof + OXT + R + 1);
+  const int Jmin = floordiv2(oy0 + dof - R - 1), Jmax = floordiv2(oy0 + dof + OYT + R + 1);
   const int CW = Imax - Imin + 1, CH = Jmax - Jmin + 1;
   TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
   cx<T>* Cs = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OXT, OYT));
   const int tid = threadIdx.y * BX + threadIdx.x;
   for (int idx = tid; idx < CW * CH; idx += BX * BY) {
     int cj = idx / CW, ci = idx - cj * CW;
-    int I = Imin + ci, J = Jmin + cj;
+    int I = Imin + ci - dof, J = Jmin + cj - dof;
     Cs[idx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? vtil[offc + (size_t)J * ncx + I] : mk<T>(T(0), T(0));
   }
   __syncthreads();
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const c
     const int gx0 = ox0 - R, gy0 = oy0 - R;
     for (int idx = tid; idx < CH * WX; idx += BX * BY) {
       const int cj = idx / WX, cxx = idx - cj * WX;
-      const int gx = gx0 + cxx;
+      const int gx = gx0 + cxx + dof;
       const cx<T>* r = Cs + cj * CW + (floordiv2(gx) - Imin);
       Xs[idx] = (gx & 1) ? T(0.5) * (r[0] + r[1]) : T(0.75) * r[0] + T(0.125) * (r[-1] + r[1]);
     }
@@ -187,8 +194,9 @@ __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const c
       const int gx = gx0 + cxx, gy = gy0 + cy;
       cx<T> u = mk<T>(T(0), T(0)), w = u;
       if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) {
-        const cx<T>* c = Xs + (floordiv2(gy) - Jmin) * WX + cxx;
-        u = (gy & 1) ? T(0.5) * (c[0] + c[WX]) : T(0.75) * c[0] + T(0.125) * (c[-WX] + c[WX]);
+        const int ge = gy + dof;
+        const cx<T>* c = Xs + (floordiv2(ge) - Jmin) * WX + cxx;
+        u = (ge & 1) ? T(0.5) * (c[0] + c[WX]) : T(0.75) * c[0] + T(0.125) * (c[-WX] + c[WX]);
         if (R >= 2) {
           const T k = P.k[(size_t)gy * P.nx + gx];
           w = (k * k) * u;
@@ -228,19 +236,20 @@ __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const c
 // plain t = Z w (Algorithm 1, line 11)
 template <typename T>
 __global__ void __launch_bounds__(256) k_defl_prolong(const cx<T>* __restrict__ w, int ncx, int ncy,
-                                                      cx<T>* __restrict__ t, int nx, int ny) {
+                                                      cx<T>* __restrict__ t, int nx, int ny, int dof) {
   const size_t n = (size_t)nx * ny;
   const size_t off = (size_t)blockIdx.y * n, offc = (size_t)blockIdx.y * ncx * ncy;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    int gy = (int)(i / nx), gx = (int)(i - (size_t)gy * nx);
+    // vertex-grid coordinates (dof = 1 on Dirichlet grids: unknown g is vertex g + 1)
+    int gy = (int)(i / nx) + dof, gx = (int)(i % nx) + dof;
     int I0 = floordiv2(gx - 1), I1 = floordiv2(gx + 2), J0 = floordiv2(gy - 1), J1 = floordiv2(gy + 2);
     cx<T> acc = mk<T>(T(0), T(0));
     for (int J = J0; J <= J1; ++J) {
-      if (J < 0 || J >= ncy) continue;
+      if (J - dof < 0 || J - dof >= ncy) continue;
       cx<T> row = mk<T>(T(0), T(0));
       for (int I = I0; I <= I1; ++I) {
-        if (I < 0 || I >= ncx) continue;
-        row = row + pw<T>(gx - 2 * I) * w[offc + (size_t)J * ncx + I];
+        if (I - dof < 0 || I - dof >= ncx) continue;
+        row = row + pw<T>(gx - 2 * I) * w[offc + (size_t)(J - dof) * ncx + (I - dof)];
       }
       acc = acc + pw<T>(gy - 2 * J) * row;
     }
@@ -252,14 +261,15 @@ __global__ void __launch_bounds__(256) k_defl_prolong(const cx<T>* __restrict__ 
 constexpr int RXC = 32, RYC = 16;
 template <typename TI, typename T>
 __global__ void __launch_bounds__(BX* BY) k_defl_restrict(const cx<TI>* __restrict__ v, int nx, int ny,
-                                                            cx<T>* __restrict__ vhat, int ncx, int ncy) {
+                                                            cx<T>* __restrict__ vhat, int ncx, int ncy, int dof) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int FW = 2 * RXC + 3, FH = 2 * RYC + 3;
   cx<T>* F = reinterpret_cast<cx<T>*>(smem);
   cx<T>* XR = F + FW * FH;
   const size_t off = (size_t)blockIdx.z * nx * ny, offc = (size_t)blockIdx.z * ncx * ncy;
   const int x0c = blockIdx.x * RXC, y0c = blockIdx.y * RYC;
-  const int fx0 = 2 * x0c - 2, fy0 = 2 * y0c - 2;
+  // coarse unknown I is centred on fine unknown 2I + dof (dof = 1 on Dirichlet grids)
+  const int fx0 = 2 * x0c - 2 + dof, fy0 = 2 * y0c - 2 + dof;
   const int tid = threadIdx.y * BX + threadIdx.x;
   for (int idx = tid; idx < FW * FH; idx += BX * BY) {
     int fy = idx / FW, fx = idx - fy * FW;
@@ -294,7 +304,9 @@ __global__ void __launch_bounds__(BX* BY) k_mg_down(OpP<T> P, const cx<T>* __res
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny, offc = (size_t)blockIdx.z * ncx * ncy;
   f += off;
   const int x0c = blockIdx.x * DXC, y0c = blockIdx.y * DYC;
-  const int ox0 = 2 * x0c - 1, oy0 = 2 * y0c - 1;
+  // full weighting centred on fine node 2I (2I + 1 on Dirichlet grids)
+  const int dof = P.bc != 0;
+  const int ox0 = 2 * x0c - 1 + dof, oy0 = 2 * y0c - 1 + dof;
   TileView<T, R> t = make_tile<T, R>(smem, OX, OY, ox0, oy0);
   cx<T>* RS = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OX, OY));
   tile_fill<T, R>(t, P, JacZeroSrc<T, R>{f, P, omega});
@@ -353,19 +365,21 @@ __global__ void __launch_bounds__(BX* BY) k_mg_up(OpP<T> P, const cx<T>* __restr
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny, offc = (size_t)blockIdx.z * ncx * ncy;
   f += off;
   const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
-  const int Imin = floordiv2(ox0 - R), Imax = floordiv2(ox0 + OXT + R - 1) + 1;
-  const int Jmin = floordiv2(oy0 - R), Jmax = floordiv2(oy0 + OYT + R - 1) + 1;
+  // vertex-grid coarse indices (Dirichlet: fine unknown g is vertex g + 1, coarse I is vertex I + 1)
+  const int dof = P.bc != 0;
+  const int Imin = floordiv2(ox0 + dof - R), Imax = floordiv2(ox0 + dof + OXT + R - 1) + 1;
+  const int Jmin = floordiv2(oy0 + dof - R), Jmax = floordiv2(oy0 + dof + OYT + R - 1) + 1;
   const int EW = Imax - Imin + 1, EH = Jmax - Jmin + 1;
   TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
   cx<T>* Es = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(OXT, OYT));
   const int tid = threadIdx.y * BX + threadIdx.x;
   for (int idx = tid; idx < EW * EH; idx += BX * BY) {
     int cj = idx / EW, ci = idx - cj * EW;
-    int I = Imin + ci, J = Jmin + cj;
+    int I = Imin + ci - dof, J = Jmin + cj - dof;
     Es[idx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[offc + (size_t)J * ncx + I] : mk<T>(T(0), T(0));
   }
   __syncthreads();
-  tile_fill<T, R>(t, P, UpSrc<T, R>{f, P, omega, Es, EW, Imin, Jmin});
+  tile_fill<T, R>(t, P, UpSrc<T, R>{f, P, omega, Es, EW, Imin, Jmin, dof});
   auto emit = [&](int ox, int oy, cx<T> val) {
     const int gx = ox0 + ox, gy = oy0 + oy;
     const size_t i = (size_t)gy * P.nx + gx;
@@ -396,17 +410,17 @@ __global__ void __launch_bounds__(BX* BY) k_mg_up(OpP<T> P, const cx<T>* __restr
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fw(const cx<T>* __restrict__ r, int nx, int ny, cx<T>* __restrict__ rc,
-                                            int ncx, int ncy) {
+                                            int ncx, int ncy, int dof) {
   const size_t nc = (size_t)ncx * ncy;
   const size_t off = (size_t)blockIdx.y * nx * ny, offc = (size_t)blockIdx.y * nc;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nc; i += (size_t)gridDim.x * blockDim.x) {
     int J = (int)(i / ncx), I = (int)(i - (size_t)J * ncx);
     cx<T> s = mk<T>(T(0), T(0));
     for (int b = -1; b <= 1; ++b) {
-      int gy = 2 * J + b;
+      int gy = 2 * J + b + dof;  // centred on fine 2J (2J + 1 on Dirichlet grids)
       if (gy < 0 || gy >= ny) continue;
       for (int a = -1; a <= 1; ++a) {
-        int gx = 2 * I + a;
+        int gx = 2 * I + a + dof;
         if (gx < 0 || gx >= nx) continue;
         T w = T((2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b)));
         s = s + w * r[off + (size_t)gy * nx + gx];
@@ -418,18 +432,23 @@ __global__ void __launch_bounds__(256) k_fw(const cx<T>* __restrict__ r, int nx,
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(const cx<T>* __restrict__ ec, int ncx, int ncy,
-                                                     cx<T>* __restrict__ u, int nx, int ny) {
+                                                     cx<T>* __restrict__ u, int nx, int ny, int dof) {
   const size_t n = (size_t)nx * ny;
   const size_t off = (size_t)blockIdx.y * n, offc = (size_t)blockIdx.y * ncx * ncy;
+  // coarse value at vertex-grid coarse index (I, J); zero at the vertices a Dirichlet grid omits
+  auto E = [&](int I, int J) -> cx<T> {
+    I -= dof;
+    J -= dof;
+    return (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[offc + (size_t)J * ncx + I] : mk<T>(T(0), T(0));
+  };
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    int gy = (int)(i / nx), gx = (int)(i - (size_t)gy * nx);
+    int gy = (int)(i / nx) + dof, gx = (int)(i % nx) + dof;
     int I = gx >> 1, J = gy >> 1, ex = gx & 1, ey = gy & 1;
-    const cx<T>* e = ec + offc + (size_t)J * ncx + I;
-    cx<T> a = e[0];
-    if (ex) a = T(0.5) * (a + e[1]);
+    cx<T> a = E(I, J);
+    if (ex) a = T(0.5) * (a + E(I + 1, J));
     if (ey) {
-      cx<T> b = e[ncx];
-      if (ex) b = T(0.5) * (b + e[ncx + 1]);
+      cx<T> b = E(I, J + 1);
+      if (ex) b = T(0.5) * (b + E(I + 1, J + 1));
       a = T(0.5) * (a + b);
     }
     u[off + i] = u[off + i] + a;
@@ -557,22 +576,23 @@ cudaError_t launch_defl_prolong_resid(Ctx& c, const OpDesc& op, int tcomp, int t
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_defl_prolong(Ctx& c, int dt, int nx, int ny, const void* w, void* t, int nrhs) {
-  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+cudaError_t launch_defl_prolong(Ctx& c, int dt, int nx, int ny, const void* w, void* t, int nrhs, int bc) {
+  const int dof = bc != 0;
+  int ncx = coarse_n(nx, bc), ncy = coarse_n(ny, bc);
   size_t n = (size_t)nx * ny;
   ProfScope ps(c, F_DEFL_PROLONG, (double)nrhs * n * elem_bytes(dt) * 1.25);
   if (dt == C128)
     k_defl_prolong<double><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(w), ncx, ncy,
-                                                                    reinterpret_cast<cx<double>*>(t), nx, ny);
+                                                                    reinterpret_cast<cx<double>*>(t), nx, ny, dof);
   else
     k_defl_prolong<float><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<float>*>(w), ncx, ncy,
-                                                                   reinterpret_cast<cx<float>*>(t), nx, ny);
+                                                                   reinterpret_cast<cx<float>*>(t), nx, ny, dof);
   return cudaGetLastError();
 }
 
 template <typename TI, typename T>
-static cudaError_t dr_t(Ctx& c, int nx, int ny, const void* v, void* vhat, int nrhs) {
-  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+static cudaError_t dr_t(Ctx& c, int nx, int ny, const void* v, void* vhat, int nrhs, int bc) {
+  int ncx = coarse_n(nx, bc), ncy = coarse_n(ny, bc);
   constexpr int FW = 2 * RXC + 3, FH = 2 * RYC + 3;
   size_t sm = sizeof(cx<T>) * (FW * FH + FH * RXC);
   cudaError_t e = set_smem(k_defl_restrict<TI, T>, sm);
@@ -580,20 +600,21 @@ static cudaError_t dr_t(Ctx& c, int nx, int ny, const void* v, void* vhat, int n
   ProfScope ps(c, F_DEFL_RESTRICT, (double)nrhs * ((double)nx * ny * sizeof(cx<TI>) + (double)ncx * ncy * sizeof(cx<T>)));
   dim3 grid((ncx + RXC - 1) / RXC, (ncy + RYC - 1) / RYC, nrhs);
   k_defl_restrict<TI, T><<<grid, dim3(BX, BY), sm, c.s>>>(reinterpret_cast<const cx<TI>*>(v), nx, ny,
-                                                          reinterpret_cast<cx<T>*>(vhat), ncx, ncy);
+                                                          reinterpret_cast<cx<T>*>(vhat), ncx, ncy, bc != 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_defl_restrict(Ctx& c, int tin, int tout, int nx, int ny, const void* v, void* vhat, int nrhs) {
-  if (tin == C128 && tout == C128) return dr_t<double, double>(c, nx, ny, v, vhat, nrhs);
-  if (tin == C64 && tout == C64) return dr_t<float, float>(c, nx, ny, v, vhat, nrhs);
-  if (tin == C128 && tout == C64) return dr_t<double, float>(c, nx, ny, v, vhat, nrhs);
+cudaError_t launch_defl_restrict(Ctx& c, int tin, int tout, int nx, int ny, const void* v, void* vhat, int nrhs,
+                                 int bc) {
+  if (tin == C128 && tout == C128) return dr_t<double, double>(c, nx, ny, v, vhat, nrhs, bc);
+  if (tin == C64 && tout == C64) return dr_t<float, float>(c, nx, ny, v, vhat, nrhs, bc);
+  if (tin == C128 && tout == C64) return dr_t<double, float>(c, nx, ny, v, vhat, nrhs, bc);
   return cudaErrorInvalidValue;
 }
 
 template <typename T, int R>
 static cudaError_t down_r(Ctx& c, const OpDesc& d, const void* f, void* fc, double omega, int nrhs) {
-  int ncx = (d.nx + 1) / 2, ncy = (d.ny + 1) / 2;
+  int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
   constexpr int OX = 2 * DXC + 1, OY = 2 * DYC + 1;
   size_t sm = tile_smem_bytes<T, R>(OX, OY) + sizeof(cx<T>) * OX * OY;
   cudaError_t e = set_smem(k_mg_down<T, R>, sm);
@@ -621,7 +642,7 @@ cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void
 template <typename T, int R>
 static cudaError_t up_r(Ctx& c, const OpDesc& d, const void* f, const void* ec, void* y, double omega,
                         const void* add, int nrhs) {
-  int ncx = (d.nx + 1) / 2, ncy = (d.ny + 1) / 2;
+  int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
   const int EW = (OXT + 2 * R) / 2 + 3, EH = (OYT + 2 * R) / 2 + 3;
   size_t sm = tile_smem_bytes<T, R>(OXT, OYT) + sizeof(cx<T>) * EW * EH;
   cudaError_t e = set_smem(k_mg_up<T, R>, sm);
@@ -653,29 +674,31 @@ cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs) {
-  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs, int bc) {
+  const int dof = bc != 0;
+  int ncx = coarse_n(nx, bc), ncy = coarse_n(ny, bc);
   size_t nc = (size_t)ncx * ncy;
   ProfScope ps(c, F_MISC, (double)nrhs * ((double)nx * ny + nc) * elem_bytes(dt));
   if (dt == C128)
     k_fw<double><<<dim3(grid1d(nc), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(r), nx, ny,
-                                                           reinterpret_cast<cx<double>*>(rc), ncx, ncy);
+                                                           reinterpret_cast<cx<double>*>(rc), ncx, ncy, dof);
   else
     k_fw<float><<<dim3(grid1d(nc), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<float>*>(r), nx, ny,
-                                                          reinterpret_cast<cx<float>*>(rc), ncx, ncy);
+                                                          reinterpret_cast<cx<float>*>(rc), ncx, ncy, dof);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs) {
-  int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs, int bc) {
+  const int dof = bc != 0;
+  int ncx = coarse_n(nx, bc), ncy = coarse_n(ny, bc);
   size_t n = (size_t)nx * ny;
   ProfScope ps(c, F_MISC, (double)nrhs * (2.0 * n + (double)ncx * ncy) * elem_bytes(dt));
   if (dt == C128)
     k_prolong_add<double><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(ec), ncx, ncy,
-                                                                   reinterpret_cast<cx<double>*>(u), nx, ny);
+                                                                   reinterpret_cast<cx<double>*>(u), nx, ny, dof);
   else
     k_prolong_add<float><<<dim3(grid1d(n), nrhs), 256, 0, c.s>>>(reinterpret_cast<const cx<float>*>(ec), ncx, ncy,
-                                                                  reinterpret_cast<cx<float>*>(u), nx, ny);
+                                                                  reinterpret_cast<cx<float>*>(u), nx, ny, dof);
   return cudaGetLastError();
 }
 

@@ -161,3 +161,28 @@ def test_config_validation_of_new_fields(L):
         assert L.hz_setup(ctypes.byref(g), ctypes.c_void_p(1), ctypes.byref(c), None, ctypes.byref(h)) == hz.HZ_EINVAL
         msg = L.hz_last_error().decode()
         assert "coarsened" not in msg, (bad, msg)       # refused for the field itself
+
+
+def test_dirichlet_grid_coarsening_rule(L):
+    """Dirichlet grids hold interior unknowns: a side of n coarsens to (n - 1) / 2 and must be odd
+    and at least 3; vertex grids need odd sides of at least 5.  Refused before any device work."""
+    import paper_2412_04980_gb300 as hz
+    h = ctypes.c_void_p()
+    for nx, ny, bc, levels in ((8, 15, 1, 2), (15, 15, 1, 5), (3, 15, 0, 2)):
+        g = hz.HzGrid(nx, ny, 0.1, bc)
+        c = hz.config(levels=levels)
+        assert L.hz_setup(ctypes.byref(g), ctypes.c_void_p(1), ctypes.byref(c), None, ctypes.byref(h)) == hz.HZ_EINVAL
+        assert "coarsened" in L.hz_last_error().decode()
+
+
+def test_dirichlet_estimate_follows_interior_sizes():
+    """hz_estimate_bytes on a Dirichlet grid uses the (n - 1) / 2 coarse sides: a 127^2 Dirichlet
+    grid needs less than the 129^2 vertex grid with the same levels."""
+    import paper_2412_04980_gb300 as hz
+    L_ = hz.lib()
+    g_d, g_s = hz.HzGrid(127, 127, 1 / 128, 1), hz.HzGrid(129, 129, 1 / 128, 0)
+    c = hz.config(levels=4)
+    bd, bs = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L_.hz_estimate_bytes(ctypes.byref(g_d), ctypes.byref(c), ctypes.byref(bd)) == hz.HZ_OK
+    assert L_.hz_estimate_bytes(ctypes.byref(g_s), ctypes.byref(c), ctypes.byref(bs)) == hz.HZ_OK
+    assert 0 < bd.value < bs.value
