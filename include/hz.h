@@ -74,7 +74,8 @@ typedef struct hz_handle_s* hz_handle;
 
 /* Grid of the finest level (Section 2.1). */
 typedef struct {
-  int nx, ny;   /* nodes per side; Sommerfeld: odd and coarsenable levels-1 times */
+  int nx, ny;   /* nodes per side, odd and coarsenable levels-1 times (Sommerfeld: n -> (n + 1)
+                   / 2, at least 5 before each step; Dirichlet: n -> (n - 1) / 2, at least 3) */
   double h;     /* uniform spacing, > 0 */
   int bc;       /* HZ_BC_* */
 } hz_grid;

@@ -343,7 +343,7 @@ class Helmholtz:
         import torch
         ny, nx = self.level_size(level)
         n = self._nrhs(v, ny, nx)
-        cy, cx = (ny + 1) // 2, (nx + 1) // 2
+        cy, cx = self.level_size(level + 1)
         out = torch.empty((n, cy, cx) if v.dim() == 3 else (cy, cx), dtype=v.dtype, device=v.device)
         _check(lib().hz_defl_restrict(self._h, level, self._dt(v), _ptr(v), _ptr(out), n), "hz_defl_restrict")
         return out
@@ -351,7 +351,7 @@ class Helmholtz:
     def defl_prolong(self, level: int, w):
         import torch
         ny, nx = self.level_size(level)
-        cy, cx = (ny + 1) // 2, (nx + 1) // 2
+        cy, cx = self.level_size(level + 1)
         n = self._nrhs(w, cy, cx)
         out = torch.empty((n, ny, nx) if w.dim() == 3 else (ny, nx), dtype=w.dtype, device=w.device)
         _check(lib().hz_defl_prolong(self._h, level, self._dt(w), _ptr(w), _ptr(out), n), "hz_defl_prolong")

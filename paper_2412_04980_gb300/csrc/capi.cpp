@@ -152,7 +152,6 @@ int hz_apply(hz_handle hp, const void* x, void* y, int nrhs) {
 int hz_precond(hz_handle hp, const void* v, void* x, int nrhs) {
   GUARD_HANDLE(hp);
   if (!v || !x) return bad("null vector");
-  if (H_->g.bc != HZ_BC_SOMMERFELD) return HZ_ENOTSUP;
   if (int s = check_nrhs(H_, nrhs, true)) return s;
   Level& L = H_->lv[0];
   for (int q = 0; q < nrhs; ++q) H_->st[q] = RhsStats();
@@ -189,7 +188,6 @@ static void fill_stats(Handle* H, hz_stats* stats, int nrhs, double ms) {
 int hz_solve(hz_handle hp, const void* b, void* u, int nrhs, double tol, unsigned flags, hz_stats* stats) {
   GUARD_HANDLE(hp);
   if (!b || !u) return bad("null vector");
-  if (H_->g.bc != HZ_BC_SOMMERFELD) return HZ_ENOTSUP;
   if (!(tol > 0) || !(tol < 1)) return bad("tol must be in (0, 1)");
   if (int s = check_nrhs(H_, nrhs, true)) return s;
   auto t0 = std::chrono::steady_clock::now();
