@@ -42,6 +42,8 @@ WORKLOADS = {
     "mp1b_129": "129x129 constant k = 20, point source at the centre, 2-level, tol 1e-6",
     "random_1025": "1025x1025 seeded random-velocity model, k_max h = 0.3, 4-level MADP, tol 1e-6",
     "random_513": "513x513 seeded random-velocity model, k_max h = 0.3, 3-level MADP, tol 1e-6",
+    "mp1a_1023": "1023x1023 interior unknowns, homogeneous Dirichlet (MP-1a), constant k = 320 (k h = 0.3125), "
+                 "centre source, 4-level MADP, tol 1e-6",
     "wedge_2049_64rhs": "2049x2049 square version of the synthetic wedge (1000 x 1000 m), k_max h = 0.3, 64 unit "
                         "point sources evenly spaced along the top row, 6-level MADP, tol 1e-6 per right-hand side",
 }
@@ -150,6 +152,7 @@ def oracle_sample(workload: str, counts: dict) -> dict:
     from oracle.multigrid import CSLPMultigrid
 
     p = mp.named(workload)
+    dirichlet = p.meta.get("bc") == "dirichlet"
     sched = schedule_config(counts.get("schedule", "madp"), p)
     cfg = MADPConfig(levels=p.levels, negdef_from_level=p.negdef_from_level,
                      mg_max_level=sched.get("mg_max_level", 2))
@@ -160,13 +163,14 @@ def oracle_sample(workload: str, counts: dict) -> dict:
     u = mp.random_complex((p.ny, p.nx), seed=1)
     k = p.k
     for l in range(1, ml + 1):
-        kl = T.inject(k, 2 ** (l - 1))
+        kl = (T.inject_dirichlet(k, 2 ** (l - 1)) if dirichlet else T.inject(k, 2 ** (l - 1))) if l > 1 else k
         ul = u
         t = time.perf_counter()
-        O.apply_level(ul, kl, l, p.h, 1.0)
+        (O.apply_level_dirichlet if dirichlet else O.apply_level)(ul, kl, l, p.h, 1.0)
         unit[f"A{l}"] = time.perf_counter() - t
         if l <= cfg.mg_max_level:
-            mg = CSLPMultigrid(kl, l, p.h, shift, cfg.mg_omega, cfg.mg_nu1, cfg.mg_nu2, cfg.mg_coarsest_side)
+            mg = CSLPMultigrid(kl, l, p.h, shift, cfg.mg_omega, cfg.mg_nu1, cfg.mg_nu2, cfg.mg_coarsest_side,
+                               "dirichlet" if dirichlet else "sommerfeld")
             t = time.perf_counter()
             mg(ul)
             unit[f"V{l}"] = time.perf_counter() - t
@@ -176,10 +180,10 @@ def oracle_sample(workload: str, counts: dict) -> dict:
         unit[f"G{l}"] = time.perf_counter() - t                  # one MGS step: dot + axpy
         if l < ml:
             t = time.perf_counter()
-            v = T.deflation_restrict(ul)
+            v = (T.deflation_restrict_dirichlet if dirichlet else T.deflation_restrict)(ul)
             unit[f"Zt{l}"] = time.perf_counter() - t
             t = time.perf_counter()
-            T.deflation_prolong(v, ul.shape)
+            (T.deflation_prolong_dirichlet if dirichlet else T.deflation_prolong)(v, ul.shape)
             unit[f"Z{l}"] = time.perf_counter() - t
             u = v
     sample_s = time.perf_counter() - t_total
@@ -655,8 +659,9 @@ def main():
     if args.graphs is not None:
         extra["graphs"] = args.graphs
     extra.update(schedule_config(args.schedule, p))
-    H = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision=args.precision,
-                     **extra)
+    bc = p.meta.get("bc", "sommerfeld")
+    H = hz.Helmholtz(k, p.h, bc=bc, levels=p.levels, negdef_from_level=p.negdef_from_level,
+                     precision=args.precision, **extra)
     u = torch.empty_like(b)
 
     barrier = rank_barrier
@@ -725,8 +730,8 @@ def main():
     if not args.no_fp64 and rank == 0 and args.precision != "fp64":
         H.close()
         torch.cuda.empty_cache()
-        H64 = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="fp64",
-                           **extra)
+        H64 = hz.Helmholtz(k, p.h, bc=bc, levels=p.levels, negdef_from_level=p.negdef_from_level,
+                           precision="fp64", **extra)
         H64.solve(b, u, tol=1e-6)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

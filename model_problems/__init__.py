@@ -215,4 +215,10 @@ def named(name: str) -> Problem:
         return random_field(513, 5.0, seed=3, levels=3, negdef_from_level=4)
     if name == "wedge_2049_64rhs":
         return wedge_square(2049, 64)
+    if name == "mp1a_1023":
+        # MP-1a at k h = 0.3125 (Section 4.3.1's resolution): k = 320 on 1023^2 interior unknowns;
+        # levels 1023, 511, 255, 127, the fourth negative definite at this k h
+        p = mp1a(1024, 320.0, levels=4)
+        p.negdef_from_level = 4
+        return p
     raise KeyError(name)
