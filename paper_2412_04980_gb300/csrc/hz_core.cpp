@@ -1152,7 +1152,6 @@ int cslp_bicgstab(Handle* h, int l, const void* b, void* x, int nb, int* its_out
       if (all) break;
     }
   }
-  if (L.capg < 1) CS(fetch());
   for (int q = 0; q < nb; ++q) {
     if (!std::isfinite(hs[q].rn2)) {
       set_error("non-finite residual in the Bi-CGSTAB CSLP solve");
