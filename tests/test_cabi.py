@@ -186,3 +186,16 @@ def test_dirichlet_estimate_follows_interior_sizes():
     assert L_.hz_estimate_bytes(ctypes.byref(g_d), ctypes.byref(c), ctypes.byref(bd)) == hz.HZ_OK
     assert L_.hz_estimate_bytes(ctypes.byref(g_s), ctypes.byref(c), ctypes.byref(bs)) == hz.HZ_OK
     assert 0 < bd.value < bs.value
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libhz.so every entry point raises instead of computing."""
+    import paper_2412_04980_gb300 as hz
+    monkeypatch.setattr(hz, "_LIB", None)
+    monkeypatch.setattr(hz, "library_path", lambda: str(tmp_path / "libhz.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        hz.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        hz.config(levels=2)
+    with pytest.raises(RuntimeError, match="missing"):
+        hz.estimate_bytes(129, 129, 1 / 128, levels=2)
