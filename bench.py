@@ -77,7 +77,8 @@ def schedule_config(name: str, p) -> dict:
     wavenumber k_dim = k_max sqrt(L_x L_y) (Section 4.3.2)."""
     import numpy as np
     ml = p.levels
-    kdim = float(np.max(p.k)) * math.sqrt((p.nx - 1) * p.h * (p.ny - 1) * p.h)
+    e = 1 if p.meta.get("bc") == "dirichlet" else -1        # Dirichlet arrays hold interior unknowns
+    kdim = float(np.max(p.k)) * math.sqrt((p.nx + e) * p.h * (p.ny + e) * p.h)
     if name == "madp":
         return {}
     if name == "madp_w":
@@ -227,9 +228,25 @@ def load_counts(workload: str):
     return SOLVE_COUNTS.get(workload)
 
 
+def host_cpu() -> dict:
+    """The host the oracle ran on: logical CPUs and the processor model (from /proc/cpuinfo on Linux)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
 def cpu_line(workload, res, steps_note):
     est = res["est_s_per_solve"]
-    return {"value": 1.0 / est, "unit": "solves/s", "cores": res["cores"], "kind": "oracle",
+    return {"value": 1.0 / est, "unit": "solves/s", "cores": res["cores"], "kind": "oracle", "host": host_cpu(),
             "sample": f"each oracle primitive (A_l, V-cycle, Z^T, Z, MGS step) timed once at every level size of "
                       f"{workload} ({res['sample_s']:.1f} s of CPU work), scaled by the solve's per-level "
                       f"iteration counts to {est:.0f} s per solve{steps_note}",
