@@ -22,7 +22,10 @@ cycle runs with the Dirichlet operators, transfers and injection of
 Pins (tests/test_oracle_multigrid.py): for the Poisson operator (k = 0) the
 V(1,1) convergence factor lies in the textbook range (both boundary types); the
 exact solution is a fixed point of every Jacobi sweep; a single-level hierarchy
-is an exact solve.
+is an exact solve; with k != 0 every coarse multigrid level's operator, divided
+by 4^(l-1), is consistent with -Laplace(u) - shift k^2 u (second order inside,
+first order on the boundary rows with the Sommerfeld data folded in), which
+fixes its spacing, its ghost spacing, its scale and its injected wavenumber.
 """
 from __future__ import annotations
 

@@ -26,9 +26,14 @@ Pins (tests/test_oracle_operators.py): closed-form Dirichlet eigenpairs, O(h^2)
 convergence of manufactured solutions with Dirichlet and Sommerfeld data,
 symmetry of the edge-scaled Sommerfeld matrix, a dense direct solve, the
 reduction of ``apply_level`` at level 1 to ``apply_5pt``, Galerkin triple
-products for the interior rows of levels 2-3, and brute-force diagonals.
-Parity unpinned: the near-boundary rows of levels >= 2 (ghost layer and zero
-padding), which the paper calls an open problem and fixes only in words.
+products for the interior rows of levels 2-3, brute-force diagonals, and for
+levels 2-4: first-order consistency of the physical-boundary rows with
+-Laplace(u) - shift k^2 u plus the folded-in Sommerfeld data (fixes the ghost
+spacing H_l and the scale 4^(l-1)), and exactness of the rows whose stencil
+reaches the first outside layer on waves that satisfy the ghost relation
+exactly (fixes that layer's ghost value and the zero ghost wavenumber).
+Not fixed by any pin: the zero padding beyond the first outside layer, which is
+this implementation's reading of what the paper calls an open problem.
 
 * ``apply_level_dirichlet`` / ``diag_level_dirichlet``   the level-l operator on a
                     homogeneous Dirichlet grid (MP-1a): the Galerkin stencil at every
