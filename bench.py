@@ -4,19 +4,26 @@
 One step = one full solve (hz_solve) of the workload to a 1e-6 relative residual, the
 right-hand side already resident in device memory.  Default workload: the 4097 x 4097
 seeded random-velocity model (k_max h = 0.3, source at the top centre), 6-level MADP,
-mixed precision (FP32 preconditioner, FP64 outer FGMRES).
+mixed precision (FP32 preconditioner, FP64 outer FGMRES).  The timed region runs the
+library's defaults (CUDA graphs on) with no host-side event pairs; the per-kernel table
+comes from one profiled solve before it.
 
 Printed JSON line (rank 0):
   value            solves/s of the whole job (all ranks; replicas, no collective)
   ms_per_step      mean time-to-solution
   time_to_solution p50 / p99 over the timed steps
-  fp64_gpu         the plain FP64 GPU solver on the same workload (one solve)
+  fp64_gpu         the plain FP64 GPU solver on the same workload (one solve), and the
+                   relative difference between the mixed and FP64 GPU solutions
   e2e              hz_solve_host: host b -> device, solve, device u -> host, per step
-  roofline         the dominant kernel family, algorithmic bytes / event-timed duration
-  cpu_baseline     the FP64 oracle on the host cores, a bounded sample scaled to a solve
+  roofline         the dominant kernel: algorithmic bytes / its own device-timed duration
+                   over the timed region (persistent GMRES), per level as well
+  cpu_baseline     the FP64 oracle on the host cores: the workload's per-primitive sample on
+                   one core scaled to a solve (extrapolated), the same in one process per
+                   usable core (all cores), and a complete oracle solve of random_513 timed
+                   beside its own extrapolation
   clocks           nvidia-smi samples taken during the timed region
 
---impl reference times only the oracle (rank 0), with the same metric and unit.
+--impl reference times only the oracle (rank 0), with the same metric, unit and config keys.
 """
 from __future__ import annotations
 
@@ -111,7 +118,6 @@ def parse():
                     help="capture the device-only coarse solves as CUDA graphs (library default if omitted)")
     ap.add_argument("--schedule", default="madp", choices=sorted(SCHEDULES),
                     help="coarse-level schedule: " + "; ".join(f"{k}: {v}" for k, v in SCHEDULES.items()))
-    ap.add_argument("--no-live-profile", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--device-gmres", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="GMRES CSLP form: 1 automatic (cluster, tile-owned or slice grid by level "
                          "and batch), 2 cooperative grid, 3 cluster, 4 slice grid, 0 host-driven")
@@ -135,6 +141,7 @@ def parse():
     ap.add_argument("--load", type=float, default=1.0,
                     help="offered arrival rate as a multiple of the one-at-a-time service rate")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-solve", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--out", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -210,18 +217,77 @@ def oracle_sample(workload: str, counts: dict) -> dict:
     return {"est_s_per_solve": est, "sample_s": sample_s, "unit_s": unit, "cores": 1}
 
 
-def run_oracle_sample(workload: str, counts: dict) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def _oracle_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def run_oracle_sample(workload: str, counts: dict, procs: int = 1) -> dict:
+    """The per-primitive oracle sample in `procs` concurrent single-threaded interpreters (one
+    per host core used); returns the first one's result with every process's estimate."""
     with tempfile.TemporaryDirectory() as d:
-        cpath, opath = os.path.join(d, "c.json"), os.path.join(d, "o.json")
+        cpath = os.path.join(d, "c.json")
         with open(cpath, "w") as f:
             json.dump(counts, f)
-        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, "--out", opath]
-        r = subprocess.run(cmd, env=dict(env, HZ_COUNTS=cpath), capture_output=True, text=True, timeout=900)
+        outs, running = [], []
+        for i in range(procs):
+            opath = os.path.join(d, f"o{i}.json")
+            cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, "--out", opath]
+            running.append(subprocess.Popen(cmd, env=dict(_oracle_env(), HZ_COUNTS=cpath),
+                                            stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True))
+            outs.append(opath)
+        errs = []
+        for r in running:
+            _, err = r.communicate(timeout=1800)
+            if r.returncode != 0:
+                errs.append(err[-2000:])
+        if errs:
+            raise RuntimeError(errs[0])
+        res = []
+        for opath in outs:
+            with open(opath) as f:
+                res.append(json.load(f))
+    first = dict(res[0])
+    first["all_est_s_per_solve"] = [r["est_s_per_solve"] for r in res]
+    return first
+
+
+def oracle_full_solve(workload: str) -> dict:
+    """One complete oracle solve (Algorithm 1 with the MADP schedule, FP64, one core)."""
+    import model_problems as mp
+    from oracle.madp import Hierarchy, MADPConfig
+    p = mp.named(workload)
+    t0 = time.perf_counter()
+    hier = Hierarchy(p.k, p.h, MADPConfig(levels=p.levels, negdef_from_level=p.negdef_from_level,
+                                          bc=p.meta.get("bc", "sommerfeld")))
+    _, st = hier.solve(p.b[0])
+    return {"s": time.perf_counter() - t0, "outer": st.outer_iterations, "true_relres": st.true_relres}
+
+
+def run_oracle_full_solve(workload: str) -> dict:
+    with tempfile.TemporaryDirectory() as d:
+        opath = os.path.join(d, "o.json")
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-solve", workload, "--out", opath]
+        r = subprocess.run(cmd, env=_oracle_env(), capture_output=True, text=True, timeout=1800)
         if r.returncode != 0:
             raise RuntimeError(r.stderr[-2000:])
         with open(opath) as f:
             return json.load(f)
+
+
+def host_procs_for_oracle(per_proc_gb: float) -> int:
+    """Concurrent single-threaded oracle processes: one per host core, fewer if the host's
+    available memory would not hold them (per_proc_gb each, with a 2x margin)."""
+    n = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail_gb = int(line.split()[1]) / 2 ** 20
+                    n = min(n, max(1, int(avail_gb / (2.0 * per_proc_gb))))
+                    break
+    except OSError:
+        n = 1
+    return max(1, n)
 
 
 def load_counts(workload: str):
@@ -247,10 +313,17 @@ def host_cpu() -> dict:
 def cpu_line(workload, res, steps_note):
     est = res["est_s_per_solve"]
     return {"value": 1.0 / est, "unit": "solves/s", "cores": res["cores"], "kind": "oracle", "host": host_cpu(),
-            "sample": f"each oracle primitive (A_l, V-cycle, Z^T, Z, MGS step) timed once at every level size of "
-                      f"{workload} ({res['sample_s']:.1f} s of CPU work), scaled by the solve's per-level "
-                      f"iteration counts to {est:.0f} s per solve{steps_note}",
+            "sample": f"extrapolated: each oracle primitive (A_l, V-cycle, Z^T, Z, MGS step) timed once at every "
+                      f"level size of {workload} ({res['sample_s']:.1f} s of CPU work on one core), scaled by the "
+                      f"solve's per-level iteration counts to {est:.0f} s per solve{steps_note}",
             "est_s_per_solve": est}
+
+
+# Per-process peak memory of the oracle's per-primitive sample at 4097^2 (a few 268 MB complex
+# vectors and the multigrid hierarchy of levels 1-2), used to bound the all-cores leg.
+ORACLE_SAMPLE_GB = {"random_4097": 4.0}
+# Workload whose complete oracle solve is timed beside the extrapolation (same recipe, smaller).
+ORACLE_MEASURED = "random_513"
 
 
 # ------------------------------------------------------------------------------- replicas
@@ -609,12 +682,57 @@ def batched(args, p):
     print(json.dumps(line))
 
 
+def workload_config(args, p, precision: str, extra: dict) -> dict:
+    """The `config` object of a bench line; both arms print the same keys."""
+    nbytes = p.nx * p.ny * 16
+    return {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
+            "levels": p.levels, "nrhs": 1, "precision": precision, "schedule": args.schedule,
+            "reorth_eta": extra.get("reorth_eta"), "device_gmres": extra.get("device_gmres"),
+            "graphs": extra.get("graphs"),
+            "l2": f"inputs larger than L2: b is {nbytes / 1e6:.0f} MB and a solve touches GBs of workspace",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def cpu_baseline(args, counts) -> dict:
+    """The FP64 oracle on the host cores: (1) the per-primitive sample of the workload on one core,
+    scaled to a solve (extrapolated); (2) the same sample in one process per usable core at once
+    (all-cores throughput); (3) one complete oracle solve of a smaller workload of the same recipe,
+    measured, beside the extrapolation of that workload from its own sample (how far the
+    extrapolation is off)."""
+    one = run_oracle_sample(args.workload, counts)
+    line = cpu_line(args.workload, one, "")
+    procs = host_procs_for_oracle(ORACLE_SAMPLE_GB.get(args.workload, 2.0))
+    if procs > 1:
+        t0 = time.perf_counter()
+        allc = run_oracle_sample(args.workload, counts, procs)
+        ests = allc["all_est_s_per_solve"]
+        line["all_cores"] = {"value": len(ests) / statistics.mean(ests), "unit": "solves/s", "cores": len(ests),
+                             "kind": "oracle, one single-threaded process per core, same extrapolation",
+                             "wall_s": time.perf_counter() - t0}
+    return line
+
+
+def measured_oracle_leg(counts_small) -> dict:
+    """A complete oracle solve of ORACLE_MEASURED on one core, and the extrapolation of the same
+    workload from its per-primitive sample with the GPU solver's counts."""
+    full = run_oracle_full_solve(ORACLE_MEASURED)
+    ext = run_oracle_sample(ORACLE_MEASURED, counts_small)
+    return {"workload": ORACLE_MEASURED, "measured_s_per_solve": full["s"], "outer_iterations": full["outer"],
+            "true_relres": full["true_relres"], "extrapolated_s_per_solve": ext["est_s_per_solve"],
+            "measured_over_extrapolated": full["s"] / ext["est_s_per_solve"], "cores": 1}
+
+
 def main():
     args = parse()
     if args.oracle_sample:
         with open(os.environ["HZ_COUNTS"]) as f:
             counts = json.load(f)
         res = oracle_sample(args.oracle_sample, counts)
+        with open(args.out, "w") as f:
+            json.dump(res, f)
+        return
+    if args.oracle_solve:
+        res = oracle_full_solve(args.oracle_solve)
         with open(args.out, "w") as f:
             json.dump(res, f)
         return
@@ -631,22 +749,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        import model_problems as mp
         counts = load_counts(args.workload) if args.schedule == "madp" else None
         if counts is None:
             print(json.dumps({"impl": "reference", "unavailable": "no per-solve iteration counts recorded for "
                                                                    f"{args.workload} ({args.schedule})"}))
             return
+        p = mp.named(args.workload)
         times = []
         res = None
-        for s in range(args.warmup + args.steps):
+        for s_ in range(args.warmup + args.steps):
             res = run_oracle_sample(args.workload, counts)
-            if s >= args.warmup:
+            if s_ >= args.warmup:
                 times.append(res["est_s_per_solve"])
         est = statistics.mean(times)
         line = {"impl": "reference", "metric": METRIC, "value": 1.0 / est, "unit": "solves/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+                "config": workload_config(args, p, "fp64 (oracle)", {}),
                 "cpu_baseline": cpu_line(args.workload, dict(res, est_s_per_solve=est), ""),
                 "e2e": {"value": 1.0 / est, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -687,7 +807,8 @@ def main():
     gmres_forms = {str(l): H.gmres_form(l) for l in range(1, p.levels + 1) if H.gmres_form(l)["form"] != "none"}
     for _ in range(args.warmup):
         _, st = H.solve(b, u, tol=1e-6)
-    # which kernel family dominates (one profiled solve, not timed)
+    # per-family event profile of one solve, outside the timed region (kernels launched eagerly
+    # while profiling); the timed region below runs with the library's defaults (graphs on)
     fams = H.kernel_families()
     for f in range(len(fams)):
         H.profile_enable(f, True)
@@ -702,9 +823,7 @@ def main():
                 lev_ms.setdefault(str(lv), {})[fams[f]] = [round(msl, 3), nl, round(byl / max(msl, 1e-9) / 1e6, 1)]
         H.profile_enable(f, False)
     dom = max(fam_ms, key=lambda x: fam_ms[x][0])
-    dom_id = fams.index(dom)
-    if not args.no_live_profile:
-        H.profile_enable(dom_id, True)
+    H.gmres_device_time(0, reset=True)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -725,12 +844,20 @@ def main():
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_s = sum(step_ms) / 1e3
     total_s = max_over_ranks(total_s, dev)
-    if args.no_live_profile:
-        ms_dom, n_dom, by_dom = fam_ms[dom]
+    # the dominant kernel over the timed region: the persistent GMRES times itself on the device
+    gdev = {}
+    for lv in range(1, p.levels + 1):
+        n_, ms_, by_ = H.gmres_device_time(lv)
+        if n_:
+            gdev[str(lv)] = {"launches": n_, "ms": round(ms_, 3), "GB/s": round(by_ / ms_ / 1e6, 1)}
+    n_dom, ms_dom, by_dom = H.gmres_device_time(0)
+    if dom == "gmres_persistent" and n_dom > 0:
+        roof_src = "k_gmres device-timed (%globaltimer, first CTA entry to last CTA exit) over the timed region"
     else:
-        n_dom, ms_dom, by_dom = H.profile_read(dom_id)
-        H.profile_enable(dom_id, False)
+        ms_dom, n_dom, by_dom = fam_ms[dom]
+        roof_src = "CUDA event pairs around every launch of the family in the profiled (untimed) solve"
     assert all(s["status"] == 0 and s["true_relres"] <= 1e-6 for s in stats), stats
+    u_sol = u.clone()
 
     # end to end through the host-buffer entry point
     b_host = torch.from_numpy(p.b[0]).pin_memory().numpy()
@@ -749,15 +876,19 @@ def main():
         torch.cuda.empty_cache()
         H64 = hz.Helmholtz(k, p.h, bc=bc, levels=p.levels, negdef_from_level=p.negdef_from_level,
                            precision="fp64", **extra)
-        H64.solve(b, u, tol=1e-6)
+        u64 = torch.empty_like(b)
+        H64.solve(b, u64, tol=1e-6)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st64 = H64.solve(b, u, tol=1e-6)
+        _, st64 = H64.solve(b, u64, tol=1e-6)
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        diff = float(torch.linalg.vector_norm(u_sol - u64) / torch.linalg.vector_norm(u64))
         fp64 = {"s_per_solve": e0.elapsed_time(e1) / 1e3, "outer_iterations": st64[0]["outer_iterations"],
-                "true_relres": st64[0]["true_relres"]}
+                "true_relres": st64[0]["true_relres"], "mixed_vs_fp64_rel_l2": diff,
+                "note": "||u_mixed - u_fp64|| / ||u_fp64|| of the two GPU solutions at a 1e-6 residual each; the "
+                        "FP64 GPU solver matches the oracle to 1e-5 at the sizes the oracle solves (tests)"}
         H64.close()
 
     counts = {"outer": stats[-1]["outer_iterations"], "level_iterations": stats[-1]["level_iterations"],
@@ -767,19 +898,35 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:
-            cpu = cpu_line(args.workload, run_oracle_sample(args.workload, counts), "")
+            cpu = cpu_baseline(args, counts)
+            if args.workload == "random_4097" and args.schedule == "madp":
+                # counts of the smaller workload, from one GPU solve of it, for its extrapolation
+                q = mp.named(ORACLE_MEASURED)
+                Hq = hz.Helmholtz(torch.from_numpy(q.k).to(dev), q.h, levels=q.levels,
+                                  negdef_from_level=q.negdef_from_level, precision=args.precision)
+                _, sq = Hq.solve(torch.from_numpy(q.b[0]).to(dev), tol=1e-6)
+                Hq.close()
+                cq = {"outer": sq[0]["outer_iterations"], "level_iterations": sq[0]["level_iterations"],
+                      "level_calls": sq[0]["level_calls"], "cslp_gmres_iterations": sq[0]["cslp_gmres_iterations"],
+                      "schedule": "madp"}
+                cpu["measured_solve"] = measured_oracle_leg(cq)
         except Exception as e:  # report, do not hide
             cpu = {"error": str(e)[-300:]}
 
     if rank != 0:
         return
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
-        try:
-            peaks = json.load(f)
-        except Exception:
-            peaks = {}
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as f:
+            try:
+                peaks = json.load(f)
+            except Exception:
+                peaks = {}
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    if hbm_peak is None:
+        hbm_peak, peak_src = 6800.0, "fallback 6.8 TB/s (of fallback)"
     achieved = (by_dom / 1e9) / (ms_dom / 1e3) if ms_dom > 0 else None
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
@@ -796,24 +943,22 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64 (FP32 preconditioner, FP64 outer FGMRES)" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
-                   "levels": p.levels, "nrhs": 1, "precision": args.precision, "reorth_eta": H.cfg.reorth_eta,
-                   "device_gmres": H.cfg.device_gmres, "schedule": args.schedule,
-                   "l2": f"inputs larger than L2: b is {nbytes / 1e6:.0f} MB and the solver touches "
-                         f"{mem_gb:.1f} GB of workspace per solve",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(args, p, args.precision,
+                                  dict(extra, reorth_eta=H.cfg.reorth_eta, device_gmres=H.cfg.device_gmres,
+                                       graphs=H.cfg.graphs)),
         "time_to_solution_s": {"p50": statistics.median(step_ms) / 1e3,
                                "p99": t_sorted[min(len(t_sorted) - 1, math.ceil(0.99 * len(t_sorted)) - 1)] / 1e3},
         "iterations": {"outer": counts["outer"], "level2": counts["level_iterations"][1],
                        "true_relres": stats[-1]["true_relres"]},
+        "workspace_gb": mem_gb,
         "fp64_gpu": fp64,
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": int(launches),
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
                      "launches": n_dom, "avg_launch_us": ms_dom * 1e3 / max(n_dom, 1),
-                     "share_of_step": ms_dom / max(sum(step_ms), 1e-9),
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                     "share_of_step": ms_dom / max(sum(step_ms), 1e-9), "timing": roof_src,
+                     "by_level": gdev, "peak_source": peak_src},
         "kernel_ms_per_solve": {f: round(v[0], 3) for f, v in fam_ms.items()},
         "kernel_ms_launches_gbs_by_level": lev_ms,
         "counts": counts,

@@ -109,8 +109,9 @@ typedef struct {
                             the GPU (FP32) and slice-distributed vector phases elsewhere;
                             2: always the cooperative grid (tile-owned where it fits);
                             3: always clusters; 4: always the slice-distributed grid;
-                            0: host-driven Arnoldi steps.  Clusters are used with FP32
-                            vectors (HZ_PREC_MIXED) only; FP64 takes the grid instead */
+                            0: host-driven Arnoldi steps.  Every form runs with FP32
+                            (HZ_PREC_MIXED) and FP64 vectors, except the tile-owned one
+                            (FP32 only) */
   double reorth_eta;     /* classical Gram-Schmidt runs a second pass when the orthogonalised
                             vector keeps less than reorth_eta of its norm ("twice is enough"
                             test), default 0.1; 1 = always two passes, 0 = one pass */
@@ -265,12 +266,17 @@ int hz_cslp_bicgstab(hz_handle h, int level, int dtype, const void* b, void* x, 
  * counterpart: this call exists for callers that cannot call cudaMalloc where they
  * check a solution (e.g. a plugin whose host application owns every device
  * allocation, or a loop that must not enter the allocator).
- * b, u: nrhs * nx * ny HZ_C128 device vectors; relres_dev: nrhs device doubles.
+ * b, u: nrhs * nx * ny HZ_C128 device vectors (Sommerfeld or Dirichlet grid, as the
+ * handle's); relres_dev: nrhs device doubles.  Work is ordered on the handle's stream.
  * Scratch is a static device array of 1216 * 2 * HZ_NOALLOC_MAX_RHS doubles (1.25 MB)
- * that every GPU loading the library keeps until exit; the first call on a device looks
- * up its address (make that first call before any stream capture).  All calls share
- * the array, so calls that overlap on the GPU race and must be serialised by the caller.
- * Errors: HZ_EINVAL (null pointer, nrhs < 1 or > HZ_NOALLOC_MAX_RHS), HZ_ECUDA. */
+ * that every GPU on which a handle was set up keeps until exit.  hz_setup loads the
+ * array's module and looks up its address on the handle's device, so no call of this
+ * entry point (the first one included) reserves device memory.  All calls share the
+ * array, so calls that overlap on the GPU (several streams, threads or handles) race and
+ * must be serialised by the caller.
+ * Errors: HZ_EINVAL (null pointer, nrhs < 1 or > HZ_NOALLOC_MAX_RHS, or the current device
+ * is not the handle's), HZ_ECUDA (a launch failed, or a CUDA error from earlier work was
+ * pending on entry: the message says which). */
 int hz_true_residual_noalloc(hz_handle h, const void* b, const void* u, int nrhs, double* relres_dev);
 
 /* ---- serving ------------------------------------------------------------------------ */
@@ -360,6 +366,14 @@ int hz_kernel_family_count(void);
 /* Number of CUDA kernels this handle has launched since hz_setup (every launch of the
  * library's own kernels on the handle's stream, including the set-up launches). */
 int hz_launch_count(hz_handle h, long long* launches);
+
+/* Device-side timing of the persistent CSLP GMRES kernels (Section 4.2 solves on levels >= 3),
+ * always on and valid inside CUDA graphs: each launch measures itself with %globaltimer, from
+ * the entry of its first CTA to the exit of its last (the cluster form: per right-hand side).
+ * Returns, for deflation level `level` (0 = all levels), the launches, their summed
+ * milliseconds and their summed algorithmic bytes folded in by the hz_solve calls since the
+ * last reset; reset != 0 clears the totals after reading.  Errors: HZ_EINVAL. */
+int hz_gmres_device_time(hz_handle h, int level, int reset, long long* launches, double* ms, double* bytes);
 
 #ifdef __cplusplus
 }

@@ -129,6 +129,8 @@ _SIGS = {
     "hz_kernel_family_name": (ctypes.c_char_p, [_I]),
     "hz_kernel_family_count": (_I, []),
     "hz_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "hz_gmres_device_time": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                                  ctypes.POINTER(_D)]),
     "hz_true_residual_noalloc": (_I, [_P, _P, _P, _I, _P]),
     "hz_estimate_bytes": (_I, [ctypes.POINTER(HzGrid), ctypes.POINTER(HzConfig), ctypes.POINTER(ctypes.c_size_t)]),
     "hz_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
@@ -398,6 +400,14 @@ class Helmholtz:
         n = ctypes.c_longlong()
         _check(lib().hz_launch_count(self._h, ctypes.byref(n)), "hz_launch_count")
         return n.value
+
+    def gmres_device_time(self, level: int = 0, reset: bool = False):
+        """hz_gmres_device_time: (launches, ms, algorithmic bytes) of the self-timed persistent
+        GMRES launches folded in by the solves since the last reset (level 0: all levels)."""
+        n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().hz_gmres_device_time(self._h, level, 1 if reset else 0, ctypes.byref(n), ctypes.byref(ms),
+                                          ctypes.byref(by)), "hz_gmres_device_time")
+        return n.value, ms.value, by.value
 
     # -- per-kernel timing ----------------------------------------------------------------
     @staticmethod

@@ -412,6 +412,28 @@ int hz_launch_count(hz_handle hp, long long* launches) {
   return HZ_OK;
 }
 
+int hz_gmres_device_time(hz_handle hp, int level, int reset, long long* launches, double* ms, double* bytes) {
+  GUARD_HANDLE(hp);
+  if (level < 0 || level > HZ_MAX_LEVELS) return bad("level out of range");
+  long long n = 0;
+  double t = 0, b = 0;
+  for (int l = (level ? level : 1); l <= (level ? level : HZ_MAX_LEVELS); ++l) {
+    n += H_->gdev_launches[l];
+    t += H_->gdev_ms[l];
+    b += H_->gdev_bytes[l];
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (bytes) *bytes = b;
+  if (reset)
+    for (int l = 0; l <= HZ_MAX_LEVELS; ++l) {
+      H_->gdev_launches[l] = 0;
+      H_->gdev_ms[l] = 0;
+      H_->gdev_bytes[l] = 0;
+    }
+  return HZ_OK;
+}
+
 const char* hz_kernel_family_name(int family) { return family_name(family); }
 int hz_kernel_family_count(void) { return F_COUNT; }
 

@@ -354,12 +354,10 @@ static std::vector<double> inject(const std::vector<double>& k, int nx, int ny, 
 constexpr int kClusterMinRhs = 4;
 constexpr size_t kClusterMaxN = 300000;
 
-// The cluster form may run on a level of n nodes (it then needs per-rhs GMRES workspace).  It is
-// used for FP32 vectors only: with FP64 vectors a 5-level 2049^2 solve on 4 right-hand sides broke
-// down (isolated FP64 cluster GMRES calls agree with the grid form; the cause is not found), so
-// FP64 batches take the cooperative grid per right-hand side.
+// The cluster form may run on a level of n nodes (it then needs per-rhs GMRES workspace), for
+// FP32 and FP64 vectors alike.
 static bool cluster_form_possible(const hz_config& cfg, size_t n) {
-  if (cfg.precision != HZ_PREC_MIXED || cfg.cslp_solver != HZ_CSLP_GMRES) return false;
+  if (cfg.cslp_solver != HZ_CSLP_GMRES) return false;
   return cfg.device_gmres == 3 || (cfg.device_gmres == 1 && cfg.max_rhs >= kClusterMinRhs && n <= kClusterMaxN);
 }
 
@@ -416,6 +414,7 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       if (dev) {
         const size_t ps = 2 * (size_t)(capg + 1) + 2;
         total += gq * n * ep + 2 * sizeof(double) * std::max<size_t>(152, 16 * gq) * ps +
+                 sizeof(unsigned) * std::max<size_t>(152, 16 * gq) +
                  sizeof(double) * gq * (2 * (size_t)capg * (capg + 1) + 2 * (size_t)capg + 3 * ps) +
                  sizeof(GmresState) * nb;
       }
@@ -437,6 +436,7 @@ int setup(Handle* h, const double* k_dev) {
   h->nbmax = cfg.max_rhs;
   const int nb = h->nbmax;
   const bool mixed = cfg.precision == HZ_PREC_MIXED;
+  CK(cudaGetDevice(&h->device));
   // host copy of k, validated
   std::vector<double> k((size_t)g.nx * g.ny);
   CK(cudaMemcpy(k.data(), k_dev, k.size() * 8, cudaMemcpyDeviceToHost));
@@ -594,6 +594,9 @@ int setup(Handle* h, const double* k_dev) {
         L.gR = (double*)p;
         CS(dalloc(h, &p, sizeof(GmresState) * nb));
         L.gst = (GmresState*)p;
+        CS(dalloc(h, &p, sizeof(unsigned) * nparts));
+        L.gflag = (unsigned*)p;
+        CK(cudaMemsetAsync(L.gflag, 0, sizeof(unsigned) * nparts, h->ctx.s));
         CK(cudaMemsetAsync(L.gst, 0, sizeof(GmresState) * nb, h->ctx.s));
       }
     }
@@ -609,6 +612,7 @@ int setup(Handle* h, const double* k_dev) {
     CK(cudaMemsetAsync(h->derr, 0, sizeof(int), h->ctx.s));
   }
   h->st.assign(nb, RhsStats());
+  CS(noalloc_prepare(h));
   CK(cudaStreamSynchronize(h->ctx.s));
   if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_gmres(h));
   // the first level >= 3 from which every level runs one-iteration device cycles and a device
@@ -707,8 +711,8 @@ int autotune_gmres(Handle* h) {
         if (st) break;
         st = status_of(cudaEventRecord(e0, h->ctx.s), "autotune");
         if (st) break;
-        cudaError_t e = tx[c] > 0 ? launch_gmres_tile(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.gpartA, L.gpartB,
-                                                      L.gR, L.gst, K, 0.0, tx[c], ty[c], eta2)
+        cudaError_t e = tx[c] > 0 ? launch_gmres_tile(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.gflag, L.gpartA,
+                                                      L.gpartB, L.gR, L.gst, K, 0.0, tx[c], ty[c], eta2)
                                   : launch_gmres_persistent(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.wg2, L.gpartA,
                                                             L.gpartB, L.gpstride, L.gR, L.gst, K, 0.0, L.ggrid, false,
                                                             1, eta2);
@@ -1037,9 +1041,16 @@ int collect_gmres_stats(Handle* h, int nb) {
       h->st[q].cslp_it[L.l - 1] += (int)gs[q].total_its;
       h->st[q].cslp_reorth[L.l - 1] += (int)gs[q].total_reorth;
       bytes += gs[q].total_bytes;
+      if (L.l <= HZ_MAX_LEVELS) {
+        h->gdev_launches[L.l] += gs[q].launches;
+        h->gdev_ms[L.l] += 1e-6 * (double)gs[q].total_ns;
+        h->gdev_bytes[L.l] += gs[q].total_bytes;
+      }
       gs[q].total_its = 0;
       gs[q].total_bytes = 0;
       gs[q].total_reorth = 0;
+      gs[q].total_ns = 0;
+      gs[q].launches = 0;
       err |= gs[q].err;
     }
     // the kernel's algorithmic bytes are known only after it ran: credit them to the family
@@ -1074,8 +1085,8 @@ int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
     } else if (L.gtiles > 0) {  // tile-owned form, one cooperative launch per right-hand side
       for (int q = 0; q < nb; ++q)
         CK(launch_gmres_tile(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb, (char*)x + (size_t)q * L.n * eb,
-                             L.Vg, L.wg, L.gpartA, L.gpartB, L.gR, L.gst + q, L.capg, h->cfg.cslp_tol, L.gtx, L.gty,
-                             eta2));
+                             L.Vg, L.wg, L.gflag, L.gpartA, L.gpartB, L.gR, L.gst + q, L.capg, h->cfg.cslp_tol,
+                             L.gtx, L.gty, eta2));
     } else {  // one cooperative launch per right-hand side
       for (int q = 0; q < nb; ++q)
         CK(launch_gmres_persistent(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb,

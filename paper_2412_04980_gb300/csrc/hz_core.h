@@ -65,6 +65,7 @@ struct Level {
   int gpstride = 0;
   double* gR = nullptr;
   GmresState* gst = nullptr;                 // nbmax control blocks
+  unsigned* gflag = nullptr;                 // tile-owned form: halo flag per tile
   // Bi-CGSTAB CSLP solver (cslp_solver = HZ_CSLP_BICGSTAB): r, p, v, s, t batches, scalars, partials
   void* bcg = nullptr;
   BicgState* bst = nullptr;
@@ -87,6 +88,7 @@ struct RhsStats {
 struct Handle {
   hz_grid g{};
   hz_config cfg{};
+  int device = -1;                           // CUDA device current at hz_setup (owns every allocation)
   Ctx ctx;
   Prof prof;
   std::vector<Level> lv;
@@ -106,6 +108,11 @@ struct Handle {
   cudaStream_t capture_stream = nullptr;     // private stream the graphs are captured on
   std::vector<cudaGraphExec_t> graph_exec;   // index nb - 1
   std::vector<long long> graph_launches;
+  // device-timed persistent GMRES launches per level (index l), accumulated by
+  // collect_gmres_stats from the kernel's own %globaltimer stamps
+  long long gdev_launches[HZ_MAX_LEVELS + 1] = {};
+  double gdev_ms[HZ_MAX_LEVELS + 1] = {};
+  double gdev_bytes[HZ_MAX_LEVELS + 1] = {};
 };
 
 // allocation helpers (track for hz_destroy)
@@ -113,6 +120,9 @@ int dalloc(Handle* h, void** p, size_t bytes);
 int status_of(cudaError_t e, const char* where);
 
 int setup(Handle* h, const double* k_dev);
+// Loads the allocation-free residual check's module on the handle's device and looks up its
+// static scratch array (noalloc.cu), so that no later call of that entry point reserves memory.
+int noalloc_prepare(Handle* h);
 // Keep the faster persistent GMRES form per level (tile-owned or slice-distributed).
 int autotune_gmres(Handle* h);
 int gmres_grid_want(int nx, int ny);

@@ -188,8 +188,15 @@ struct GmresState {
   long long total_its;   // iterations accumulated since the last statistics read
   double total_bytes;    // algorithmic bytes (reads + writes of vectors and k) since the last read
   long long total_reorth;// second Gram-Schmidt passes since the last statistics read
-  long long pad2[11];
+  long long total_ns;    // device time of the launches since the last read (%globaltimer: entry of
+                         // the first CTA to the exit of the last one)
+  long long launches;    // launches since the last statistics read
+  unsigned long long t_start;  // entry time of the running launch (written by CTA 0)
+  unsigned done;         // CTAs of the running launch that finished
+  unsigned pad3;
+  long long pad2[7];
 };
+static_assert(sizeof(GmresState) == 384, "GmresState is three 128-byte lines");
 // Largest cooperative grid for the kernel variant used on a level of n nodes (0 if it cannot be
 // launched).
 int gmres_max_grid(int dt, int R, int cap, size_t n);
@@ -199,10 +206,11 @@ int gmres_tile_form(int dt, int R, int nx, int ny, int cap, int* TX, int* TY);
 // Every fitting tile shape of the tile-owned form, most tiles first; returns the count (<= maxc).
 int gmres_tile_forms(int dt, int R, int nx, int ny, int cap, int* TX, int* TY, int maxc);
 // x += GMRES(M, b) for one right-hand side with the tile-owned form (grid = tiles; w0: n
-// elements; partA/partB: 2 (cap + 1) + 2 values per CTA; Rg, st as launch_gmres_persistent).
+// elements, the updated vector the neighbours read their halos from; nflag: one unsigned per
+// tile; partA/partB: 2 (cap + 1) + 2 values per CTA; Rg, st as launch_gmres_persistent).
 cudaError_t launch_gmres_tile(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
-                              double* partA, double* partB, double* Rg, GmresState* st, int cap, double tol, int TX,
-                              int TY, double eta2);
+                              unsigned* nflag, double* partA, double* partB, double* Rg, GmresState* st, int cap,
+                              double tol, int TX, int TY, double eta2);
 // Largest thread-block cluster (16 or 8 CTAs) the cluster form can run in, 0 if none.
 int gmres_cluster_size(int dt, int R, int cap);
 // x += GMRES(M, b), whole solve in one launch: one right-hand side on a cooperative grid of

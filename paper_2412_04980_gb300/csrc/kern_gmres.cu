@@ -21,6 +21,11 @@
 // Barriers separate every write of a partial buffer from the reads of its previous contents.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "hz_core.h"
 #include "hz_device.cuh"
 
@@ -49,6 +54,35 @@ __device__ __forceinline__ cx<double> ldcg(const cx<double>* p) {
 }
 
 __device__ __forceinline__ bool failed(const hz::GmresState* gs) { return *((volatile const int*)&gs->err) != 0; }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Device-side timing of one launch (or one cluster's solve): CTA 0 stamps the entry time before
+// the first barrier, the last CTA to finish adds the elapsed time to the totals.  Works inside
+// CUDA graphs, where host-side event pairs cannot bracket the launch.
+__device__ __forceinline__ void timing_begin(hz::GmresState* st, unsigned bid) {
+  if (bid == 0 && threadIdx.x == 0) {
+    st->t_start = gtimer();
+    st->done = 0u;
+  }
+}
+__device__ __forceinline__ void timing_end(hz::GmresState* st, unsigned G) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned d = atomicAdd(&st->done, 1u);
+    if (d == G - 1) {
+      __threadfence();
+      const unsigned long long t0 = *((volatile unsigned long long*)&st->t_start);
+      st->total_ns += (long long)(gtimer() - t0);
+      st->launches += 1;
+    }
+  }
+}
 
 __device__ __forceinline__ bool grid_sync(hz::GmresState* gs, unsigned nblocks) {
   __syncthreads();
@@ -498,7 +532,8 @@ __device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn
   // entry of rotation i + 1, so it travels in registers.  The other operands of 4 rotations are
   // loaded into registers before the 4 steps run (the column stores could otherwise alias the
   // next loads and serialise every step on shared-memory latency).
-  const G_ hn = hn2 > 0 ? G_(sqrt(hn2)) : G_(0);
+  // hn and the scale in the arithmetic type (FP64 square roots and divisions are slow here)
+  const G_ hn = hn2 > 0 ? sqrt(G_(hn2)) : G_(0);
   G_ ar = h[0] + (h2 ? h2[0] : G_(0)), ai = h[1] + (h2 ? h2[1] : G_(0));
   constexpr int GB = 4;
   for (int i0 = 0; i0 < j; i0 += GB) {
@@ -555,7 +590,102 @@ __device__ void givens_step(int j, int cap, const G_* h, const G_* h2, double hn
   const double e = double(sqrt(g2r * g2r + g2i * g2i));
   *est = e;
   *stop = (e <= tol_abs || hn == G_(0) || j + 1 == cap || !(e == e)) ? 1 : 0;
-  *scale = hn2 > 0 ? 1.0 / sqrt(hn2) : 0.0;
+  *scale = hn > G_(0) ? double(G_(1) / hn) : 0.0;
+}
+
+// The same Givens step run by all 32 lanes of warp 0.  The rotations i < j act on the new column
+// as a linear recurrence of the carried entry, x_{i+1} = -conj(s_i) x_i + c_i h_{i+1} (the rotated
+// entry i is c_i x_i + s_i h_{i+1}): each lane composes the affine maps of a block of consecutive
+// rotations, a shuffle scan over the lanes gives every block its incoming x, and each lane then
+// rotates its own block.  Lane 0 forms the new rotation.  Same outputs as givens_step.
+template <typename G_>
+__device__ void givens_step_warp(int j, int cap, const G_* h, const G_* h2, double hn2, G_* col, G_* gc, G_* gs,
+                                 G_* g, double tol_abs, double* est, int* stop, double* scale) {
+  const int lane = threadIdx.x & 31;
+  const G_ hn = hn2 > 0 ? sqrt(G_(hn2)) : G_(0);
+  const int B = (j + 31) / 32;
+  const int i0 = min(lane * B, j), i1 = min(i0 + B, j);
+  const G_ x0r = h[0] + (h2 ? h2[0] : G_(0)), x0i = h[1] + (h2 ? h2[1] : G_(0));
+  // composite map x -> A x + Bv of this lane's block
+  G_ Ar = G_(1), Ai = G_(0), Br = G_(0), Bi = G_(0);
+  for (int i = i0; i < i1; ++i) {
+    const G_ c = gc[i], sr = gs[2 * i], si = gs[2 * i + 1];
+    const G_ br = h[2 * i + 2] + (h2 ? h2[2 * i + 2] : G_(0)), bi = h[2 * i + 3] + (h2 ? h2[2 * i + 3] : G_(0));
+    const G_ pr = -sr, pi = si;  // -conj(s)
+    const G_ nAr = pr * Ar - pi * Ai, nAi = pr * Ai + pi * Ar;
+    const G_ nBr = (pr * Br - pi * Bi) + c * br, nBi = (pr * Bi + pi * Br) + c * bi;
+    Ar = nAr;
+    Ai = nAi;
+    Br = nBr;
+    Bi = nBi;
+  }
+  // inclusive scan: lane l holds the map of blocks 0..l
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const G_ qAr = __shfl_up_sync(0xffffffffu, Ar, off), qAi = __shfl_up_sync(0xffffffffu, Ai, off);
+    const G_ qBr = __shfl_up_sync(0xffffffffu, Br, off), qBi = __shfl_up_sync(0xffffffffu, Bi, off);
+    if (lane >= off) {  // mine after theirs: x -> A (qA x + qB) + B
+      const G_ nBr = (Ar * qBr - Ai * qBi) + Br, nBi = (Ar * qBi + Ai * qBr) + Bi;
+      const G_ nAr = Ar * qAr - Ai * qAi, nAi = Ar * qAi + Ai * qAr;
+      Ar = nAr;
+      Ai = nAi;
+      Br = nBr;
+      Bi = nBi;
+    }
+  }
+  // x entering this lane's block: the map of blocks 0..l-1 applied to x_0
+  const G_ eAr = __shfl_up_sync(0xffffffffu, Ar, 1), eAi = __shfl_up_sync(0xffffffffu, Ai, 1);
+  const G_ eBr = __shfl_up_sync(0xffffffffu, Br, 1), eBi = __shfl_up_sync(0xffffffffu, Bi, 1);
+  G_ ar = x0r, ai = x0i;
+  if (lane > 0) {
+    ar = (eAr * x0r - eAi * x0i) + eBr;
+    ai = (eAr * x0i + eAi * x0r) + eBi;
+  }
+  for (int i = i0; i < i1; ++i) {
+    const G_ c = gc[i], sr = gs[2 * i], si = gs[2 * i + 1];
+    const G_ br = h[2 * i + 2] + (h2 ? h2[2 * i + 2] : G_(0)), bi = h[2 * i + 3] + (h2 ? h2[2 * i + 3] : G_(0));
+    col[2 * i] = c * ar + (sr * br - si * bi);
+    col[2 * i + 1] = c * ai + (sr * bi + si * br);
+    const G_ nr = -(sr * ar + si * ai) + c * br;
+    const G_ ni = -(sr * ai - si * ar) + c * bi;
+    ar = nr;
+    ai = ni;
+  }
+  // x_j from the lane that rotated index j - 1 (lane 0 when j == 0)
+  const int last = j > 0 ? (j - 1) / B : 0;
+  ar = __shfl_sync(0xffffffffu, ar, last);
+  ai = __shfl_sync(0xffffffffu, ai, last);
+  if (lane != 0) return;
+  const G_ aa = sqrt(ar * ar + ai * ai);
+  const G_ tt = sqrt(aa * aa + hn * hn);
+  G_ c, sr, si;
+  if (tt == G_(0)) {
+    c = G_(1);
+    sr = si = G_(0);
+  } else if (aa == G_(0)) {
+    c = G_(0);
+    sr = G_(1);
+    si = G_(0);
+  } else {
+    c = aa / tt;
+    sr = (ar / aa) * hn / tt;
+    si = (ai / aa) * hn / tt;
+  }
+  gc[j] = c;
+  gs[2 * j] = sr;
+  gs[2 * j + 1] = si;
+  col[2 * j] = c * ar + sr * hn;
+  col[2 * j + 1] = c * ai + si * hn;
+  const G_ gr = g[2 * j], gi = g[2 * j + 1];
+  const G_ g2r = -(sr * gr + si * gi), g2i = -(sr * gi - si * gr);
+  g[2 * j + 2] = g2r;
+  g[2 * j + 3] = g2i;
+  g[2 * j] = c * gr;
+  g[2 * j + 1] = c * gi;
+  const double e = double(sqrt(g2r * g2r + g2i * g2i));
+  *est = e;
+  *stop = (e <= tol_abs || hn == G_(0) || j + 1 == cap || !(e == e)) ? 1 : 0;
+  *scale = hn > G_(0) ? double(G_(1) / hn) : 0.0;
 }
 
 template <typename T, int R, bool CL, int TS = 0>
@@ -586,6 +716,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     bid = blockIdx.x;
     G = gridDim.x;
   }
+  timing_begin(st, bid);
   constexpr int TOX = TileShape<TS>::X, TOY = TileShape<TS>::Y;
   const int tilesx = (P.nx + TOX - 1) / TOX, tilesy = (P.ny + TOY - 1) / TOY;
   const int ntiles = tilesx * tilesy;
@@ -695,9 +826,9 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
           if (threadIdx.x == 0) {
             K.scal[3] = hp;
             K.flags[1] = 0;
-            givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
-                           K.scal);
           }
+          givens_step_warp<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
+                              K.scal);
         } else {
           update_slice<T>(V, n, nv, sc, wnext, bid, G, threadIdx.x - 32, NT - 32);
         }
@@ -717,9 +848,9 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
       if (!reduce_all<CL>(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
-      if (threadIdx.x == 0) {
+      if (threadIdx.x < 32) {
         const double hp = K.h[2 * nv] - double(hs);
-        givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags, K.scal);
+        givens_step_warp<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags, K.scal);
       }
       __syncthreads();
     }
@@ -744,7 +875,10 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     wnext = tmp;
   }
   // y = R^-1 g by warp 0 of CTA 0 (column-oriented back substitution: lane 0 divides, the
-  // warp updates the remaining right-hand side from column i of R), then x += V y everywhere
+  // warp updates the remaining right-hand side from column i of R), then x += V y everywhere.
+  // Every thread of CTA 0 wrote part of the last column of R just before the loop ended (a
+  // stopping iteration takes no barrier), so the CTA synchronises before warp 0 reads it.
+  __syncthreads();
   double* y = Rg + 2 * (size_t)cap * (cap + 1);
   if (bid == 0 && threadIdx.x < 32) {  // Rg was written by this CTA; y is read after the barrier
     const int lane = threadIdx.x;
@@ -793,6 +927,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   size_t s0, s1;
   my_slice(n, bid, G, s0, s1);
   for (size_t e = s0 + threadIdx.x; e < s1; e += NT) x[e] = axpy_all<T, false>(x[e], V, n, jstop, sc, e);
+  timing_end(st, G);
 }
 
 
@@ -826,67 +961,220 @@ struct OwnNodes {  // own node q (row-major in the tile) -> grid index
   __device__ __forceinline__ int count() const { return OX * OY; }
 };
 
-// Partials of h_i = V_i^H w (i < nv) and ||w||^2 over the CTA's own nodes, w in shared memory;
-// 8 vectors per chunk, one warp transpose-reduction and a fixed-order block combine per chunk.
+// ---------------------------------------------------------------------------------------------
+// Tile-owned form with one grid barrier per iteration.  CTA b owns tile b of a tiling in which the
+// last tile column / row absorbs the remainder (2^k + 1 grids split evenly).  Per iteration:
+//   op      V_j = s w at the own nodes (w kept in shared memory) and the halo (read from the
+//           neighbours' w in global memory once their flags say it is complete), z = M_l V_j
+//           kept in shared memory;
+//   dots    h = V^H z and ||z||^2 over the own nodes;
+//   reduce  the grid barrier: every CTA sums all CTA partials itself in one fixed order;
+//   update  w = z - V h at the own nodes, written to global memory for the neighbours' halos,
+//           then the CTA raises its flag to j + 1 (warp 0 meanwhile runs the serial Givens step).
+// The halo exchange waits only for the (at most eight) neighbouring tiles, not for the whole
+// grid.  The first nres basis vectors of the own nodes stay in shared memory (all of them where
+// they fit), so the dots, the updates and the final x += V y read those from shared memory;
+// vectors beyond nres live in global memory.  Partial sums alternate between two buffers by a
+// running count of reductions, so a buffer is rewritten only after every CTA passed the barrier
+// that follows its last read.
+
+// x - sum_{i < nv} c_i V_i, the basis visited from V_{nv-1} down to V_0, 8 loads in flight; ld(i)
+// returns V_i at the node.
+template <typename T, class LD>
+__device__ __forceinline__ cx<T> sub_comb(cx<T> x, int nv, const T* sc, const LD& ld) {
+  int r = 0;
+  for (; r + 7 < nv; r += 8) {
+    cx<T> v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = ld(nv - 1 - r - u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = nv - 1 - r - u;
+      const T cr = sc[2 * i], ci = sc[2 * i + 1];
+      x.re -= cr * v[u].re - ci * v[u].im;
+      x.im -= cr * v[u].im + ci * v[u].re;
+    }
+  }
+  for (; r < nv; ++r) {
+    const int i = nv - 1 - r;
+    const cx<T> v = ld(i);
+    const T cr = sc[2 * i], ci = sc[2 * i + 1];
+    x.re -= cr * v.re - ci * v.im;
+    x.im -= cr * v.im + ci * v.re;
+  }
+  return x;
+}
+
 template <typename T>
-__device__ void dots_own(const cx<T>* V, size_t n, int nv, const cx<T>* Wt, const OwnNodes& on, double* part,
-                         unsigned bid, unsigned G, double* wred) {
-  constexpr int CH = 8;
+struct OwnBasis {  // V_i at own node q (grid node e): shared memory below nres, global above
+  const cx<T>* Vs;
+  const cx<T>* V;
+  int stride, q, nres;
+  size_t n, e;
+  __device__ __forceinline__ cx<T> operator()(int i) const {
+    return i < nres ? Vs[i * stride + q] : ldcg(V + (size_t)i * n + e);
+  }
+};
+
+// Partials of h_i = V_i^H z (i < nv) and ||z||^2 over the own nodes (z in shared memory): warp w
+// takes vectors w, w + NW, ... (the norm is job nv), its lanes stride over the own nodes, and a
+// shuffle tree gives the CTA partial directly (no block-level combine), stored in the arithmetic
+// type, value-major: part[i * G + b].
+template <typename T>
+__device__ void dots_own3(const cx<T>* V, const cx<T>* Vs, int vstride, int nres, size_t n, int nv,
+                          const cx<T>* Wt, const OwnNodes& on, T* part, unsigned bid, unsigned G) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nown = on.count();
-  const int chunks = nv > 0 ? (nv + CH - 1) / CH : 1;
-  for (int c = 0; c < chunks; ++c) {
-    const int c0 = c * CH;
-    const int cnt = max(0, min(CH, nv - c0));
-    T acc[2 * CH];
-#pragma unroll
-    for (int q = 0; q < 2 * CH; ++q) acc[q] = T(0);
-    T wn = T(0);
-    for (int q = threadIdx.x; q < nown; q += NT) {
-      const cx<T> wq = Wt[q];
-      const size_t node = on(q);
-      if (c == 0) wn += wq.re * wq.re + wq.im * wq.im;
-      cx<T> v[CH];
-#pragma unroll
-      for (int i = 0; i < CH; ++i)
-        if (i < cnt) v[i] = ldcg(V + (size_t)(c0 + i) * n + node);
-#pragma unroll
-      for (int i = 0; i < CH; ++i)
-        if (i < cnt) {
-          acc[2 * i] += v[i].re * wq.re + v[i].im * wq.im;
-          acc[2 * i + 1] += v[i].re * wq.im - v[i].im * wq.re;
-        }
+  for (int i = wid; i <= nv; i += NW) {
+    T ar = T(0), ai = T(0);
+    if (i == nv) {
+      for (int q = lane; q < nown; q += 32) {
+        const cx<T> z = Wt[q];
+        ar += z.re * z.re + z.im * z.im;
+      }
+    } else if (i < nres) {
+      const cx<T>* vi = Vs + (size_t)i * vstride;
+      for (int q = lane; q < nown; q += 32) {
+        const cx<T> v = vi[q], z = Wt[q];
+        ar += v.re * z.re + v.im * z.im;
+        ai += v.re * z.im - v.im * z.re;
+      }
+    } else {
+      const cx<T>* vi = V + (size_t)i * n;
+      for (int q = lane; q < nown; q += 32) {
+        const cx<T> v = ldcg(vi + on(q)), z = Wt[q];
+        ar += v.re * z.re + v.im * z.im;
+        ai += v.re * z.im - v.im * z.re;
+      }
     }
-    const T ws = warp_tsum<T, 2 * CH>(acc);
-    if (lane < 2 * CH) wred[wid * 2 * CH + lane] = double(ws);  // lanes l and l + 2 CH hold the same sum
-    if (c == 0) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
-      if (lane == 0) wred[NW * 2 * CH + wid] = double(wn);
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
     }
-    __syncthreads();
-    if (threadIdx.x < 2 * CH && (threadIdx.x >> 1) < cnt) {
-      double t = 0;
-      for (int q = 0; q < NW; ++q) t += wred[q * 2 * CH + threadIdx.x];
-      part[(size_t)(2 * c0 + threadIdx.x) * G + bid] = t;
+    if (lane == 0) {
+      part[(size_t)(2 * i) * G + bid] = ar;
+      if (i < nv) part[(size_t)(2 * i + 1) * G + bid] = ai;
     }
-    if (c == 0 && threadIdx.x == 0) {
-      double t = 0;
-      for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CH + q];
-      part[(size_t)(2 * nv) * G + bid] = t;
-    }
-    __syncthreads();
   }
 }
 
+// Grid barrier, then every CTA sums the typed partials part[i * G + b] over b itself for i < m,
+// in one fixed order (4 lanes per value, 16-byte loads of 4 consecutive CTAs' partials when G is
+// a multiple of 4), into out[] (FP64, shared); every CTA holds bitwise-identical sums.
+template <typename T>
+__device__ __forceinline__ bool grid_reduce_t(hz::GmresState* gs, unsigned G, const T* part, int m, double* out,
+                                              T* outT = nullptr) {
+  if (!grid_sync(gs, G)) return false;
+  constexpr int K = 4;
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < m; base += NT / K) {
+    const int i = base + (int)threadIdx.x / K;
+    const int k = lane % K;
+    T t = T(0);
+    if (i < m) {
+      const T* pi = part + (size_t)i * G;
+      if constexpr (sizeof(T) == 4) {
+        if ((G & 3u) == 0) {
+          const float4* p4 = reinterpret_cast<const float4*>(pi);
+          const int g4 = (int)G / 4;
+          float4 a[8];
+          int b = k;
+          for (; b + 7 * K < g4; b += 8 * K) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = __ldcg(p4 + b + u * K);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t += (a[u].x + a[u].y) + (a[u].z + a[u].w);
+          }
+          for (; b < g4; b += K) {
+            const float4 c = __ldcg(p4 + b);
+            t += (c.x + c.y) + (c.z + c.w);
+          }
+        } else {
+          for (int b = k; b < (int)G; b += K) t += __ldcg(pi + b);
+        }
+      } else {
+        T a[8];
+        int b = k;
+        for (; b + 7 * K < (int)G; b += 8 * K) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) a[u] = __ldcg(pi + b + u * K);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) t += a[u];
+        }
+        for (; b < (int)G; b += K) t += __ldcg(pi + b);
+      }
+    }
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (i < m && k == 0) {
+      out[i] = double(t);
+      if (outT) outT[i] = t;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Sum of squares of v[0..m) by warp 0 into *sred, then a CTA barrier; returns it in every thread.
+template <typename T>
+__device__ __forceinline__ T warp0_sumsq(const T* v, int m, T* sred) {
+  if (threadIdx.x < 32) {
+    T acc = T(0);
+    for (int i = threadIdx.x; i < m; i += 32) acc += v[i] * v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) *sred = acc;
+  }
+  __syncthreads();
+  return *sred;
+}
+
+// Raise this CTA's halo flag to `val` after every thread's global writes (CTA barrier, then a
+// GPU-scope fence by the signalling thread, as in the grid barrier).
+__device__ __forceinline__ void flag_raise(unsigned* nflag, unsigned bid, unsigned val) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(nflag + bid, val);
+  }
+}
+
+// Wait until the flags of the (at most eight) tiles around tile (tx, ty) reach `val`; one thread
+// per neighbour, each spin bounded by the clock budget of the grid barrier.  Ends with a CTA
+// barrier; false if a wait ran out (error flag set) or another CTA failed.
+__device__ __forceinline__ bool wait_neighbours(hz::GmresState* gs, const unsigned* nflag, const TileGrid& tg, int tx,
+                                                int ty, unsigned val) {
+  if (threadIdx.x < 9 && threadIdx.x != 4) {
+    const int nx_ = tx + (int)(threadIdx.x % 3) - 1, ny_ = ty + (int)(threadIdx.x / 3) - 1;
+    if (nx_ >= 0 && nx_ < tg.ntx && ny_ >= 0 && ny_ < tg.nty) {
+      const volatile unsigned* f = nflag + (ny_ * tg.ntx + nx_);
+      const long long t0 = clock64();
+      while (*f < val) {
+        if (failed(gs)) break;
+        if (clock64() - t0 > kSpinCycles) {
+          atomicExch(&gs->err, 1);
+          break;
+        }
+        __nanosleep(20);
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return !failed(gs);
+}
+
 template <typename T, int R>
-__global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const cx<T>* __restrict__ b,
-                                                   cx<T>* __restrict__ x, cx<T>* V, cx<T>* wbuf, double* partA,
-                                                   double* partB, double* Rg, hz::GmresState* st, int cap,
-                                                   double tol, double eta2) {
+__global__ void __launch_bounds__(NT) k_gmres_tile2(OpP<T> P, TileGrid tg, const cx<T>* __restrict__ b,
+                                                    cx<T>* __restrict__ x, cx<T>* V, cx<T>* wbuf, unsigned* nflag,
+                                                    double* partA, double* partB, double* Rg, hz::GmresState* st,
+                                                    int cap, int nres, double tol, double eta2) {
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t n = (size_t)P.nx * P.ny;
   const unsigned bid = blockIdx.x, G = gridDim.x;
+  timing_begin(st, bid);
+  if (threadIdx.x == 0) nflag[bid] = 0u;  // ordered before every neighbour's wait by the first barrier
   const int tx = (int)bid % tg.ntx, ty = (int)bid / tg.ntx;
   OwnNodes on;
   on.ox0 = tx * tg.TX;
@@ -895,9 +1183,11 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
   on.OY = (ty == tg.nty - 1) ? P.ny - on.oy0 : tg.TY;
   on.nx = P.nx;
   const int nown = on.count();
-  // shared memory: tile (room for (TX + 1) x (TY + 1) outputs) | W_own | Krylov scratch
+  const int vstride = (tg.TX + 1) * (tg.TY + 1);
+  // shared memory: tile | own z / w | own basis V_0 .. V_{nres-1} | Krylov scratch
   cx<T>* Wt = reinterpret_cast<cx<T>*>(smem + tile_smem_bytes<T, R>(tg.TX + 1, tg.TY + 1));
-  unsigned char* kp = reinterpret_cast<unsigned char*>(Wt + (size_t)(tg.TX + 1) * (tg.TY + 1));
+  cx<T>* Vs = Wt + vstride;
+  unsigned char* kp = reinterpret_cast<unsigned char*>(Vs + (size_t)nres * vstride);
   KShared K;
   K.h = reinterpret_cast<double*>(kp);
   K.h1 = K.h + 2 * (cap + 1) + 2;
@@ -914,12 +1204,17 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
   T* colT = sc + 2 * (cap + 1);
   T* hT = colT + 2 * (cap + 1);
   T* h1T = hT + 2 * (cap + 1) + 2;
+  const TileView<T, R> tv = make_tile<T, R>(smem, on.OX, on.OY, on.ox0, on.oy0);
+  const int WX = on.OX + 2 * R, WY = on.OY + 2 * R;
+  const int gx0 = on.ox0 - R, gy0 = on.oy0 - R;
 
-  // beta = ||b|| over the own nodes, reduced over the grid
+  // beta = ||b|| over the own nodes, reduced over the grid; w_{-1} := b at the own nodes
   for (int q = threadIdx.x; q < nown; q += NT) Wt[q] = ldcg(b + on(q));
   __syncthreads();
-  dots_own<T>(V, n, 0, Wt, on, partA, bid, G, K.wred);
-  if (!grid_reduce(st, G, partA, 0, 1, nullptr, K.scal + 1)) return;
+  unsigned rc = 0;  // reductions so far: partial buffer rc & 1
+  dots_own3<T>(V, Vs, vstride, 0, n, 0, Wt, on, reinterpret_cast<T*>(partA), bid, G);
+  if (!grid_reduce_t<T>(st, G, reinterpret_cast<const T*>(partA), 1, K.scal + 1)) return;
+  ++rc;
   const double beta = sqrt(K.scal[1]);
   if (!(beta > 0)) {
     if (bid == 0 && threadIdx.x == 0) {
@@ -933,19 +1228,34 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
     gT[0] = T(beta);
     gT[1] = T(0);
   }
-  const cx<T>* src = b;
-  double s = 1.0 / beta;
+  T s = T(1.0 / beta);
+  const cx<T>* src = b;  // the vector the halo is read from: b, then the neighbours' w
   int jstop = 0;
   double est = beta;
-  // algorithmic bytes in units of one vector: ||b|| reads b once
   const double eb = (double)sizeof(cx<T>), ekb = (double)sizeof(T);
   double vec_units = 1.0, k_units = 0.0;
   int reorths = 0;
-  const TileView<T, R> tv = make_tile<T, R>(smem, on.OX, on.OY, on.ox0, on.oy0);
   for (int j = 0; j < cap; ++j) {
-    // op: V_j = s * src at the own nodes, W_own = M_l V_j
+    // ---- op: V_j = s w (own cells from shared memory, halo cells from global memory), z = M V_j
+    if (j > 0 && !wait_neighbours(st, nflag, tg, tx, ty, (unsigned)j)) return;
+    for (int idx = threadIdx.x; idx < WX * WY; idx += NT) {
+      const int cy = idx / WX, cxx = idx - cy * WX;
+      const int ox = cxx - R, oy = cy - R;
+      const int gx = gx0 + cxx, gy = gy0 + cy;
+      cx<T> v = mk<T>(T(0), T(0));
+      T kk = T(0);
+      if (gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny) {
+        const size_t e = (size_t)gy * P.nx + gx;
+        const bool own = ox >= 0 && ox < on.OX && oy >= 0 && oy < on.OY;
+        v = s * (own ? Wt[oy * on.OX + ox] : ldcg(src + e));
+        if (R >= 2) kk = P.k[e];
+      }
+      tv.U[idx] = v;
+      if (R >= 2) tv.W[idx] = (kk * kk) * v;
+    }
+    __syncthreads();
+    tile_finish<T, R>(tv, P);
     cx<T>* Vj = V + (size_t)j * n;
-    tile_fill<T, R>(tv, P, ScaledSrc<T>{src, P.nx, T(s)});
     for (int it = threadIdx.x; it < on.OX * ((on.OY + 3) / 4); it += NT) {
       const int ox = it % on.OX, sy = (it / on.OX) * 4;
       const int cnt = min(4, on.OY - sy);
@@ -953,89 +1263,77 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
       tile_op_seg<T, R>(tv, P, ox, sy, cnt, v);
       for (int k = 0; k < cnt; ++k) {
         const int q = (sy + k) * on.OX + ox;
+        const cx<T> u = tv.u(ox + R, sy + k + R);
         Wt[q] = v[k];
-        Vj[on(q)] = tv.u(ox + R, sy + k + R);
+        if (j < nres) Vs[j * vstride + q] = u;
+        else Vj[on(q)] = u;
       }
     }
     __syncthreads();
-    vec_units += 2.0;  // read the previous vector, write V_j (M_l V_j stays on chip)
+    vec_units += 2.0;  // read the previous vector, write V_j (z stays on chip)
     k_units += 1.0;
     const int nv = j + 1;
     vec_units += nv;  // V_0..V_j
-    dots_own<T>(V, n, nv, Wt, on, partA, bid, G, K.wred);
-    if (!grid_reduce(st, G, partA, 0, 2 * nv + 1, nullptr, K.h)) return;
-    bool updated = false;
-    {
-      const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
-      const double wn2 = K.h[2 * nv];
-      const double hp = wn2 - double(hs);
-      if (hp >= eta2 * wn2) {  // one pass: warp 0 rotates while the other warps update the own nodes
-        for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
-        __syncthreads();
-        if (threadIdx.x < 32) {
-          if (threadIdx.x == 0) {
-            K.scal[3] = hp;
-            K.flags[1] = 0;
-            givens_step<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
-                           K.scal);
-          }
-        } else {
-          for (int q = threadIdx.x - 32; q < nown; q += NT - 32) {
-            const size_t node = on(q);
-            wbuf[node] = axpy_all<T, true>(Wt[q], V, n, nv, sc, node);
-          }
+    T* part = reinterpret_cast<T*>((rc & 1) ? partB : partA);
+    dots_own3<T>(V, Vs, vstride, nres, n, nv, Wt, on, part, bid, G);
+    if (!grid_reduce_t<T>(st, G, part, 2 * nv + 1, K.h, hT)) return;
+    ++rc;
+    const double wn2 = K.h[2 * nv];
+    double hp = wn2 - double(warp0_sumsq<T>(hT, 2 * nv, hT + 2 * (cap + 1) + 1));
+    if (hp >= eta2 * wn2) {
+      // one pass: warp 0 rotates while the other warps form w = z - V h at the own nodes
+      if (threadIdx.x < 32) {
+        givens_step_warp<T>(j, cap, hT, (const T*)nullptr, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags,
+                            K.scal);
+      } else {
+        for (int q = threadIdx.x - 32; q < nown; q += NT - 32) {
+          const size_t e = on(q);
+          const cx<T> w = sub_comb<T>(Wt[q], nv, hT, OwnBasis<T>{Vs, V, vstride, q, nres, n, e});
+          Wt[q] = w;
+          wbuf[e] = w;
         }
-        updated = true;
-      } else if (threadIdx.x == 0) {
-        K.scal[3] = hp;
-        K.flags[1] = 1;
       }
-    }
-    __syncthreads();
-    if (K.flags[1]) {  // second classical pass on the own nodes (w stays in shared memory)
+      vec_units += nv + 1;
+    } else {
+      // second classical pass: w' = z - V h, h2 = V^H w', w'' = w' - V h2
       ++reorths;
-      vec_units += 2 * nv;
-      for (int i = threadIdx.x; i < 2 * nv; i += NT) {
-        sc[i] = T(K.h[i]);
-        h1T[i] = hT[i];
+      for (int i = threadIdx.x; i < 2 * nv; i += NT) h1T[i] = hT[i];
+      for (int q = threadIdx.x; q < nown; q += NT)
+        Wt[q] = sub_comb<T>(Wt[q], nv, hT, OwnBasis<T>{Vs, V, vstride, q, nres, n, on(q)});
+      __syncthreads();
+      T* part2 = reinterpret_cast<T*>((rc & 1) ? partB : partA);
+      dots_own3<T>(V, Vs, vstride, nres, n, nv, Wt, on, part2, bid, G);
+      if (!grid_reduce_t<T>(st, G, part2, 2 * nv + 1, K.h, hT)) return;
+      ++rc;
+      hp = K.h[2 * nv] - double(warp0_sumsq<T>(hT, 2 * nv, hT + 2 * (cap + 1) + 1));
+      if (threadIdx.x < 32) {
+        givens_step_warp<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags, K.scal);
+      } else {
+        for (int q = threadIdx.x - 32; q < nown; q += NT - 32) {
+          const size_t e = on(q);
+          const cx<T> w = sub_comb<T>(Wt[q], nv, hT, OwnBasis<T>{Vs, V, vstride, q, nres, n, e});
+          Wt[q] = w;
+          wbuf[e] = w;
+        }
       }
-      __syncthreads();
-      for (int q = threadIdx.x; q < nown; q += NT) Wt[q] = axpy_all<T, true>(Wt[q], V, n, nv, sc, on(q));
-      __syncthreads();
-      dots_own<T>(V, n, nv, Wt, on, partB, bid, G, K.wred);
-      if (!grid_reduce(st, G, partB, 0, 2 * nv + 1, nullptr, K.h)) return;
-      const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
-      if (threadIdx.x == 0) {
-        const double hp = K.h[2 * nv] - double(hs);
-        givens_step<T>(j, cap, h1T, hT, hp, colT, gcT, gsT, gT, tol_abs, K.scal + 2, K.flags, K.scal);
-      }
-      __syncthreads();
+      vec_units += 2 * nv + (nv + 1);
     }
+    s = hp > 0 ? T(1) / sqrt(T(hp)) : T(0);
+    src = wbuf;
+    flag_raise(nflag, bid, (unsigned)(j + 1));  // ends with the CTA barrier the rotation needs too
     if (bid == 0) {  // CTA 0 keeps the rotated column j (FP64) for the final triangular solve
       double* Rc = Rg + 2 * (size_t)j * (cap + 1);
       for (int i = threadIdx.x; i < 2 * nv; i += NT) Rc[i] = double(colT[i]);
-    }
-    if (!K.flags[0]) {  // w' = w - V h at the own nodes, to global memory for the neighbours' halos
-      vec_units += nv + 1;
-      if (!updated) {
-        for (int i = threadIdx.x; i < 2 * nv; i += NT) sc[i] = T(K.h[i]);
-        __syncthreads();
-        for (int q = threadIdx.x; q < nown; q += NT) {
-          const size_t node = on(q);
-          wbuf[node] = axpy_all<T, true>(Wt[q], V, n, nv, sc, node);
-        }
-      }
-      if (!grid_sync(st, G)) return;
     }
     est = K.scal[2];
     if (K.flags[0]) {
       jstop = j + 1;
       break;
     }
-    s = K.scal[0];
-    src = wbuf;
   }
-  // y = R^-1 g by warp 0 of CTA 0, then x += V y at the own nodes
+  // y = R^-1 g by warp 0 of CTA 0 (after the barrier that makes the last column of R visible
+  // to warp 0), then x += V y at the own nodes
+  __syncthreads();
   double* y = Rg + 2 * (size_t)cap * (cap + 1);
   if (bid == 0 && threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -1078,12 +1376,14 @@ __global__ void __launch_bounds__(NT) k_gmres_tile(OpP<T> P, TileGrid tg, const 
     st->total_bytes += (vec_units + jstop + 2) * eb * (double)n + k_units * ekb * (double)n;
   }
   if (!grid_sync(st, G)) return;
-  for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(__ldcg(y + i));
+  for (int i = threadIdx.x; i < 2 * jstop; i += NT) sc[i] = T(-__ldcg(y + i));
   __syncthreads();
+  // x + V y as x - V (-y): the combination routine with negated coefficients
   for (int q = threadIdx.x; q < nown; q += NT) {
-    const size_t node = on(q);
-    x[node] = axpy_all<T, false>(x[node], V, n, jstop, sc, node);
+    const size_t e = on(q);
+    x[e] = sub_comb<T>(x[e], jstop, sc, OwnBasis<T>{Vs, V, vstride, q, nres, n, e});
   }
+  timing_end(st, G);
 }
 
 template <typename T>
@@ -1120,9 +1420,37 @@ size_t kshared_bytes(int cap) {
   return tile_smem_bytes<T, R>(TileShape<TS>::X, TileShape<TS>::Y) + krylov_smem_bytes<T>(cap);
 }
 
+// Shared memory of the tile-owned form: tile, own z / w, nres own basis vectors, Krylov scratch.
 template <typename T, int R>
-size_t tile_form_smem(int TX, int TY, int cap) {
-  return tile_smem_bytes<T, R>(TX + 1, TY + 1) + sizeof(cx<T>) * (size_t)(TX + 1) * (TY + 1) + krylov_smem_bytes<T>(cap);
+size_t tile_form_smem(int TX, int TY, int cap, int nres = 0) {
+  const size_t vs = (size_t)(TX + 1) * (TY + 1);
+  return tile_smem_bytes<T, R>(TX + 1, TY + 1) + sizeof(cx<T>) * vs * (1 + (size_t)nres) + krylov_smem_bytes<T>(cap);
+}
+
+// Basis vectors of the own nodes that the tile-owned form keeps in shared memory: as many as fit
+// (at most cap + 1) while every tile stays co-resident.
+template <typename T, int R>
+int tile_form_nres(int nx, int ny, int cap, int TX, int TY) {
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  const size_t base = tile_form_smem<T, R>(TX, TY, cap, 0);
+  const size_t per_vec = sizeof(cx<T>) * (size_t)(TX + 1) * (TY + 1);
+  if (base > (size_t)optin) return 0;
+  int nres = (int)std::min<size_t>((size_t)cap + 1, ((size_t)optin - base) / per_vec);
+  const int tiles = tiles_along(nx, TX) * tiles_along(ny, TY);
+  for (; nres > 0; nres = nres > 8 ? nres - 8 : 0) {
+    const size_t sm = tile_form_smem<T, R>(TX, TY, cap, nres);
+    int per = 0;
+    if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile2<T, R>), sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres_tile2<T, R>, NT, sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (tiles <= per * sms) break;
+  }
+  return nres;
 }
 
 // Tile shapes of the tile-owned form that fit an nx x ny level: every CTA owns one tile and all
@@ -1141,12 +1469,12 @@ int tile_form_list(int nx, int ny, int cap, int* TXo, int* TYo, int maxc) {
     const size_t sm = tile_form_smem<T, R>(TX, TY, cap);
     if (sm > (size_t)optin) continue;
     const int nt = tiles_along(nx, TX) * tiles_along(ny, TY);
-    if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile<T, R>), sm) != cudaSuccess) {
+    if (hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile2<T, R>), sm) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres_tile<T, R>, NT, sm) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gmres_tile2<T, R>, NT, sm) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -1179,26 +1507,37 @@ int tile_form_choice(int nx, int ny, int cap, int* TXo, int* TYo) {
 }
 
 template <typename T, int R>
-cudaError_t gmres_tile_t(hz::Ctx& c, const hz::OpDesc& d, const void* b, void* x, void* V, void* w0, double* partA,
-                         double* partB, double* Rg, hz::GmresState* st, int cap, double tol, int TX, int TY,
-                         double eta2) {
+cudaError_t gmres_tile_t(hz::Ctx& c, const hz::OpDesc& d, const void* b, void* x, void* V, void* w0,
+                         unsigned* nflag, double* partA, double* partB, double* Rg, hz::GmresState* st, int cap,
+                         double tol, int TX, int TY, double eta2) {
   TileGrid tg;
   tg.TX = TX;
   tg.TY = TY;
   tg.ntx = tiles_along(d.nx, TX);
   tg.nty = tiles_along(d.ny, TY);
   const int grid = tg.ntx * tg.nty;
-  const size_t sm = tile_form_smem<T, R>(TX, TY, cap);
-  cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile<T, R>), sm);
+  // resident basis vectors, decided once per level shape and process
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, int> nres_cache;
+  int nres;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(d.nx, d.ny, cap, TX, TY);
+    auto it = nres_cache.find(key);
+    if (it == nres_cache.end()) it = nres_cache.emplace(key, tile_form_nres<T, R>(d.nx, d.ny, cap, TX, TY)).first;
+    nres = it->second;
+  }
+  const size_t sm = tile_form_smem<T, R>(TX, TY, cap, nres);
+  cudaError_t e = hz::ensure_dyn_smem(reinterpret_cast<const void*>(k_gmres_tile2<T, R>), sm);
   if (e != cudaSuccess) return e;
   OpP<T> P = mkop<T>(d);
   const cx<T>* bb = reinterpret_cast<const cx<T>*>(b);
   cx<T>* xx = reinterpret_cast<cx<T>*>(x);
   cx<T>* VV = reinterpret_cast<cx<T>*>(V);
   cx<T>* wb = reinterpret_cast<cx<T>*>(w0);
-  void* args[] = {&P, &tg, &bb, &xx, &VV, &wb, &partA, &partB, &Rg, &st, &cap, &tol, &eta2};
+  void* args[] = {&P, &tg, &bb, &xx, &VV, &wb, &nflag, &partA, &partB, &Rg, &st, &cap, &nres, &tol, &eta2};
   hz::ProfScope ps(c, hz::F_GMRES, 0.0);
-  return cudaLaunchCooperativeKernel((const void*)k_gmres_tile<T, R>, dim3(grid), dim3(NT), args, sm, c.s);
+  return cudaLaunchCooperativeKernel((const void*)k_gmres_tile2<T, R>, dim3(grid), dim3(NT), args, sm, c.s);
 }
 
 // The grid form uses 64 x 32 tiles on FP32 levels of at least 2^18 nodes with the radius-3
@@ -1342,41 +1681,28 @@ int gmres_cluster_size(int dt, int R, int cap) {
   return 0;
 }
 
+// The tile-owned form runs with FP32 vectors only (FP64 tiles would not fit the registers).
 int gmres_tile_form(int dt, int R, int nx, int ny, int cap, int* TX, int* TY) {
-  if (dt == C128) {
-    if (R == 1) return tile_form_choice<double, 1>(nx, ny, cap, TX, TY);
-    if (R == 2) return tile_form_choice<double, 2>(nx, ny, cap, TX, TY);
-    if (R == 3) return tile_form_choice<double, 3>(nx, ny, cap, TX, TY);
-  } else {
-    if (R == 1) return tile_form_choice<float, 1>(nx, ny, cap, TX, TY);
-    if (R == 2) return tile_form_choice<float, 2>(nx, ny, cap, TX, TY);
-    if (R == 3) return tile_form_choice<float, 3>(nx, ny, cap, TX, TY);
-  }
+  if (dt != C64) return 0;
+  if (R == 1) return tile_form_choice<float, 1>(nx, ny, cap, TX, TY);
+  if (R == 2) return tile_form_choice<float, 2>(nx, ny, cap, TX, TY);
+  if (R == 3) return tile_form_choice<float, 3>(nx, ny, cap, TX, TY);
   return 0;
 }
 
 int gmres_tile_forms(int dt, int R, int nx, int ny, int cap, int* TX, int* TY, int maxc) {
-  if (dt == C128) {
-    if (R == 1) return tile_form_list<double, 1>(nx, ny, cap, TX, TY, maxc);
-    if (R == 2) return tile_form_list<double, 2>(nx, ny, cap, TX, TY, maxc);
-    if (R == 3) return tile_form_list<double, 3>(nx, ny, cap, TX, TY, maxc);
-  } else {
-    if (R == 1) return tile_form_list<float, 1>(nx, ny, cap, TX, TY, maxc);
-    if (R == 2) return tile_form_list<float, 2>(nx, ny, cap, TX, TY, maxc);
-    if (R == 3) return tile_form_list<float, 3>(nx, ny, cap, TX, TY, maxc);
-  }
+  if (dt != C64) return 0;
+  if (R == 1) return tile_form_list<float, 1>(nx, ny, cap, TX, TY, maxc);
+  if (R == 2) return tile_form_list<float, 2>(nx, ny, cap, TX, TY, maxc);
+  if (R == 3) return tile_form_list<float, 3>(nx, ny, cap, TX, TY, maxc);
   return 0;
 }
 
 cudaError_t launch_gmres_tile(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* V, void* w0,
-                              double* partA, double* partB, double* Rg, GmresState* st, int cap, double tol, int TX,
-                              int TY, double eta2) {
-#define HZ_GT(T_, R_) return gmres_tile_t<T_, R_>(c, M, b, x, V, w0, partA, partB, Rg, st, cap, tol, TX, TY, eta2)
-  if (dt == C128) {
-    if (M.R == 1) HZ_GT(double, 1);
-    if (M.R == 2) HZ_GT(double, 2);
-    if (M.R == 3) HZ_GT(double, 3);
-  } else {
+                              unsigned* nflag, double* partA, double* partB, double* Rg, GmresState* st, int cap,
+                              double tol, int TX, int TY, double eta2) {
+#define HZ_GT(T_, R_) return gmres_tile_t<T_, R_>(c, M, b, x, V, w0, nflag, partA, partB, Rg, st, cap, tol, TX, TY, eta2)
+  if (dt == C64) {
     if (M.R == 1) HZ_GT(float, 1);
     if (M.R == 2) HZ_GT(float, 2);
     if (M.R == 3) HZ_GT(float, 3);

@@ -9,14 +9,17 @@
 // residual with the norms and keeps its block partial sums in a fixed static array.
 //
 // Scratch: g_partials, a file-scope __device__ array of 1216 x 2 x 64 doubles
-// (1216 CTAs x 2 sums x HZ_NOALLOC_MAX_RHS right-hand sides, 1.25 MB).  Every GPU that
-// loads the library holds it until the process exits.  Host code cannot use the array's
-// name as a device address, so its address is looked up once per device with
-// cudaGetSymbolAddress (the first call on each device does this; make that first call
-// before any stream capture).  Every call reuses the same array and each partial is
-// written before it is read, so nothing needs clearing; calls that overlap on the GPU
-// (concurrent streams, several host threads) race on the array and must be serialised.
+// (1216 CTAs x 2 sums x HZ_NOALLOC_MAX_RHS right-hand sides, 1.25 MB).  Every GPU on which
+// a handle was set up holds it until the process exits.  Host code cannot use the array's
+// name as a device address, so hz_setup looks the address up with cudaGetSymbolAddress on
+// the handle's device and queries both kernels' attributes there: with CUDA's lazy module
+// loading that is the moment the module (kernels and array) is loaded, so the array is
+// reserved during hz_setup and no call of this entry point, the first included, reserves
+// device memory.  Every call reuses the same array and each partial is written before it is
+// read, so nothing needs clearing; calls that overlap on the GPU (concurrent streams,
+// several host threads, several handles) race on the array and must be serialised.
 #include <mutex>
+#include <string>
 
 #include "hz_core.h"
 #include "hz_device.cuh"
@@ -113,11 +116,8 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 double* g_addr[kMaxDevices] = {};
 
-// Device address of g_partials on the current device (looked up once per device).
-int scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return hz::status_of(e, "cudaGetDevice");
+// Device address of g_partials on device dev (looked up once per device, with dev current).
+int scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) {
     hz::set_error("device index beyond the static scratch table");
     return HZ_ENOTSUP;
@@ -125,7 +125,7 @@ int scratch_address(double** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_partials);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
     if (e != cudaSuccess) return hz::status_of(e, "cudaGetSymbolAddress(g_partials)");
     g_addr[dev] = reinterpret_cast<double*>(p);
   }
@@ -134,6 +134,22 @@ int scratch_address(double** out) {
 }
 
 }  // namespace
+
+namespace hz {
+
+// Called by setup() with the handle's device current: loads this file's module (kernels and
+// the static array) and caches the array's device address.
+int noalloc_prepare(Handle* H) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_resid_norm);
+  if (e != cudaSuccess) return status_of(e, "cudaFuncGetAttributes(k_resid_norm)");
+  e = cudaFuncGetAttributes(&fa, k_resid_finish);
+  if (e != cudaSuccess) return status_of(e, "cudaFuncGetAttributes(k_resid_finish)");
+  double* part = nullptr;
+  return scratch_address(H->device, &part);
+}
+
+}  // namespace hz
 
 using namespace hz;
 
@@ -151,16 +167,37 @@ extern "C" int hz_true_residual_noalloc(hz_handle hp, const void* b, const void*
     return HZ_EINVAL;
   }
   hz::Handle* H = &hp->h;
+  // an error left by earlier, unrelated work is reported as such, not as this call's failure
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    hz::set_error(std::string("a CUDA error was pending before hz_true_residual_noalloc: ") + cudaGetErrorString(e));
+    return HZ_ECUDA;
+  }
+  int dev = -1;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hz::status_of(e, "cudaGetDevice");
+  if (dev != H->device) {
+    hz::set_error("the current CUDA device is not the device the handle was set up on");
+    return HZ_EINVAL;
+  }
   const hz::Level& L = H->lv[0];
   double* part = nullptr;
-  if (int s = scratch_address(&part)) return s;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    part = g_addr[dev];  // set by hz_setup on this device
+  }
+  if (!part) {
+    hz::set_error("the static scratch array was not prepared on this device");
+    return HZ_ENOTSUP;
+  }
   const size_t n = L.n;
   size_t nb = (n + kNT * 4 - 1) / (kNT * 4);
   const int nparts = (int)(nb < kParts ? (nb > 0 ? nb : 1) : kParts);
   k_resid_norm<<<dim3(nparts, nrhs), kNT, 0, H->ctx.s>>>(L.nx, L.ny, 1.0 / (H->g.h * H->g.h), H->g.h, L.k_d,
                                                          reinterpret_cast<const cx<double>*>(b),
                                                          reinterpret_cast<const cx<double>*>(u), part, H->g.bc);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return hz::status_of(e, "k_resid_norm");
   k_resid_finish<<<nrhs, kNT, 0, H->ctx.s>>>(part, nparts, relres_dev);
   e = cudaGetLastError();

@@ -90,8 +90,9 @@ def test_estimate_bytes_host_only(L):
     assert e(513, max_rhs=4, device_gmres=2, **m) < e(513, max_rhs=4, device_gmres=3, **m)
     assert e(513, max_rhs=3, device_gmres=1, **m) == e(513, max_rhs=3, device_gmres=2, **m)
     assert e(513, max_rhs=4, device_gmres=1, **m) == e(513, max_rhs=4, device_gmres=3, **m)
-    # FP64 vectors never take the cluster form
-    assert e(513, levels=5, max_rhs=4, device_gmres=3) == e(513, levels=5, max_rhs=4, device_gmres=2)
+    # FP64 vectors take the cluster form too (per-rhs workspace), like FP32
+    assert e(513, levels=5, max_rhs=4, device_gmres=3) > e(513, levels=5, max_rhs=4, device_gmres=2)
+    assert e(513, levels=5, max_rhs=4, device_gmres=1) == e(513, levels=5, max_rhs=4, device_gmres=3)
     assert e(513, levels=5, precision="mixed") < e(513, levels=5, precision="fp64")
     # a level with m iterations or a tolerance keeps a larger Krylov basis than a one-iteration level
     assert e(513, levels=5) < e(513, levels=5, cycle_m=2) < e(513, levels=5, cycle_m=3)
@@ -147,6 +148,8 @@ def test_diagnostics_reject_null_handles(L):
     assert L.hz_level_gmres_form(None, 1, ctypes.byref(f), ctypes.byref(c), ctypes.byref(cl)) == hz.HZ_EINVAL
     n = ctypes.c_longlong()
     assert L.hz_launch_count(None, ctypes.byref(n)) == hz.HZ_EINVAL
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    assert L.hz_gmres_device_time(None, 0, 0, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)) == hz.HZ_EINVAL
 
 
 def test_config_validation_of_new_fields(L):
