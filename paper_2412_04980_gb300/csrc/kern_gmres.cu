@@ -55,6 +55,22 @@ __device__ __forceinline__ cx<double> ldcg(const cx<double>* p) {
 
 __device__ __forceinline__ bool failed(const hz::GmresState* gs) { return *((volatile const int*)&gs->err) != 0; }
 
+// Asynchronous 8-byte global -> shared copies (one complex FP32 value; any 8-byte aligned source,
+// so the odd-length vectors of 2^k + 1 grids need no padding).  A thread waits only for its own
+// copies and reads only the slots it filled, so the pipelines below need no CTA barrier.
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The FP32 slice dots stream the basis through a ring of kStages stages of 8 x 512 complex values
+// in shared memory (the operator tile's space, unused between operator phases).
+constexpr int kStages = 3;
+constexpr size_t kRingBytes = (size_t)kStages * 8 * 512 * 8;
+
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -341,6 +357,90 @@ constexpr size_t kStreamSlice = 2 * NT; // slices above this use the streaming d
 // thread keeps its EPT values of w in registers and streams the basis one vector at a time
 // (EPT loads in flight per vector), accumulating 16 vectors per chunk before one warp
 // transpose-reduction and a fixed-order block combine per chunk.
+// FP32 streaming dots with the basis arriving through the cp.async ring (kStages - 1 vector blocks
+// in flight per thread instead of one); otherwise the same sums in the same order as dots_stream.
+__device__ void dots_stream_async(const cx<float>* V, size_t n, int nv, const cx<float>* w, double* part,
+                                  bool with_norm, double* wred, unsigned bid, unsigned G, cx<float>* ring) {
+  constexpr int EPT = 8, CH = 16;
+  constexpr size_t BLK = (size_t)EPT * NT;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  size_t s0, s1;
+  my_slice(n, bid, G, s0, s1);
+  const int nblk = (int)((s1 - s0 + BLK - 1) / BLK);
+  const int chunks = nv > 0 ? (nv + CH - 1) / CH : (with_norm ? 1 : 0);
+  for (int c = 0; c < chunks; ++c) {
+    const int c0 = c * CH;
+    const int cnt = max(0, min(CH, nv - c0));
+    const bool nrm = with_norm && c == 0;
+    const int total = nblk * cnt;  // stream positions t = block * cnt + vector
+    auto issue = [&](int t) {
+      if (t < total) {
+        const int bi = t / cnt, i = t - bi * cnt;
+        const size_t blk = s0 + (size_t)bi * BLK;
+        const cx<float>* Vi = V + (size_t)(c0 + i) * n;
+        cx<float>* stg = ring + (size_t)(t % kStages) * BLK;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const size_t e = blk + threadIdx.x + (size_t)k * NT;
+          if (e < s1) cp_async8(stg + threadIdx.x + k * NT, Vi + e);
+        }
+      }
+      cp_async_commit();
+    };
+    for (int t = 0; t < kStages - 1; ++t) issue(t);
+    float acc[2 * CH];
+#pragma unroll
+    for (int q = 0; q < 2 * CH; ++q) acc[q] = 0.f;
+    float wn = 0.f;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const size_t blk = s0 + (size_t)bi * BLK;
+      cx<float> wv[EPT];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const size_t e = blk + threadIdx.x + (size_t)k * NT;
+        wv[k] = e < s1 ? ldcg(w + e) : mk<float>(0.f, 0.f);
+        if (nrm) wn += wv[k].re * wv[k].re + wv[k].im * wv[k].im;
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        if (i < cnt) {
+          const int t = bi * cnt + i;
+          issue(t + kStages - 1);
+          cp_async_wait<kStages - 1>();
+          const cx<float>* stg = ring + (size_t)(t % kStages) * BLK;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const size_t e = blk + threadIdx.x + (size_t)k * NT;
+            const cx<float> v = e < s1 ? stg[threadIdx.x + k * NT] : mk<float>(0.f, 0.f);
+            acc[2 * i] += v.re * wv[k].re + v.im * wv[k].im;
+            acc[2 * i + 1] += v.re * wv[k].im - v.im * wv[k].re;
+          }
+        }
+      }
+    }
+    cp_async_wait<0>();
+    const float ws = warp_tsum<float, 2 * CH>(acc);
+    wred[wid * 2 * CH + lane] = double(ws);
+    if (nrm) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+      if (lane == 0) wred[NW * 2 * CH + wid] = double(wn);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * CH && (threadIdx.x >> 1) < cnt) {
+      double t = 0;
+      for (int q = 0; q < NW; ++q) t += wred[q * 2 * CH + threadIdx.x];
+      part[(size_t)(2 * c0 + threadIdx.x) * G + bid] = t;
+    }
+    if (nrm && threadIdx.x == 0) {
+      double t = 0;
+      for (int q = 0; q < NW; ++q) t += wred[NW * 2 * CH + q];
+      part[(size_t)(2 * nv) * G + bid] = t;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __device__ void dots_stream(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride,
                             bool with_norm, double* wred, unsigned bid, unsigned G) {
@@ -407,9 +507,18 @@ __device__ void dots_stream(const cx<T>* V, size_t n, int nv, const cx<T>* w, do
 
 template <typename T>
 __device__ void dots_pass(const cx<T>* V, size_t n, int nv, const cx<T>* w, double* part, int pstride, bool with_norm,
-                          double* wred, unsigned bid, unsigned G) {
-  if ((n + G - 1) / G > kStreamSlice) dots_stream<T>(V, n, nv, w, part, pstride, with_norm, wred, bid, G);
-  else dots_warp<T>(V, n, nv, w, part, pstride, with_norm, bid, G);
+                          double* wred, unsigned bid, unsigned G, void* ring = nullptr) {
+  if ((n + G - 1) / G > kStreamSlice) {
+    if constexpr (sizeof(T) == 4) {
+      if (ring) {
+        dots_stream_async(V, n, nv, w, part, with_norm, wred, bid, G, reinterpret_cast<cx<float>*>(ring));
+        return;
+      }
+    }
+    dots_stream<T>(V, n, nv, w, part, pstride, with_norm, wred, bid, G);
+  } else {
+    dots_warp<T>(V, n, nv, w, part, pstride, with_norm, bid, G);
+  }
 }
 
 // x[e] (+/-)= sum_i c_i V_i[e]; 8 vectors per step with all loads issued first (8 in flight).
@@ -720,7 +829,11 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
   constexpr int TOX = TileShape<TS>::X, TOY = TileShape<TS>::Y;
   const int tilesx = (P.nx + TOX - 1) / TOX, tilesy = (P.ny + TOY - 1) / TOY;
   const int ntiles = tilesx * tilesy;
-  unsigned char* kp = smem + tile_smem_bytes<T, R>(TOX, TOY);
+  // the operator tile, and for FP32 the cp.async ring of the vector phases, share the first region
+  constexpr size_t kTileRegion = tile_smem_bytes<T, R>(TOX, TOY);
+  constexpr size_t kRegion = (sizeof(T) == 4 && kRingBytes > kTileRegion) ? kRingBytes : kTileRegion;
+  void* ring = sizeof(T) == 4 ? (void*)smem : nullptr;
+  unsigned char* kp = smem + kRegion;
   KShared K;
   K.h = reinterpret_cast<double*>(kp);
   K.h1 = K.h + 2 * (cap + 1) + 2;
@@ -809,7 +922,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     // loses more than reorth_eta of its norm, in which case a second classical pass runs
     const int nv = j + 1;
     vec_units += nv + 1;  // read V_0..V_j and w
-    dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
+    dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G, ring);
     if (!reduce_all<CL>(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
     bool updated = false;
     {
@@ -845,7 +958,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
       update_pass<T>(V, n, nv, K.h, sc, wnext, bid, G);
       if (!bar_all<CL>(st, G)) return;
       for (int i = threadIdx.x; i < 2 * nv; i += NT) h1T[i] = hT[i];
-      dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G);
+      dots_pass<T>(V, n, nv, wnext, partA, pstride, true, K.wred, bid, G, ring);
       if (!reduce_all<CL>(st, G, partA, pstride, 2 * nv + 1, red, K.h)) return;
       const T hs = typed_copy_sumsq<T>(K.h, hT, 2 * nv, 2 * nv, hT + 2 * (cap + 1) + 1);
       if (threadIdx.x < 32) {
@@ -1417,7 +1530,9 @@ size_t krylov_smem_bytes(int cap) {
 
 template <typename T, int R, int TS = 0>
 size_t kshared_bytes(int cap) {
-  return tile_smem_bytes<T, R>(TileShape<TS>::X, TileShape<TS>::Y) + krylov_smem_bytes<T>(cap);
+  const size_t tile = tile_smem_bytes<T, R>(TileShape<TS>::X, TileShape<TS>::Y);
+  const size_t region = (sizeof(T) == 4 && kRingBytes > tile) ? kRingBytes : tile;
+  return region + krylov_smem_bytes<T>(cap);
 }
 
 // Shared memory of the tile-owned form: tile, own z / w, nres own basis vectors, Krylov scratch.

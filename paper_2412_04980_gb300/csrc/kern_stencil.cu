@@ -408,6 +408,353 @@ __global__ void __launch_bounds__(BX* BY) k_mg_up(OpP<T> P, const cx<T>* __restr
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Radius-1 multigrid sweeps as column strips.  A warp owns 64 consecutive grid columns, two per
+// lane, and walks down a band of rows keeping a window of rows in registers; a lane's own pair
+// supplies one horizontal neighbour of each of its nodes and the adjacent lanes the other (one
+// shuffle each way), so the sweep needs no shared-memory tile and no per-node index arithmetic.
+// The first and last lane of a warp only supply neighbours (the strips of adjacent warps overlap
+// by two columns on each side and compute those twice).
+//
+// With the radius-1 operator M u = D u - c S(u), D the exact diagonal (ghost feedback included)
+// and S(u) the sum of the four neighbours with the Sommerfeld ghost replaced by the inner
+// neighbour (its boundary term is in D), the pre-smoothed residual of the zero initial guess
+// u0 = omega f / D is r = f - M u0 = (1 - omega) f + c S(u0), and the post-smoothing step
+// y = u + omega (f - M u) / D with u = u0 + e is y = (1 - omega) u + u0 + omega c S(u) / D.
+template <typename T>
+__device__ __forceinline__ T r1_recip(T x) {
+  if constexpr (sizeof(T) == 4) return __fdividef(1.f, x);  // FP32 sweeps: approximate reciprocal
+  else return T(1) / x;
+}
+
+// Per-lane column data of one of the lane's two columns.
+struct R1Col {
+  int g;       // grid column
+  bool in;     // inside the grid
+  int bnd;     // 1 on the left or right boundary column (Sommerfeld)
+};
+
+template <typename T>
+struct R1Ops {  // operator constants in the sweep's type
+  T c4, ksr, ksi, c2H, c;
+  int bc, nx, ny;
+  __device__ __forceinline__ void diag(T kk, int g, T& dr, T& di) const {  // D at a node on g boundary sides
+    const T k2 = kk * kk;
+    dr = fma(-ksr, k2, c4);
+    di = -ksi * k2;
+    if (g) di -= c2H * kk * T(g);
+  }
+};
+
+// fc = FW(f - M(omega f / D)) on the coarse grid; coarse node I sits at fine node 2I + dof.
+// Strip s, lane L: coarse column I = 30 s + L - 1 at fine columns 2I + dof (a) and 2I + dof + 1
+// (b); outputs at lanes 1 .. 30.  Band: coarse rows J0 .. J0 + RB - 1.  A warp whose window
+// touches no boundary row or column (IN) runs without in-grid tests and ghost handling.
+constexpr int kPF = 3;  // rows of loads in flight per lane
+template <typename T, bool IN>
+__device__ __forceinline__ void mg_down_band(const OpP<T>& P, const cx<T>* __restrict__ f, cx<T>* __restrict__ fcz,
+                                             int ncx, int ncy, T omega, int I, int J0, int RB, int lane) {
+  const int dof = P.bc != 0;
+  const bool som = !IN && P.bc == 0;
+  const T c4 = T(4) * P.c, c2H = P.c * T(2) * P.H, om1 = T(1) - omega;
+  const int ga = 2 * I + dof, gb = ga + 1;
+  const bool ain = IN || (ga >= 0 && ga < P.nx), bin = IN || (gb >= 0 && gb < P.nx);
+  const int abnd = som && ain && (ga == 0 || ga == P.nx - 1), bbnd = som && bin && (gb == 0 || gb == P.nx - 1);
+  const int yb = 2 * J0 + dof - 2, ye = 2 * (J0 + RB) + dof;
+  // lane pointers to columns a and b of row yb (clamped for lanes outside the grid)
+  const cx<T>* fp = f + (size_t)max(yb, 0) * P.nx + max(min(ga, P.nx - 2), 0);
+  const T* kp = P.k + (size_t)max(yb, 0) * P.nx + max(min(ga, P.nx - 2), 0);
+  const int fda = ga - max(min(ga, P.nx - 2), 0);  // 0, or -1 / +1 ... for clamped edge lanes
+  auto load = [&](int gy, cx<T>& fa, cx<T>& fb, T& ka, T& kb) {
+    if (IN) {
+      const size_t o = (size_t)(gy - yb) * P.nx;
+      fa = fp[o];
+      fb = fp[o + 1];
+      ka = kp[o];
+      kb = kp[o + 1];
+    } else {
+      const bool rin = gy >= 0 && gy < P.ny;
+      const size_t o = (size_t)(gy - max(yb, 0)) * P.nx;
+      fa = (rin && ain) ? fp[o + fda] : mk<T>(T(0), T(0));
+      fb = (rin && bin) ? fp[o + fda + 1] : mk<T>(T(0), T(0));
+      ka = (rin && ain) ? kp[o + fda] : T(0);
+      kb = (rin && bin) ? kp[o + fda + 1] : T(0);
+    }
+  };
+  auto smooth0 = [&](bool cin, int cbnd, int gy, cx<T> fv, T kv) -> cx<T> {  // u0 = omega f / D
+    if (!IN && !(cin && gy >= 0 && gy < P.ny)) return mk<T>(T(0), T(0));
+    const T k2 = kv * kv;
+    const T dr = fma(-P.ksr, k2, c4);
+    T di = -P.ksi * k2;
+    if (som) {
+      const int g = cbnd + (gy == 0 || gy == P.ny - 1);
+      if (g) di -= c2H * kv * T(g);
+    }
+    const T inv = omega * r1_recip<T>(dr * dr + di * di);
+    return mk<T>((fv.re * dr + fv.im * di) * inv, (fv.im * dr - fv.re * di) * inv);
+  };
+  cx<T> fa_m1 = mk<T>(T(0), T(0)), fb_m1 = fa_m1;
+  cx<T> ua_m2 = fa_m1, ub_m2 = fa_m1, ua_m1 = fa_m1, ub_m1 = fa_m1;
+  cx<T> rhA = fa_m1, rhB = fa_m1;
+  cx<T> pfa[kPF], pfb[kPF];
+  T pka[kPF], pkb[kPF];
+#pragma unroll
+  for (int q = 0; q < kPF; ++q) load(yb + q, pfa[q], pfb[q], pka[q], pkb[q]);
+  for (int y0 = yb; y0 <= ye; y0 += kPF) {
+#pragma unroll
+    for (int q = 0; q < kPF; ++q) {
+      const int y = y0 + q;
+      if (y > ye) break;
+      const cx<T> fa = pfa[q], fb = pfb[q];
+      const T ka = pka[q], kb = pkb[q];
+      if (y + kPF <= ye) load(y + kPF, pfa[q], pfb[q], pka[q], pkb[q]);
+      const cx<T> ua = smooth0(ain, abnd, y, fa, ka), ub = smooth0(bin, bbnd, y, fb, kb);
+      if (y >= yb + 2) {
+        const int yr = y - 1;  // residual row: u0 rows yr - 1 (m2), yr (m1), yr + 1 (this)
+        cx<T> wa = mk<T>(__shfl_up_sync(0xffffffffu, ub_m1.re, 1), __shfl_up_sync(0xffffffffu, ub_m1.im, 1));
+        cx<T> eb = mk<T>(__shfl_down_sync(0xffffffffu, ua_m1.re, 1), __shfl_down_sync(0xffffffffu, ua_m1.im, 1));
+        cx<T> ea = ub_m1, wb = ua_m1;
+        cx<T> sa = ua_m2, na = ua, sb = ub_m2, nb = ub;
+        if (som) {  // ghosts take the inner neighbour
+          if (ga == 0) wa = ea;
+          if (ga == P.nx - 1) ea = wa;
+          if (gb == 0) wb = eb;
+          if (gb == P.nx - 1) eb = wb;
+          if (yr == 0) {
+            sa = na;
+            sb = nb;
+          }
+          if (yr == P.ny - 1) {
+            na = sa;
+            nb = sb;
+          }
+        }
+        cx<T> ra = om1 * fa_m1 + P.c * ((wa + ea) + (sa + na));
+        cx<T> rb = om1 * fb_m1 + P.c * ((wb + eb) + (sb + nb));
+        if (!IN) {
+          const bool rin = yr >= 0 && yr < P.ny;
+          if (!(rin && ain)) ra = mk<T>(T(0), T(0));
+          if (!(rin && bin)) rb = mk<T>(T(0), T(0));
+        }
+        // horizontal full weighting 1 2 1 centred on column a: r(a - 1) is the previous lane's rb
+        const cx<T> rw = mk<T>(__shfl_up_sync(0xffffffffu, rb.re, 1), __shfl_up_sync(0xffffffffu, rb.im, 1));
+        const cx<T> rh = (rw + rb) + T(2) * ra;
+        if (((yr - dof) & 1) != 0) {  // row 2J + dof + 1 (or the band's first row 2 J0 + dof - 1)
+          if (yr > 2 * J0 + dof - 1) {
+            const int J = (yr - dof - 1) / 2;
+            if (lane >= 1 && lane <= 30 && I < ncx && J < ncy) fcz[(size_t)J * ncx + I] = T(0.0625) * ((rhA + rh) + T(2) * rhB);
+          }
+          rhA = rh;
+        } else {
+          rhB = rh;
+        }
+      }
+      fa_m1 = fa;
+      fb_m1 = fb;
+      ua_m2 = ua_m1;
+      ub_m2 = ub_m1;
+      ua_m1 = ua;
+      ub_m1 = ub;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_down_r1(OpP<T> P, const cx<T>* __restrict__ f, cx<T>* __restrict__ fc,
+                                                    int ncx, int ncy, T omega, int RB) {
+  const int lane = threadIdx.x & 31;
+  const int strip = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (30 * strip >= ncx) return;  // whole warp
+  const int dof = P.bc != 0;
+  const int I = 30 * strip + lane - 1;
+  const int J0 = blockIdx.y * RB;
+  f += (size_t)blockIdx.z * P.nx * P.ny;
+  fc += (size_t)blockIdx.z * ncx * ncy;
+  // the warp's window: columns 2(30 s - 1) + dof .. 2(30 s + 30) + dof + 1, rows 2 J0 + dof - 2 ..
+  // 2 (J0 + RB) + dof, all strictly inside the grid (no boundary node, no outside node)
+  const int x0 = 2 * (30 * strip - 1) + dof, x1 = 2 * (30 * strip + 30) + dof + 1;
+  const int y0 = 2 * J0 + dof - 2, y1 = 2 * (J0 + RB) + dof;
+  const bool interior = x0 >= 1 && x1 <= P.nx - 2 && y0 >= 1 && y1 <= P.ny - 2;
+  if (interior) mg_down_band<T, true>(P, f, fc, ncx, ncy, omega, I, J0, RB, lane);
+  else mg_down_band<T, false>(P, f, fc, ncx, ncy, omega, I, J0, RB, lane);
+}
+
+// y = (1 - omega) u + u0 + omega c S(u) / D [+ add], u = u0 + P ec, u0 = omega f / D: the fused
+// bilinear correction and post-smoothing sweep.  Strip s, lane L: vertex columns 2V and 2V + 1
+// with V = 30 s + L - 1 (vertex column v is grid column v - dof: Dirichlet grids hold interior
+// unknowns, fine unknown g is vertex g + 1 and coarse unknown I is vertex I + 1, zero at the
+// vertices the grid omits), so the lane needs coarse vertex V (the next lane supplies V + 1);
+// outputs at lanes 1 .. 30.  Band: rows Y0 .. Y0 + RB - 1.
+template <typename T, bool IN>
+__device__ __forceinline__ void mg_up_band(const OpP<T>& P, const cx<T>* __restrict__ f, const cx<T>* __restrict__ ec,
+                                           int ncx, int ncy, cx<T>* __restrict__ y, T omega,
+                                           const cx<T>* __restrict__ add, int V, int Y0, int RB, int lane) {
+  const int dof = P.bc != 0;
+  const bool som = !IN && P.bc == 0;
+  const T c4 = T(4) * P.c, c2H = P.c * T(2) * P.H, om1 = T(1) - omega, omc = omega * P.c;
+  const int ga = 2 * V - dof, gb = ga + 1;
+  const bool ain = IN || (ga >= 0 && ga < P.nx), bin = IN || (gb >= 0 && gb < P.nx);
+  const int abnd = som && ain && (ga == 0 || ga == P.nx - 1), bbnd = som && bin && (gb == 0 || gb == P.nx - 1);
+  const bool outl = lane >= 1 && lane <= 30;
+  const int Ic = V - dof;
+  const bool icin = Ic >= 0 && Ic < ncx;
+  auto ecv = [&](int Jv) -> cx<T> {
+    const int J = Jv - dof;
+    return (icin && J >= 0 && J < ncy) ? ec[(size_t)J * ncx + Ic] : mk<T>(T(0), T(0));
+  };
+  const int ccol = max(min(ga, P.nx - 2), 0), fda = ga - ccol;
+  auto load = [&](int gy, cx<T>& fa, cx<T>& fb, T& ka, T& kb) {
+    if (IN) {
+      const size_t o = (size_t)gy * P.nx + ga;
+      fa = f[o];
+      fb = f[o + 1];
+      ka = P.k[o];
+      kb = P.k[o + 1];
+    } else {
+      const bool rin = gy >= 0 && gy < P.ny;
+      const size_t o = (size_t)max(gy, 0) * P.nx + ccol + fda;
+      fa = (rin && ain) ? f[o] : mk<T>(T(0), T(0));
+      fb = (rin && bin) ? f[o + 1] : mk<T>(T(0), T(0));
+      ka = (rin && ain) ? P.k[o] : T(0);
+      kb = (rin && bin) ? P.k[o + 1] : T(0);
+    }
+  };
+  const int yb = Y0 - 1, ye = min(Y0 + RB, P.ny);  // window rows yb .. ye (inclusive)
+  int gyv = yb + dof;
+  int Jv = gyv >= 0 ? (gyv >> 1) : -((1 - gyv) >> 1);
+  cx<T> c0 = ecv(Jv), c1 = ecv(Jv + 1), c2 = ecv(Jv + 2);  // coarse rows Jv .. Jv + 2 at column V
+  cx<T> pfa[kPF], pfb[kPF];
+  T pka[kPF], pkb[kPF];
+#pragma unroll
+  for (int q = 0; q < kPF; ++q) load(yb + q, pfa[q], pfb[q], pka[q], pkb[q]);
+  cx<T> ua_m2 = mk<T>(T(0), T(0)), ub_m2 = ua_m2, ua_m1 = ua_m2, ub_m1 = ua_m2;
+  cx<T> u0a_m1 = ua_m2, u0b_m1 = ua_m2;
+  T dra_m1 = T(0), dia_m1 = T(0), iva_m1 = T(0), drb_m1 = T(0), dib_m1 = T(0), ivb_m1 = T(0);
+  for (int y00 = yb; y00 <= ye; y00 += kPF) {
+#pragma unroll
+    for (int q = 0; q < kPF; ++q) {
+      const int gy = y00 + q;
+      if (gy > ye) break;
+      const cx<T> fa = pfa[q], fb = pfb[q];
+      const T ka = pka[q], kb = pkb[q];
+      if (gy + kPF <= ye) load(gy + kPF, pfa[q], pfb[q], pka[q], pkb[q]);
+      const int gv = gy + dof;
+      const int Jn = gv >= 0 ? (gv >> 1) : -((1 - gv) >> 1);
+      if (Jn != Jv) {  // advanced to the next coarse row
+        Jv = Jn;
+        c0 = c1;
+        c1 = c2;
+        c2 = ecv(Jv + 2);
+      }
+      // bilinear correction at vertex columns 2V (the coarse value) and 2V + 1 (with V + 1)
+      const cx<T> cv = (gv & 1) ? T(0.5) * (c0 + c1) : c0;
+      const cx<T> cn = mk<T>(__shfl_down_sync(0xffffffffu, cv.re, 1), __shfl_down_sync(0xffffffffu, cv.im, 1));
+      const cx<T> ea = cv, eb = T(0.5) * (cv + cn);
+      const bool rin = IN || (gy >= 0 && gy < P.ny);
+      const int gyb = som && (gy == 0 || gy == P.ny - 1);
+      cx<T> ua = mk<T>(T(0), T(0)), ub = ua, u0a = ua, u0b = ua;
+      T dra = T(0), dia = T(0), iva = T(0), drb = T(0), dib = T(0), ivb = T(0);
+      if (rin && ain) {
+        const T k2 = ka * ka;
+        dra = fma(-P.ksr, k2, c4);
+        dia = -P.ksi * k2;
+        if (som) {
+          const int g = abnd + gyb;
+          if (g) dia -= c2H * ka * T(g);
+        }
+        iva = r1_recip<T>(dra * dra + dia * dia);
+        u0a = mk<T>(omega * (fa.re * dra + fa.im * dia) * iva, omega * (fa.im * dra - fa.re * dia) * iva);
+        ua = u0a + ea;
+      }
+      if (rin && bin) {
+        const T k2 = kb * kb;
+        drb = fma(-P.ksr, k2, c4);
+        dib = -P.ksi * k2;
+        if (som) {
+          const int g = bbnd + gyb;
+          if (g) dib -= c2H * kb * T(g);
+        }
+        ivb = r1_recip<T>(drb * drb + dib * dib);
+        u0b = mk<T>(omega * (fb.re * drb + fb.im * dib) * ivb, omega * (fb.im * drb - fb.re * dib) * ivb);
+        ub = u0b + eb;
+      }
+      if (gy >= yb + 2) {  // output row gy - 1
+        const int yr = gy - 1;
+        cx<T> wa = mk<T>(__shfl_up_sync(0xffffffffu, ub_m1.re, 1), __shfl_up_sync(0xffffffffu, ub_m1.im, 1));
+        cx<T> eb2 = mk<T>(__shfl_down_sync(0xffffffffu, ua_m1.re, 1), __shfl_down_sync(0xffffffffu, ua_m1.im, 1));
+        cx<T> ea2 = ub_m1, wb = ua_m1;
+        cx<T> sa = ua_m2, na = ua, sb = ub_m2, nb = ub;
+        if (som) {
+          if (ga == 0) wa = ea2;
+          if (ga == P.nx - 1) ea2 = wa;
+          if (gb == 0) wb = eb2;
+          if (gb == P.nx - 1) eb2 = wb;
+          if (yr == 0) {
+            sa = na;
+            sb = nb;
+          }
+          if (yr == P.ny - 1) {
+            na = sa;
+            nb = sb;
+          }
+        }
+        if (outl && (IN || (yr >= Y0 && yr < P.ny))) {
+          const size_t o = (size_t)yr * P.nx;
+          if (ain) {
+            const cx<T> sn = (wa + ea2) + (sa + na);
+            const cx<T> qv = mk<T>((sn.re * dra_m1 + sn.im * dia_m1) * iva_m1, (sn.im * dra_m1 - sn.re * dia_m1) * iva_m1);
+            cx<T> out = (om1 * ua_m1 + u0a_m1) + omc * qv;
+            if (add) out = out + add[o + ga];
+            y[o + ga] = out;
+          }
+          if (bin) {
+            const cx<T> sn = (wb + eb2) + (sb + nb);
+            const cx<T> qv = mk<T>((sn.re * drb_m1 + sn.im * dib_m1) * ivb_m1, (sn.im * drb_m1 - sn.re * dib_m1) * ivb_m1);
+            cx<T> out = (om1 * ub_m1 + u0b_m1) + omc * qv;
+            if (add) out = out + add[o + gb];
+            y[o + gb] = out;
+          }
+        }
+      }
+      ua_m2 = ua_m1;
+      ub_m2 = ub_m1;
+      ua_m1 = ua;
+      ub_m1 = ub;
+      u0a_m1 = u0a;
+      u0b_m1 = u0b;
+      dra_m1 = dra;
+      dia_m1 = dia;
+      iva_m1 = iva;
+      drb_m1 = drb;
+      dib_m1 = dib;
+      ivb_m1 = ivb;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mg_up_r1(OpP<T> P, const cx<T>* __restrict__ f, const cx<T>* __restrict__ ec,
+                                                  int ncx, int ncy, cx<T>* __restrict__ y, T omega,
+                                                  const cx<T>* __restrict__ add, int RB) {
+  const int lane = threadIdx.x & 31;
+  const int strip = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int dof = P.bc != 0;
+  if (60 * strip - dof >= P.nx) return;  // whole warp
+  const int V = 30 * strip + lane - 1;
+  const int Y0 = blockIdx.y * RB;
+  const size_t off = (size_t)blockIdx.z * P.nx * P.ny;
+  f += off;
+  y += off;
+  ec += (size_t)blockIdx.z * ncx * ncy;
+  if (add) add += off;
+  // window columns 60 s - 2 - dof .. 60 s + 59 - dof (lanes 0 .. 31), rows Y0 - 1 .. Y0 + RB: all
+  // strictly inside the grid
+  const int x0 = 60 * strip - 2 - dof, x1 = 60 * strip + 61 - dof;
+  const bool interior = x0 >= 1 && x1 <= P.nx - 2 && Y0 - 1 >= 1 && Y0 + RB <= P.ny - 2;
+  if (interior) mg_up_band<T, true>(P, f, ec, ncx, ncy, y, omega, add, V, Y0, RB, lane);
+  else mg_up_band<T, false>(P, f, ec, ncx, ncy, y, omega, add, V, Y0, RB, lane);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fw(const cx<T>* __restrict__ r, int nx, int ny, cx<T>* __restrict__ rc,
                                             int ncx, int ncy, int dof) {
@@ -612,6 +959,42 @@ cudaError_t launch_defl_restrict(Ctx& c, int tin, int tout, int nx, int ny, cons
   return cudaErrorInvalidValue;
 }
 
+// Band height (rows per warp) of a strip sweep: the tallest band up to maxrb that still gives
+// about 16 warps per SM (152 SMs), at least 2 rows.
+static int band_rows(int strips, int rows, int nrhs, int maxrb) {
+  const long long want = 152LL * 16;
+  int rb = maxrb;
+  while (rb > 2 && (long long)strips * ((rows + rb - 1) / rb) * nrhs < want) rb /= 2;
+  return rb;
+}
+
+template <typename T>
+static cudaError_t down_r1(Ctx& c, const OpDesc& d, const void* f, void* fc, double omega, int nrhs) {
+  const int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
+  ProfScope ps(c, F_MG_DOWN, (double)nrhs * ((double)d.n() * (sizeof(cx<T>) + sizeof(T)) + (double)ncx * ncy * sizeof(cx<T>)));
+  const int strips = (ncx + 29) / 30;
+  const int RB = band_rows(strips, ncy, nrhs, 16);
+  dim3 grid((strips + 7) / 8, (ncy + RB - 1) / RB, nrhs);
+  k_mg_down_r1<T><<<grid, 256, 0, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f), reinterpret_cast<cx<T>*>(fc),
+                                         ncx, ncy, T(omega), RB);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t up_r1(Ctx& c, const OpDesc& d, const void* f, const void* ec, void* y, double omega,
+                         const void* add, int nrhs) {
+  const int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
+  double bytes = (double)nrhs * ((double)d.n() * (sizeof(cx<T>) * (add ? 3 : 2) + sizeof(T)) + (double)ncx * ncy * sizeof(cx<T>));
+  ProfScope ps(c, F_MG_UP, bytes);
+  const int strips = (d.nx + d.bc + 59) / 60;
+  const int RB = band_rows(strips, d.ny, nrhs, 32);
+  dim3 grid((strips + 7) / 8, (d.ny + RB - 1) / RB, nrhs);
+  k_mg_up_r1<T><<<grid, 256, 0, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f),
+                                       reinterpret_cast<const cx<T>*>(ec), ncx, ncy, reinterpret_cast<cx<T>*>(y),
+                                       T(omega), reinterpret_cast<const cx<T>*>(add), RB);
+  return cudaGetLastError();
+}
+
 template <typename T, int R>
 static cudaError_t down_r(Ctx& c, const OpDesc& d, const void* f, void* fc, double omega, int nrhs) {
   int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
@@ -628,11 +1011,11 @@ static cudaError_t down_r(Ctx& c, const OpDesc& d, const void* f, void* fc, doub
 
 cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void* fc, double omega, int nrhs) {
   if (dt == C128) {
-    if (op.R == 1) return down_r<double, 1>(c, op, f, fc, omega, nrhs);
+    if (op.R == 1) return down_r1<double>(c, op, f, fc, omega, nrhs);
     if (op.R == 2) return down_r<double, 2>(c, op, f, fc, omega, nrhs);
     if (op.R == 3) return down_r<double, 3>(c, op, f, fc, omega, nrhs);
   } else {
-    if (op.R == 1) return down_r<float, 1>(c, op, f, fc, omega, nrhs);
+    if (op.R == 1) return down_r1<float>(c, op, f, fc, omega, nrhs);
     if (op.R == 2) return down_r<float, 2>(c, op, f, fc, omega, nrhs);
     if (op.R == 3) return down_r<float, 3>(c, op, f, fc, omega, nrhs);
   }
@@ -663,11 +1046,11 @@ cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const 
   (void)yout2;
   (void)tout2;
   if (dt == C128) {
-    if (op.R == 1) return up_r<double, 1>(c, op, f, ec, y, omega, add, nrhs);
+    if (op.R == 1) return up_r1<double>(c, op, f, ec, y, omega, add, nrhs);
     if (op.R == 2) return up_r<double, 2>(c, op, f, ec, y, omega, add, nrhs);
     if (op.R == 3) return up_r<double, 3>(c, op, f, ec, y, omega, add, nrhs);
   } else {
-    if (op.R == 1) return up_r<float, 1>(c, op, f, ec, y, omega, add, nrhs);
+    if (op.R == 1) return up_r1<float>(c, op, f, ec, y, omega, add, nrhs);
     if (op.R == 2) return up_r<float, 2>(c, op, f, ec, y, omega, add, nrhs);
     if (op.R == 3) return up_r<float, 3>(c, op, f, ec, y, omega, add, nrhs);
   }
