@@ -123,7 +123,7 @@ def parse():
                          "and batch), 2 cooperative grid, 3 cluster, 4 slice grid, 0 host-driven")
     ap.add_argument("--reorth-eta", type=float, default=None,
                     help="Gram-Schmidt reorthogonalisation threshold (library default if omitted)")
-    ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply", "levelop", "prolong"],
+    ap.add_argument("--micro", default=None, choices=["gmres", "vcycle", "apply", "levelop", "prolong", "restrict"],
                     help="time one building block on the workload's finest grid instead of a solve")
     ap.add_argument("--repeat", type=int, default=20)
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per call in --micro mode")
@@ -434,12 +434,12 @@ def micro(args):
     extra = {"mg_max_level": 0} if args.micro == "gmres" else {}
     if args.device_gmres is not None:
         extra["device_gmres"] = args.device_gmres
-    lev = args.level if args.micro in ("gmres", "levelop", "prolong") else 1
-    if lev > 1 or args.micro == "prolong":
+    lev = args.level if args.micro in ("gmres", "levelop", "prolong", "restrict") else 1
+    if lev > 1 or args.micro in ("prolong", "restrict"):
         # a coarse level (or the level above a prolongation) with the default multigrid on levels
         # 1-2 and minimal Krylov bases above
         extra = {k_: v for k_, v in extra.items() if k_ != "mg_max_level"}
-        H = hz.Helmholtz(k, p.h, levels=lev + (1 if args.micro == "prolong" else 0), precision=prec,
+        H = hz.Helmholtz(k, p.h, levels=lev + (1 if args.micro in ("prolong", "restrict") else 0), precision=prec,
                          max_rhs=args.nrhs, restart=1, l2_maxit=1, negdef_from_level=p.negdef_from_level, **extra)
     else:
         H = hz.Helmholtz(k, p.h, levels=1, precision=prec, max_rhs=args.nrhs, **extra)
@@ -454,7 +454,8 @@ def micro(args):
     fams = H.kernel_families()
     run = {"gmres": lambda: H.cslp_gmres(lev, f), "vcycle": lambda: H.mg_vcycle(1, f),
            "apply": lambda: H.apply(f), "levelop": lambda: H.level_apply(lev, f, "M"),
-           "prolong": lambda: H.defl_prolong_residual(lev, vt, f)}[args.micro]
+           "prolong": lambda: H.defl_prolong_residual(lev, vt, f),
+           "restrict": lambda: H.defl_restrict(lev, f)}[args.micro]
     for _ in range(args.warmup):
         out = run()
     torch.cuda.synchronize()
