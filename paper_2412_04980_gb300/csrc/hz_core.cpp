@@ -1250,36 +1250,22 @@ int precond(Handle* h, int l, const void* v, int dv, void* xout, int nb) {
 }
 
 // One-iteration (F)GMRES cycle of a coarse level (levels 3..ml-1, and the coarsest level when it
-// is treated as negative definite) with every scalar step on the device: the same Arnoldi step
-// as cycle() with m = 1, no host round trip.  Iteration counts and breakdowns are collected at
-// the end of the solve.  r0 = L.b, solution L.x (zero on entry) += X_0 y.
+// is treated as negative definite) with every scalar step on the device.  With m = 1 the cycle's
+// result is the minimal-residual step x = (w^H b / w^H w) P b, w = A P b (Algorithm 1: v = b/||b||,
+// one Arnoldi step, y from the 2 x 1 least-squares problem); no host round trip.  Iteration counts
+// and breakdowns are collected at the end of the solve.  r0 = L.b, solution L.x (zero on entry).
 static int cycle_m1_device(Handle* h, Level& L, int nb, const std::function<int(const void*, void*)>& prec,
                            const std::function<int(const void*, void*)>& op) {
   Ctx& c = h->ctx;
   Scalars& sc = L.sc;
   const size_t n = L.n, bn = (size_t)nb * n;
-  const int nv = 1, ldA = 2 * nv + 1;
-  double* hA = sc.dev + sc.hA;
-  double* hB = hA + (size_t)nb * ldA;
-  double* n1 = hB + (size_t)nb * 2 * nv;
-  double* n2 = n1 + nb;
-  double* flag = n2 + nb;
-  double* beta = sc.dev + sc.nrm;
-  double* cs = sc.dev + sc.csc;
+  double* d = sc.dev + sc.hA;          // b^H w and ||w||^2, stride 3
   double* coef = sc.dev + sc.ccomb;
-  CK(launch_multidot(c, L.dvec, L.b, 0, 1, L.b, n, nb, hA, h->ws));
-  CK(launch_m1_begin(c, hA, nb, cs, beta, h->derr));
-  CK(launch_scale_dev(c, L.dvec, L.b, L.V, cs, 0, n, nb));
-  CS(prec(L.V, L.X));
-  CS(op(L.X, L.w));
-  const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
-  CK(launch_multidot(c, L.dvec, L.V, bn, nv, L.w, n, nb, hA, h->ws, 1));
-  CK(launch_update(c, L.dvec, L.V, bn, nv, hA, ldA, L.dvec, L.w, n, nb, n1, h->ws));
-  CK(launch_dgks_flag(c, hA + 2 * nv, ldA, n1, flag, nb, eta2));
-  CK(launch_multidot(c, L.dvec, L.V, bn, nv, L.w, n, nb, hB, h->ws, 0, flag));
-  CK(launch_update(c, L.dvec, L.V, bn, nv, hB, 2 * nv, L.dvec, L.w, n, nb, n2, h->ws, flag));
-  CK(launch_m1_finish(c, hA, ldA, hB, n1, n2, flag, beta, nb, coef, L.m1cnt, L.m1cnt + nb, h->derr));
-  CK(launch_combine(c, L.dx, L.X, bn, 1, coef, L.dvec, L.x, n, nb));
+  CS(prec(L.b, L.X));                                                     // X = P b
+  CS(op(L.X, L.w));                                                       // w = A X
+  CK(launch_multidot(c, L.dvec, L.b, 0, 1, L.w, n, nb, d, h->ws, 1));     // b^H w, ||w||^2
+  CK(launch_m1_mr(c, d, nb, coef, L.m1cnt, L.m1cnt + nb, h->derr));
+  CK(launch_combine(c, L.dx, L.X, bn, 1, coef, L.dvec, L.x, n, nb));      // x = coef X
   return HZ_OK;
 }
 

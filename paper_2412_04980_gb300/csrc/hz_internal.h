@@ -136,12 +136,10 @@ cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, co
                           void* w, size_t n, int nb, double* nrm2, void* ws, const double* skip = nullptr);
 // flag[b] = 1.0 when n1[b] >= eta2 * wn[b*ldw] (second Gram-Schmidt pass not needed), else 0.0
 cudaError_t launch_dgks_flag(Ctx& c, const double* wn, int ldw, const double* n1, double* flag, int nb, double eta2);
-// One-iteration FGMRES on the device: cs = 1 / ||r0|| (beta saved) and, after the Arnoldi step,
-// the least-squares coefficient y per right-hand side plus iteration / call counters.
-cudaError_t launch_m1_begin(Ctx& c, const double* nrm2, int nb, double* cs, double* beta, int* err);
-cudaError_t launch_m1_finish(Ctx& c, const double* hA, int ldA, const double* hB, const double* n1, const double* n2,
-                             const double* flag, const double* beta, int nb, double* coef, int* its, int* calls,
-                             int* err);
+// One-iteration FGMRES on the device as a minimal-residual step: from d = (b^H w, ||w||^2) per
+// right-hand side (stride 3), coef = conj(b^H w) / ||w||^2 (0 when w = 0), plus iteration / call
+// counters; a non-finite value sets *err.
+cudaError_t launch_m1_mr(Ctx& c, const double* d, int nb, double* coef, int* its, int* calls, int* err);
 // u^b (dtu) += sum_i coef[b*2nv + 2i..] X_i^b (dtx)
 cudaError_t launch_combine(Ctx& c, int dtx, const void* X, size_t ldx, int nv, const double* coef, int dtu, void* u,
                            size_t n, int nb);

@@ -192,70 +192,24 @@ __global__ void k_dgks(const double* __restrict__ wn, int ldw, const double* __r
   if (b < nb) flag[b] = (n1[b] >= eta2 * wn[(size_t)b * ldw]) ? 1.0 : 0.0;
 }
 
-// One-iteration FGMRES without a host round trip (levels whose cycle is exactly one iteration).
-// begin: beta_b = ||r0_b|| from the multidot output (||r0||^2 at nrm2[2 b]); cs_b = 1 / beta_b
-// (0 for a zero residual); a non-finite norm sets *err.
-__global__ void k_m1_begin(const double* __restrict__ nrm2, int nb, double* __restrict__ cs, double* __restrict__ beta,
-                           int* __restrict__ err) {
+// One-iteration FGMRES cycle as a minimal-residual step (Algorithm 1 with m = 1): with v = b / ||b||,
+// x = P v, w1 = A x, the least-squares coefficient is y = ||b|| conj(h11) / (|h11|^2 + h21^2) with
+// h11 = v^H w1 and |h11|^2 + h21^2 = ||w1||^2, so the cycle's result y P v equals
+// (w^H b / w^H w) P b with w = A P b.  d holds b^H w and ||w||^2 per right-hand side (stride 3).
+__global__ void k_m1_mr(const double* __restrict__ d, int nb, double* __restrict__ coef, int* __restrict__ its,
+                        int* __restrict__ calls, int* __restrict__ err) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
-  const double s = nrm2[2 * b];
-  double be = s > 0 ? sqrt(s) : 0.0;
-  if (!isfinite(be)) {
-    atomicExch(err, 1);
-    be = 0.0;
-  }
-  beta[b] = be;
-  cs[2 * b] = be > 0 ? 1.0 / be : 0.0;
-  cs[2 * b + 1] = 0.0;
-}
-
-// finish: the 2 x 1 Hessenberg column [h_00 (+ second-pass correction); ||w'||], one Givens
-// rotation, y = c beta / R_00 into coef[2 b] (0 for a zero residual); per-rhs iteration and call
-// counters; non-finite values set *err.
-__global__ void k_m1_finish(const double* __restrict__ hA, int ldA, const double* __restrict__ hB,
-                            const double* __restrict__ n1, const double* __restrict__ n2,
-                            const double* __restrict__ flag, const double* __restrict__ beta, int nb,
-                            double* __restrict__ coef, int* __restrict__ its, int* __restrict__ calls,
-                            int* __restrict__ err) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  const double be = beta[b];
+  const double hr = d[3 * b], hi = d[3 * b + 1], nw = d[3 * b + 2];
   coef[2 * b] = 0.0;
   coef[2 * b + 1] = 0.0;
-  if (!(be > 0)) return;
-  const bool second = flag[b] == 0.0;
-  const double ar = hA[(size_t)b * ldA] + (second ? hB[2 * b] : 0.0);
-  const double ai = hA[(size_t)b * ldA + 1] + (second ? hB[2 * b + 1] : 0.0);
-  const double nr = flag[b] != 0.0 ? n1[b] : n2[b];
-  const double hn = nr > 0 ? sqrt(nr) : 0.0;
-  const double aa = hypot(ar, ai);
-  const double t = sqrt((ar * ar + ai * ai) + hn * hn);
-  double c, sr, si;
-  if (t == 0) {
-    c = 1;
-    sr = si = 0;
-  } else if (aa == 0) {
-    c = 0;
-    sr = 1;
-    si = 0;
-  } else {
-    c = aa / t;
-    sr = (ar / aa) * hn / t;
-    si = (ai / aa) * hn / t;
-  }
-  const double Rr = c * ar + sr * hn, Ri = c * ai + si * hn;  // rotated R_00
-  const double est = hypot(sr, si) * be;
-  if (!isfinite(est) || !isfinite(hn)) {
+  if (!isfinite(hr) || !isfinite(hi) || !isfinite(nw)) {
     atomicExch(err, 1);
     return;
   }
-  const double g0 = c * be;
-  const double d = Rr * Rr + Ri * Ri;
-  if (d > 0) {
-    coef[2 * b] = g0 * Rr / d;
-    coef[2 * b + 1] = -g0 * Ri / d;
-  }
+  if (!(nw > 0)) return;  // b = 0 (or A P b = 0): nothing to add
+  coef[2 * b] = hr / nw;    // conj(b^H w) / ||w||^2
+  coef[2 * b + 1] = -hi / nw;
   its[b] += 1;
   calls[b] += 1;
 }
@@ -411,17 +365,9 @@ cudaError_t launch_dgks_flag(Ctx& c, const double* wn, int ldw, const double* n1
   return cudaGetLastError();
 }
 
-cudaError_t launch_m1_begin(Ctx& c, const double* nrm2, int nb, double* cs, double* beta, int* err) {
-  ProfScope ps(c, F_REDUCE, (double)nb * 40);
-  k_m1_begin<<<(nb + 127) / 128, 128, 0, c.s>>>(nrm2, nb, cs, beta, err);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_m1_finish(Ctx& c, const double* hA, int ldA, const double* hB, const double* n1, const double* n2,
-                             const double* flag, const double* beta, int nb, double* coef, int* its, int* calls,
-                             int* err) {
-  ProfScope ps(c, F_REDUCE, (double)nb * 96);
-  k_m1_finish<<<(nb + 127) / 128, 128, 0, c.s>>>(hA, ldA, hB, n1, n2, flag, beta, nb, coef, its, calls, err);
+cudaError_t launch_m1_mr(Ctx& c, const double* d, int nb, double* coef, int* its, int* calls, int* err) {
+  ProfScope ps(c, F_REDUCE, 0.0);
+  k_m1_mr<<<(nb + 127) / 128, 128, 0, c.s>>>(d, nb, coef, its, calls, err);
   return cudaGetLastError();
 }
 
