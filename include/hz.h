@@ -135,6 +135,12 @@ typedef struct {
                             tolerance cslp_tol and cap: HZ_CSLP_GMRES (default, Section 4.2) or
                             HZ_CSLP_BICGSTAB (the earlier multilevel work's choice, Sections 3.2
                             and 4.1) */
+  int sym_rows;          /* 1: solve the row-scaled system D A_h u = D b, D = 1/2 on Sommerfeld
+                            boundary edges and 1/4 at corners, whose matrix is the complex
+                            symmetric one Section 2.1 refers to (same solution u; the residuals
+                            and the stopping test are those of the scaled system; the
+                            preconditioner is built from A_h as usual); 0 (default): the
+                            ghost-eliminated rows as they are.  Sommerfeld grids only */
 } hz_config;
 
 /* Per-right-hand-side solve statistics. */
@@ -145,7 +151,8 @@ typedef struct {
   int level_calls[HZ_MAX_LEVELS];              /* [l-1]: number of level-l coarse solves */
   int cslp_gmres_iterations[HZ_MAX_LEVELS];    /* [l-1]: Krylov iterations of CSLP inverses
                                                   (GMRES, or Bi-CGSTAB with cslp_solver) */
-  double true_relres;                          /* ||b - A_h u|| / ||b|| in FP64 */
+  double true_relres;                          /* ||b - A_h u|| / ||b|| in FP64 (with sym_rows:
+                                                  ||D b - D A_h u|| / ||D b||) */
   double est_relres;                           /* last Arnoldi least-squares estimate */
   double ms;                                   /* wall time of the solve in milliseconds */
   int cslp_gmres_reorth[HZ_MAX_LEVELS];        /* [l-1]: second Gram-Schmidt passes of the
@@ -291,7 +298,7 @@ int hz_true_residual_noalloc(hz_handle h, const void* b, const void* u, int nrhs
 typedef struct hz_server_s* hz_server;
 
 typedef struct {
-  hz_grid grid;            /* finest grid, HZ_BC_SOMMERFELD */
+  hz_grid grid;            /* finest grid, HZ_BC_SOMMERFELD or HZ_BC_DIRICHLET (interior unknowns) */
   hz_config config;        /* solver configuration; config.max_rhs >= nrhs */
   const double* k_host;    /* nx*ny real FP64 wavenumbers, host; copied by hz_submit */
   const double* b_host;    /* nrhs*nx*ny HZ_C128 right-hand sides, host; copied by hz_submit */

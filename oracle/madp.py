@@ -55,7 +55,7 @@ import numpy as np
 
 from .krylov import bicgstab, fgmres, fgmres_restarted, gmres
 from .multigrid import CSLPMultigrid
-from .operators import DIRICHLET, SOMMERFELD, apply_level, apply_level_dirichlet
+from .operators import DIRICHLET, SOMMERFELD, apply_level, apply_level_dirichlet, scale_boundary_rows
 from .transfers import (coarse_size, coarse_size_dirichlet, deflation_prolong, deflation_prolong_dirichlet,
                         deflation_restrict, deflation_restrict_dirichlet, inject, inject_dirichlet)
 
@@ -83,6 +83,7 @@ class MADPConfig:
     level_tol: dict = field(default_factory=dict)   # level (3 .. ml-1) -> relative tolerance
     cslp_solver: str = "gmres"      # Krylov solver of the CSLP inverse beyond mg_max_level: gmres | bicgstab
     bc: str = SOMMERFELD            # "dirichlet": interior unknowns of a zero-boundary grid (MP-1a)
+    sym_rows: bool = False          # outer solve on D A_h u = D b (D: 1/2 on edges, 1/4 at corners)
 
 
 @dataclass
@@ -192,11 +193,16 @@ class Hierarchy:
         return u
 
     def solve(self, b, u0=None):
-        """Outer FGMRES(restart) on A_1 to relative residual tol (Section 4)."""
+        """Outer FGMRES(restart) on A_1 to relative residual tol (Section 4).  With ``sym_rows``
+        the outer operator and right-hand side are the row-scaled D A_1 and D b (the symmetric
+        form of the Sommerfeld system; the preconditioner is built from A as always)."""
         cfg = self.cfg
         self.stats = Stats()
-        u, its, rel, hist = fgmres_restarted(lambda x: self.A(1, x), b,
-                                             lambda v: self.precond(1, v),
+        if cfg.sym_rows:
+            op, rhs = (lambda x: scale_boundary_rows(self.A(1, x))), scale_boundary_rows(b)
+        else:
+            op, rhs = (lambda x: self.A(1, x)), b
+        u, its, rel, hist = fgmres_restarted(op, rhs, lambda v: self.precond(1, v),
                                              cfg.tol, cfg.restart, cfg.max_outer, u0)
         self.stats.outer_iterations = its
         self.stats.true_relres = rel

@@ -21,6 +21,9 @@ stencil sum with ghost points substituted, never an assembled matrix.
 * ``diag_5pt`` / ``diag_level``   the exact diagonal of those operators (the
                     ghost substitution feeds back into the diagonal).
 * ``jacobi``        one damped-Jacobi sweep u + omega * D^-1 (f - M u).
+* ``scale_boundary_rows``   the symmetric row scaling D (1/2 on boundary edges, 1/4 at corners)
+                    of the Sommerfeld system (pins: D A_h is complex symmetric; the scaled
+                    system has the same solution).
 
 Pins (tests/test_oracle_operators.py): closed-form Dirichlet eigenpairs, O(h^2)
 convergence of manufactured solutions with Dirichlet and Sommerfeld data,
@@ -205,6 +208,18 @@ def diag_level_dirichlet(k, level, h, shift=1.0):
     lap, kk = stencils_2d(level, h)
     R = lap.shape[0] // 2
     return lap[R, R] - shift * kk[R, R] * k * k + 0j
+
+
+def scale_boundary_rows(v):
+    """D v with D = 1/2 on the grid's boundary edges and 1/4 at its corners: the row scaling that
+    makes the ghost-eliminated Sommerfeld matrix complex symmetric (Section 2.1 calls the matrix
+    symmetric).  Applied to A_h u and to b it leaves the solution of A_h u = b unchanged."""
+    d = np.ones(v.shape[-2:])
+    d[:, 0] *= 0.5
+    d[:, -1] *= 0.5
+    d[0, :] *= 0.5
+    d[-1, :] *= 0.5
+    return d * v
 
 
 def jacobi(u, f, apply_m, diag, omega):

@@ -53,7 +53,7 @@ class HzConfig(ctypes.Structure):
         ("mg_nu2", ctypes.c_int), ("mg_coarsest_side", ctypes.c_int), ("max_rhs", ctypes.c_int),
         ("timeout_s", ctypes.c_double), ("device_gmres", ctypes.c_int), ("reorth_eta", ctypes.c_double),
         ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("cycle_m", ctypes.c_int),
-        ("level_tol", ctypes.c_double * HZ_MAX_LEVELS), ("cslp_solver", ctypes.c_int),
+        ("level_tol", ctypes.c_double * HZ_MAX_LEVELS), ("cslp_solver", ctypes.c_int), ("sym_rows", ctypes.c_int),
     ]
 
 
@@ -431,10 +431,10 @@ def _precision(cfg: dict) -> dict:
     return cfg
 
 
-def estimate_bytes(nx: int, ny: int, h: float, **cfg) -> int:
+def estimate_bytes(nx: int, ny: int, h: float, bc: int = HZ_BC_SOMMERFELD, **cfg) -> int:
     """hz_estimate_bytes: device bytes hz_setup allocates for this grid and configuration."""
     out = ctypes.c_size_t()
-    g = HzGrid(nx, ny, float(h), HZ_BC_SOMMERFELD)
+    g = HzGrid(nx, ny, float(h), bc)
     c = config(**_precision(dict(cfg)))
     _check(lib().hz_estimate_bytes(ctypes.byref(g), ctypes.byref(c), ctypes.byref(out)), "hz_estimate_bytes")
     return out.value
@@ -449,7 +449,7 @@ class Server:
         _check(lib().hz_server_create(int(budget_bytes), int(max_active), ctypes.byref(self._s)), "hz_server_create")
         self._live = {}
 
-    def submit(self, k_np, b_np, h: float, tol: float = 1e-6, **cfg) -> int:
+    def submit(self, k_np, b_np, h: float, tol: float = 1e-6, bc: str = "sommerfeld", **cfg) -> int:
         import numpy as np
         k = np.ascontiguousarray(k_np, dtype=np.float64)
         b = np.ascontiguousarray(b_np, dtype=np.complex128)
@@ -461,7 +461,8 @@ class Server:
         cfg.setdefault("max_rhs", nrhs)
         u = np.empty_like(b)
         stats = (HzStats * nrhs)()
-        req = HzRequest(HzGrid(nx, ny, float(h), HZ_BC_SOMMERFELD), config(**cfg), k.ctypes.data, b.ctypes.data,
+        grid = HzGrid(nx, ny, float(h), HZ_BC_SOMMERFELD if bc == "sommerfeld" else HZ_BC_DIRICHLET)
+        req = HzRequest(grid, config(**cfg), k.ctypes.data, b.ctypes.data,
                         u.ctypes.data, ctypes.addressof(stats), nrhs, float(tol))
         t = ctypes.c_uint64()
         _check(lib().hz_submit(self._s, ctypes.byref(req), ctypes.byref(t)), "hz_submit")

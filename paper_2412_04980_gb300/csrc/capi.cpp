@@ -92,6 +92,8 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (c.device_gmres < 0 || c.device_gmres > 4) return bad("device_gmres must be 0, 1, 2, 3 or 4");
   if (c.cycle_m < 1) return bad("cycle_m must be >= 1");
   if (c.cslp_solver != HZ_CSLP_GMRES && c.cslp_solver != HZ_CSLP_BICGSTAB) return bad("unknown cslp_solver");
+  if (c.sym_rows != 0 && c.sym_rows != 1) return bad("sym_rows must be 0 or 1");
+  if (c.sym_rows && g.bc != HZ_BC_SOMMERFELD) return bad("sym_rows scales Sommerfeld boundary rows (Sommerfeld grids only)");
   if (!(c.l2_tol >= 0 && c.l2_tol < 1)) return bad("l2_tol must be in [0, 1)");
   for (int l = 1; l <= HZ_MAX_LEVELS; ++l) {
     const double t = c.level_tol[l - 1];
@@ -146,6 +148,7 @@ int hz_apply(hz_handle hp, const void* x, void* y, int nrhs) {
   Level& L = H_->lv[0];
   OpDesc A = L.opA(C128);
   A.bc = H_->g.bc;
+  A.srow = H_->cfg.sym_rows;  // the handle's outer operator (row-scaled with sym_rows)
   return status_of(launch_level_op(H_->ctx, A, 0, C128, C128, C128, x, nullptr, y, 0.0, nrhs), "hz_apply");
 }
 

@@ -375,6 +375,7 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
   const int ml = cfg.levels, nb = cfg.max_rhs;
   const bool mixed = cfg.precision == HZ_PREC_MIXED;
   size_t total = 0, maxnv = 2;
+  if (cfg.sym_rows) total += (size_t)nb * g.nx * g.ny * 16;  // D b
   auto scal = [&](int cap) { return sizeof(double) * ((size_t)nb * 4 * (cap + 1) + 3 * (size_t)nb + 2 * (size_t)nb * (cap + 1)); };
   int nx = g.nx, ny = g.ny;
   for (int l = 1; l <= ml; ++l) {
@@ -605,6 +606,7 @@ int setup(Handle* h, const double* k_dev) {
   CS(dalloc(h, &h->ws, h->ws_bytes));
   CS(alloc_scalars(h, h->outer_sc, 1, nb));
   CS(dalloc(h, &h->rres, (size_t)nb * h->lv[0].n * 16));
+  if (cfg.sym_rows) CS(dalloc(h, &h->bscaled, (size_t)nb * h->lv[0].n * 16));
   {
     void* p;
     CS(dalloc(h, &p, sizeof(int)));
@@ -1311,6 +1313,11 @@ int solve(Handle* h, const void* b, void* u, int nb, double tol, unsigned flags)
     return HZ_OK;
   };
   OpDesc A = L.opA(C128);
+  if (cfg.sym_rows) {  // the row-scaled system D A u = D b (same u)
+    A.srow = 1;
+    CK(launch_row_scale(c, L.nx, L.ny, b, h->bscaled, nb));
+    b = h->bscaled;
+  }
   std::vector<double> bnorm, rel(nb, 0.0);
   CS(norms(b, bnorm));
   if (flags & HZ_SOLVE_INITIAL_GUESS) {

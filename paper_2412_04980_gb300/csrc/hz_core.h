@@ -100,6 +100,7 @@ struct Handle {
   std::vector<RhsStats> st;                  // per-rhs statistics of the running call
   Scalars outer_sc;                          // true-residual norms
   void* rres = nullptr;                      // level-1 true residual buffer (C128)
+  void* bscaled = nullptr;                   // sym_rows: D b, the right-hand side of the scaled system
   int* derr = nullptr;                       // device breakdown flag of the device-side cycles
   // CUDA graph of the coarse solve at level graph_level (every level from there down runs on the
   // device without host decisions), one per batch size; launches it replays, for the counter

@@ -66,6 +66,7 @@ struct OpP {
   int nx, ny;
   int R;            // stencil radius (also a template parameter of the kernels)
   int bc;           // 0 Sommerfeld, 1 Dirichlet
+  int srow;         // 1: boundary rows scaled by 1/2 per boundary side (symmetric form)
   T c;              // Laplacian scale
   T H;              // ghost spacing (2 H i k)
   T ks;             // wavenumber-stencil sum
@@ -274,7 +275,12 @@ __device__ __forceinline__ cx<T> tile_op(const TileView<T, R>& t, const OpP<T>& 
     const T dr = fma(-P.ksr, k2, T(4) * P.c);
     const T di = P.ksi * k2;
     const cx<T> u = *uc;
-    return mk<T>(fma(dr, u.re, fma(di, u.im, -P.c * s.re)), fma(dr, u.im, fma(-di, u.re, -P.c * s.im)));
+    cx<T> v = mk<T>(fma(dr, u.re, fma(di, u.im, -P.c * s.re)), fma(dr, u.im, fma(-di, u.re, -P.c * s.im)));
+    if (P.srow) {
+      const int g = bsides(P, gx, gy);
+      if (g) v = (g == 1 ? T(0.5) : T(0.25)) * v;
+    }
+    return v;
   } else {
     const int OX = t.OX;
     cx<T> lap = mk<T>(T(0), T(0)), kk = lap;

@@ -81,6 +81,7 @@ struct ProfScope {
 // Host description of one grid operator (see hzd::OpP).
 struct OpDesc {
   int nx = 0, ny = 0, R = 1, bc = 0;
+  int srow = 0;  // 1: Sommerfeld boundary rows scaled by 1/2 per boundary side (radius-1 rows)
   double c = 0, H = 0, ks = 1, sr = 1, si = 0;
   double m[7] = {}, l[7] = {};
   const double* k_d = nullptr;
@@ -122,6 +123,8 @@ cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, 
 cudaError_t launch_convert(Ctx& c, int tx, int ty, const void* x, void* y, size_t n);
 // y (ty) = x (tx) + z (tz)  (all n elements)
 cudaError_t launch_add(Ctx& c, int tx, const void* x, int tz, const void* z, int ty, void* y, size_t n);
+// y = D x for HZ_C128 vectors of an nx x ny grid: D = 1/2 on boundary edges, 1/4 at corners.
+cudaError_t launch_row_scale(Ctx& c, int nx, int ny, const void* x, void* y, int nb);
 
 // Batched Krylov kernels.  nb right-hand sides; vector i of rhs b lives at base + i*ldv + b*n
 // (elements), so a batch of one vector index is nb*n contiguous elements.

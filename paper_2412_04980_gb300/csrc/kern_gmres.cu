@@ -1506,6 +1506,7 @@ OpP<T> mkop(const hz::OpDesc& d) {
   p.ny = d.ny;
   p.R = d.R;
   p.bc = d.bc;
+  p.srow = d.srow;
   p.c = T(d.c);
   p.H = T(d.H);
   p.ks = T(d.ks);

@@ -29,6 +29,7 @@ OpP<T> make_op(const hz::OpDesc& d) {
   p.ny = d.ny;
   p.R = d.R;
   p.bc = d.bc;
+  p.srow = d.srow;
   p.c = T(d.c);
   p.H = T(d.H);
   p.ks = T(d.ks);

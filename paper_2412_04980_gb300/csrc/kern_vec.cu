@@ -6,6 +6,8 @@
 // and reduce across threads in FP64; FP64 vectors use FP64 throughout.
 #include <type_traits>
 
+#include <algorithm>
+
 #include "hz_device.cuh"
 #include "hz_internal.h"
 
@@ -214,6 +216,19 @@ __global__ void k_m1_mr(const double* __restrict__ d, int nb, double* __restrict
   calls[b] += 1;
 }
 
+// y = D x: boundary edges times 1/2, corners times 1/4 (the symmetric scaling of the Sommerfeld
+// rows), complex FP64, nb vectors of nx * ny.
+__global__ void __launch_bounds__(256) k_row_scale(const cx<double>* __restrict__ x, cx<double>* __restrict__ y,
+                                                   int nx, int ny) {
+  const size_t n = (size_t)nx * ny, off = (size_t)blockIdx.y * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int gy = (int)(i / nx), gx = (int)(i - (size_t)gy * nx);
+    const int g = (gx == 0) + (gx == nx - 1) + (gy == 0) + (gy == ny - 1);
+    const double s = g == 0 ? 1.0 : (g == 1 ? 0.5 : 0.25);
+    y[off + i] = s * x[off + i];
+  }
+}
+
 // u += sum_i coef_i X_i
 template <typename TX, typename TU>
 __global__ void __launch_bounds__(NT) k_combine(const cx<TX>* __restrict__ X, size_t ldx, int nv,
@@ -362,6 +377,15 @@ cudaError_t launch_update(Ctx& c, int dtv, const void* V, size_t ldv, int nv, co
 cudaError_t launch_dgks_flag(Ctx& c, const double* wn, int ldw, const double* n1, double* flag, int nb, double eta2) {
   ProfScope ps(c, F_REDUCE, (double)nb * 24);
   k_dgks<<<(nb + 127) / 128, 128, 0, c.s>>>(wn, ldw, n1, flag, nb, eta2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_scale(Ctx& c, int nx, int ny, const void* x, void* y, int nb) {
+  const size_t n = (size_t)nx * ny;
+  ProfScope ps(c, F_MISC, (double)nb * n * 32.0);
+  const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_row_scale<<<dim3(blocks, nb), 256, 0, c.s>>>(reinterpret_cast<const cx<double>*>(x), reinterpret_cast<cx<double>*>(y),
+                                                 nx, ny);
   return cudaGetLastError();
 }
 

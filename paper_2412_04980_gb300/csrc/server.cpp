@@ -200,8 +200,9 @@ int hz_submit(hz_server S, const hz_request* q, uint64_t* ticket) {
     set_error("hz_submit: null argument or nrhs < 1");
     return HZ_EINVAL;
   }
-  if (q->grid.bc != HZ_BC_SOMMERFELD || q->config.max_rhs < q->nrhs || !(q->tol > 0 && q->tol < 1)) {
-    set_error("hz_submit: Sommerfeld grid, config.max_rhs >= nrhs and tol in (0, 1) required");
+  if ((q->grid.bc != HZ_BC_SOMMERFELD && q->grid.bc != HZ_BC_DIRICHLET) || q->config.max_rhs < q->nrhs ||
+      !(q->tol > 0 && q->tol < 1)) {
+    set_error("hz_submit: known boundary type, config.max_rhs >= nrhs and tol in (0, 1) required");
     return HZ_EINVAL;
   }
   auto r = std::make_unique<Req>();

@@ -157,13 +157,18 @@ def test_config_validation_of_new_fields(L):
     h = ctypes.c_void_p()
     g = hz.HzGrid(9, 9, 0.1, 0)
     for bad in (dict(device_gmres=5), dict(device_gmres=-1), dict(autotune=2), dict(reorth_eta=1.5),
-                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1), dict(cslp_solver=2),
+                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1), dict(cslp_solver=2), dict(sym_rows=2),
                 dict(levels=3, level_tol={2: 0.1}), dict(levels=3, level_tol={3: 0.1}),
                 dict(levels=4, level_tol={3: 1.0}), dict(levels=4, level_tol={3: float("nan")})):
         c = hz.config(**bad)
         assert L.hz_setup(ctypes.byref(g), ctypes.c_void_p(1), ctypes.byref(c), None, ctypes.byref(h)) == hz.HZ_EINVAL
         msg = L.hz_last_error().decode()
         assert "coarsened" not in msg, (bad, msg)       # refused for the field itself
+    # the symmetric row scaling applies to Sommerfeld boundary rows only
+    c = hz.config(sym_rows=1)
+    gd = hz.HzGrid(9, 9, 0.1, 1)
+    assert L.hz_setup(ctypes.byref(gd), ctypes.c_void_p(1), ctypes.byref(c), None, ctypes.byref(h)) == hz.HZ_EINVAL
+    assert "Sommerfeld" in L.hz_last_error().decode()
 
 
 def test_dirichlet_grid_coarsening_rule(L):

@@ -135,3 +135,30 @@ def test_fp64_multi_rhs_deep_hierarchy(hz):
     H.close()
     assert all(s["status"] == 0 and s["true_relres"] <= 1e-6 for s in st)
     assert bool(np.isfinite(u.cpu().numpy()).all())
+
+
+def test_dirichlet_request_in_mix(hz):
+    """A homogeneous-Dirichlet MP-1a request (interior unknowns, 3 levels) served beside
+    Sommerfeld requests: each result equals the same solve alone, and the Dirichlet one solves
+    its system to the tolerance (true residual from the oracle's operator)."""
+    from oracle.operators import DIRICHLET
+    d = mp.mp1a(128, 20.0, levels=3)
+    est = hz.estimate_bytes(d.nx, d.ny, d.h, bc=1, levels=3, precision="mixed")
+    Hd = hz.Helmholtz(dev(d.k), d.h, bc="dirichlet", levels=3, precision="mixed")
+    got = Hd.memory_bytes()
+    ud0, sd0 = Hd.solve_host(d.b[0])
+    Hd.close()
+    assert got <= est <= 1.05 * got + (1 << 20)
+    cases = _mix()[:2]
+    alone = [_alone(hz, p, cfg) for p, cfg in cases]
+    srv = hz.Server(budget_bytes=8 << 30, max_active=3)
+    td = srv.submit(d.k, d.b[0], d.h, bc="dirichlet", levels=3, precision="mixed")
+    tickets = [srv.submit(p.k, p.b[0], p.h, **dict(cfg)) for p, cfg in cases]
+    ud, sd, _ = srv.wait(td, timeout_s=600)
+    assert np.array_equal(ud, ud0) and sd[0]["outer_iterations"] == sd0[0]["outer_iterations"]
+    r = d.b[0] - apply_helmholtz(ud, d.k, d.h, bc=DIRICHLET)
+    assert np.linalg.norm(r) / np.linalg.norm(d.b[0]) <= 1e-6
+    for t, (u0, st0) in zip(tickets, alone):
+        u, st, _ = srv.wait(t, timeout_s=600)
+        assert np.array_equal(u, u0)
+    srv.close()

@@ -190,3 +190,17 @@ def test_three_level_constant_k_table(beta2, paper_outer):
     u, st = Hierarchy(p.k, p.h, cfg).solve(p.b[0])
     assert st.true_relres <= 1e-6
     assert abs(st.outer_iterations - paper_outer) <= 1
+
+
+def test_sym_rows_solve_has_the_same_solution():
+    """The row-scaled (symmetric) outer system D A u = D b has the solution of A u = b: the
+    sym_rows solve reaches its own 1e-6 residual and agrees with the direct solve of the
+    unscaled system to within that residual's reach."""
+    from oracle.operators import scale_boundary_rows
+    p = mp.mp1b(32, 8.0)
+    ref = spla.spsolve(assemble(lambda u: apply_helmholtz(u, p.k, p.h), (p.ny, p.nx), 1).tocsc(),
+                       p.b[0].ravel()).reshape(p.ny, p.nx)
+    u, st = Hierarchy(p.k, p.h, MADPConfig(levels=2, sym_rows=True)).solve(p.b[0])
+    rs = scale_boundary_rows(p.b[0]) - scale_boundary_rows(apply_helmholtz(u, p.k, p.h))
+    assert np.linalg.norm(rs) / np.linalg.norm(scale_boundary_rows(p.b[0])) <= 1e-6
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= 1e-4

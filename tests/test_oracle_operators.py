@@ -7,7 +7,7 @@ import scipy.sparse.linalg as spla
 import model_problems as mp
 from helpers import assemble
 from oracle.operators import (DIRICHLET, SOMMERFELD, apply_5pt, apply_helmholtz, apply_level,
-                              diag_5pt, diag_level, jacobi)
+                              diag_5pt, diag_level, jacobi, scale_boundary_rows)
 from oracle.stencils import stencils_2d
 from oracle.transfers import inject, zt_1d
 
@@ -92,6 +92,9 @@ def test_sommerfeld_edge_scaled_matrix_is_symmetric():
     S = s.ravel()[:, None] * A
     assert np.max(np.abs(S - S.T)) <= 1e-12 * np.max(np.abs(S))
     assert np.max(np.abs(S.imag)) > 0
+    # the oracle's scale_boundary_rows (used by the sym_rows solve) is that scaling
+    Sd = assemble(lambda u: scale_boundary_rows(apply_helmholtz(u, k, h)), (n, n + 4), 1).toarray()
+    np.testing.assert_allclose(Sd, S, rtol=1e-15, atol=0)
 
 
 def test_level1_reduces_to_fine_operator():
