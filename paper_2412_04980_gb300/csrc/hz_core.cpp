@@ -617,6 +617,7 @@ int setup(Handle* h, const double* k_dev) {
   CS(noalloc_prepare(h));
   CK(cudaStreamSynchronize(h->ctx.s));
   if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_gmres(h));
+  if (cfg.autotune) CS(autotune_mg(h));
   // the first level >= 3 from which every level runs one-iteration device cycles and a device
   // CSLP inverse (multigrid or persistent GMRES): its coarse solve issues no host decision
   if (cfg.graphs) {
@@ -744,6 +745,22 @@ int autotune_gmres(Handle* h) {
     adopt(tx[best], ty[best]);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = {tx[best], ty[best]};
+  }
+  return HZ_OK;
+}
+
+// Band heights of the radius-1 multigrid sweeps, timed once per level shape and precision on the
+// handle's own multigrid buffers (their contents are rewritten by every V-cycle before use).
+int autotune_mg(Handle* h) {
+  for (auto& L : h->lv) {
+    const int nm = (int)L.mg.size();
+    for (int m = 0; m + 1 < nm; ++m) {
+      const MGLevel& q = L.mg[m];
+      if (q.op.R != 1 || mg_band_rows(0, q.op.nx, q.op.ny, L.dpre)) continue;
+      const void* f = m == 0 ? L.rt : q.f;
+      void* y = m == 0 ? L.t : q.e;
+      CK(tune_mg_bands(h->ctx, q.op, L.dpre, f, L.mg[m + 1].f, L.mg[m + 1].e, y, h->cfg.mg_omega, h->nbmax));
+    }
   }
   return HZ_OK;
 }

@@ -126,6 +126,8 @@ int setup(Handle* h, const double* k_dev);
 int noalloc_prepare(Handle* h);
 // Keep the faster persistent GMRES form per level (tile-owned or slice-distributed).
 int autotune_gmres(Handle* h);
+// Keep the fastest band height of the radius-1 multigrid sweeps per level shape (autotune).
+int autotune_mg(Handle* h);
 int gmres_grid_want(int nx, int ny);
 size_t estimate_bytes(const hz_grid& g, const hz_config& cfg);
 void destroy(Handle* h);

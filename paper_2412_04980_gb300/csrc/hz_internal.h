@@ -112,6 +112,13 @@ cudaError_t launch_mg_down(Ctx& c, const OpDesc& op, int dt, const void* f, void
 // up: u = omega f / D + P ec; y = u + omega (f - Op u) / D (+ add if add != null, add dtype tadd)
 cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const void* ec, void* y,
                          double omega, const void* add, int tadd, void* yout2, int tout2, int nrhs);
+// Band height (rows per warp) of the radius-1 strip sweeps: times both sweeps of a multigrid level
+// at every candidate on the given buffers (contents are overwritten) and keeps the fastest per
+// level shape and precision for the rest of the process; a no-op for other radii.
+cudaError_t tune_mg_bands(Ctx& c, const OpDesc& op, int dt, const void* f, void* fc, const void* ec, void* y,
+                          double omega, int nrhs);
+// The tuned band height of kind 0 (restriction) / 1 (prolongation) for a shape, 0 if never tuned.
+int mg_band_rows(int kind, int nx, int ny, int dt);
 // General multigrid pieces: fc = FW(r); u += P ec.
 cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs, int bc = 0);
 cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs, int bc = 0);

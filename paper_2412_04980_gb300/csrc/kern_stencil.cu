@@ -5,6 +5,9 @@
 // Every kernel is HBM-bound in FP32 and FP64-ALU-bound in FP64 on this part; inputs are
 // staged once per CTA in shared memory (tile + halo), outputs are written coalesced.
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "hz_device.cuh"
 #include "hz_internal.h"
@@ -969,15 +972,45 @@ static int band_rows(int strips, int rows, int nrhs, int maxrb) {
   return rb;
 }
 
+// Band heights of the strip sweeps chosen by timing (tune_mg_bands), per kernel, level shape and
+// precision, process-wide; shapes never timed take band_rows.
+std::mutex g_band_mu;
+std::map<std::tuple<int, int, int, int>, int> g_band;
+static int band_for(int kind, const OpDesc& d, int dt, int strips, int rows, int nrhs, int maxrb) {
+  {
+    std::lock_guard<std::mutex> lk(g_band_mu);
+    auto it = g_band.find(std::make_tuple(kind, d.nx, d.ny, dt));
+    if (it != g_band.end()) return it->second;
+  }
+  return band_rows(strips, rows, nrhs, maxrb);
+}
+
+template <typename T>
+static void down_r1_rb(cudaStream_t s, const OpDesc& d, const void* f, void* fc, double omega, int nrhs, int RB) {
+  const int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
+  const int strips = (ncx + 29) / 30;
+  dim3 grid((strips + 7) / 8, (ncy + RB - 1) / RB, nrhs);
+  k_mg_down_r1<T><<<grid, 256, 0, s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f), reinterpret_cast<cx<T>*>(fc),
+                                       ncx, ncy, T(omega), RB);
+}
+
+template <typename T>
+static void up_r1_rb(cudaStream_t s, const OpDesc& d, const void* f, const void* ec, void* y, double omega,
+                     const void* add, int nrhs, int RB) {
+  const int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
+  const int strips = (d.nx + d.bc + 59) / 60;
+  dim3 grid((strips + 7) / 8, (d.ny + RB - 1) / RB, nrhs);
+  k_mg_up_r1<T><<<grid, 256, 0, s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f),
+                                     reinterpret_cast<const cx<T>*>(ec), ncx, ncy, reinterpret_cast<cx<T>*>(y), T(omega),
+                                     reinterpret_cast<const cx<T>*>(add), RB);
+}
+
 template <typename T>
 static cudaError_t down_r1(Ctx& c, const OpDesc& d, const void* f, void* fc, double omega, int nrhs) {
   const int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
   ProfScope ps(c, F_MG_DOWN, (double)nrhs * ((double)d.n() * (sizeof(cx<T>) + sizeof(T)) + (double)ncx * ncy * sizeof(cx<T>)));
-  const int strips = (ncx + 29) / 30;
-  const int RB = band_rows(strips, ncy, nrhs, 16);
-  dim3 grid((strips + 7) / 8, (ncy + RB - 1) / RB, nrhs);
-  k_mg_down_r1<T><<<grid, 256, 0, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f), reinterpret_cast<cx<T>*>(fc),
-                                         ncx, ncy, T(omega), RB);
+  const int RB = band_for(0, d, sizeof(T) == 8 ? C128 : C64, (ncx + 29) / 30, ncy, nrhs, 16);
+  down_r1_rb<T>(c.s, d, f, fc, omega, nrhs, RB);
   return cudaGetLastError();
 }
 
@@ -987,12 +1020,54 @@ static cudaError_t up_r1(Ctx& c, const OpDesc& d, const void* f, const void* ec,
   const int ncx = coarse_n(d.nx, d.bc), ncy = coarse_n(d.ny, d.bc);
   double bytes = (double)nrhs * ((double)d.n() * (sizeof(cx<T>) * (add ? 3 : 2) + sizeof(T)) + (double)ncx * ncy * sizeof(cx<T>));
   ProfScope ps(c, F_MG_UP, bytes);
-  const int strips = (d.nx + d.bc + 59) / 60;
-  const int RB = band_rows(strips, d.ny, nrhs, 32);
-  dim3 grid((strips + 7) / 8, (d.ny + RB - 1) / RB, nrhs);
-  k_mg_up_r1<T><<<grid, 256, 0, c.s>>>(make_op<T>(d), reinterpret_cast<const cx<T>*>(f),
-                                       reinterpret_cast<const cx<T>*>(ec), ncx, ncy, reinterpret_cast<cx<T>*>(y),
-                                       T(omega), reinterpret_cast<const cx<T>*>(add), RB);
+  const int RB = band_for(1, d, sizeof(T) == 8 ? C128 : C64, (d.nx + d.bc + 59) / 60, d.ny, nrhs, 32);
+  up_r1_rb<T>(c.s, d, f, ec, y, omega, add, nrhs, RB);
+  return cudaGetLastError();
+}
+
+// Times both strip sweeps of one radius-1 multigrid level at every band height (twice, the
+// second run counts) on the given buffers and keeps the fastest for this shape and precision.
+template <typename T>
+static cudaError_t tune_bands_t(Ctx& c, const OpDesc& d, const void* f, void* fc, const void* ec, void* y,
+                                double omega, int nrhs) {
+  static const int cand[] = {2, 4, 8, 16, 32};
+  const int dt = sizeof(T) == 8 ? C128 : C64;
+  {
+    std::lock_guard<std::mutex> lk(g_band_mu);
+    if (g_band.count(std::make_tuple(0, d.nx, d.ny, dt)) && g_band.count(std::make_tuple(1, d.nx, d.ny, dt)))
+      return cudaSuccess;
+  }
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  int best[2] = {0, 0};
+  for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+    float tbest = 1e30f;
+    for (int rb : cand) {
+      float ms = 0;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, c.s);
+        if (kind == 0) down_r1_rb<T>(c.s, d, f, fc, omega, nrhs, rb);
+        else up_r1_rb<T>(c.s, d, f, ec, y, omega, nullptr, nrhs, rb);
+        cudaEventRecord(e1, c.s);
+        if ((e = cudaEventSynchronize(e1)) == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (e == cudaSuccess && ms < tbest) {
+        tbest = ms;
+        best[kind] = rb;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_band_mu);
+  g_band[std::make_tuple(0, d.nx, d.ny, dt)] = best[0];
+  g_band[std::make_tuple(1, d.nx, d.ny, dt)] = best[1];
   return cudaGetLastError();
 }
 
@@ -1056,6 +1131,19 @@ cudaError_t launch_mg_up(Ctx& c, const OpDesc& op, int dt, const void* f, const 
     if (op.R == 3) return up_r<float, 3>(c, op, f, ec, y, omega, add, nrhs);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t tune_mg_bands(Ctx& c, const OpDesc& op, int dt, const void* f, void* fc, const void* ec, void* y,
+                          double omega, int nrhs) {
+  if (op.R != 1) return cudaSuccess;  // only the radius-1 strip sweeps have a band shape
+  if (dt == C128) return tune_bands_t<double>(c, op, f, fc, ec, y, omega, nrhs);
+  return tune_bands_t<float>(c, op, f, fc, ec, y, omega, nrhs);
+}
+
+int mg_band_rows(int kind, int nx, int ny, int dt) {
+  std::lock_guard<std::mutex> lk(g_band_mu);
+  auto it = g_band.find(std::make_tuple(kind, nx, ny, dt));
+  return it == g_band.end() ? 0 : it->second;
 }
 
 cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, int nrhs, int bc) {

@@ -173,6 +173,24 @@ def test_mg_vcycle_fp32(hz):
     assert rel_inf(y, mg(f)) <= TOL32_COMPOSITE
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mg_band_autotune_is_bitwise_neutral(hz, precision):
+    """The set-up autotuner picks the band height of the radius-1 multigrid sweeps by timing; the
+    band only decides which warp computes a node, so V-cycles with the tuned bands (autotune = 1)
+    equal those with the default bands (autotune = 0) bit for bit, for 1 and 3 right-hand sides."""
+    ny, nx = 513, 769
+    k = mp.random_k(ny, nx, seed=31, kmin=5, kmax=60)
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
+    f = dev(mp.random_complex((3, ny, nx), seed=32), cdt)
+    out = []
+    for tune in (0, 1):
+        H = handle(hz, k, 1.0 / 512, levels=2, precision=precision, max_rhs=3, autotune=tune)
+        out.append((host(H.mg_vcycle(1, f)), host(H.mg_vcycle(1, f[1]))))
+        H.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[1][0][1], out[1][1])
+
+
 def test_mg_vcycle_general_path_matches(hz):
     """nu1 = nu2 = 1 through the general (unfused) kernels equals the fused path's oracle;
     nu1 = 2, nu2 = 1 matches the oracle with the same sweeps."""
