@@ -53,6 +53,9 @@ WORKLOADS = {
                  "centre source, 4-level MADP, tol 1e-6",
     "wedge_2049_64rhs": "2049x2049 square version of the synthetic wedge (1000 x 1000 m), k_max h = 0.3, 64 unit "
                         "point sources evenly spaced along the top row, 6-level MADP, tol 1e-6 per right-hand side",
+    "random_1025_16inst": "multi-instance batch: 16 independent 1025x1025 random-velocity models (seeds 100-115, "
+                          "k_max h from 0.2 to 0.3), one top-row point source each, 4-level MADP, all 16 in one "
+                          "batch (right-hand side r with its own wavenumber field r), tol 1e-6 each",
 }
 METRIC = "solves/s at a 1e-6 relative residual (time-to-solution = ms_per_step)"
 # Iteration counts of one solve of each workload at tol 1e-6, mixed precision, as the GPU
@@ -572,14 +575,16 @@ def serve(args):
 def batched(args, p):
     """Multi-source workload: every step solves all of the workload's right-hand sides, in
     lockstep sub-batches of --batch (each right-hand side keeps its own Krylov state and
-    stopping test); value = right-hand sides solved per second."""
+    stopping test); value = right-hand sides solved per second.  A multi-instance workload
+    (one wavenumber field per right-hand side) runs all its instances as one batch."""
     import torch
 
     import paper_2412_04980_gb300 as hz
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    B = args.batch
+    inst = p.k.ndim == 3
+    B = p.nrhs if inst else args.batch
     k = torch.from_numpy(p.k).to(dev)
     b_all = torch.from_numpy(p.b).to(dev)
     u_all = torch.empty_like(b_all)
@@ -588,6 +593,8 @@ def batched(args, p):
                      max_rhs=B)
     mem_gb = H.memory_bytes() / 1e9
     nr = p.nrhs
+    if inst:
+        assert H.cfg.per_rhs_k == 1
 
     def step():
         sts = []
@@ -635,11 +642,30 @@ def batched(args, p):
     H.close()
     del u_all
     torch.cuda.empty_cache()
+    alone = None
+    if inst:  # the first four instances one at a time, each on a handle of its own
+        nal = min(4, nr)
+        hs = [hz.Helmholtz(k[r].contiguous(), p.h, levels=p.levels, negdef_from_level=p.negdef_from_level,
+                           precision=args.precision) for r in range(nal)]
+        ua = torch.empty_like(b_all[0])
+        for r in range(nal):
+            hs[r].solve(b_all[r], ua, tol=1e-6)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(nal):
+            hs[r].solve(b_all[r], ua, tol=1e-6)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        alone = {"rhs_per_s": nal / (e0.elapsed_time(e1) / 1e3), "instances": nal,
+                 "ms_per_instance": e0.elapsed_time(e1) / nal}
+        for x in hs:
+            x.close()
+        torch.cuda.empty_cache()
     fp64 = None
     if not args.no_fp64:  # plain FP64 on one sub-batch of 8, scaled per right-hand side
         B64 = min(8, nr)
-        H64 = hz.Helmholtz(k, p.h, levels=p.levels, negdef_from_level=p.negdef_from_level, precision="fp64",
-                           max_rhs=B64)
+        H64 = hz.Helmholtz(k[:B64].contiguous() if inst else k, p.h, levels=p.levels,
+                           negdef_from_level=p.negdef_from_level, precision="fp64", max_rhs=B64)
         u64 = torch.empty_like(b_all[:B64])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -665,12 +691,14 @@ def batched(args, p):
         "dtype": "f32+f64 (FP32 preconditioner, FP64 outer FGMRES)" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nx": p.nx, "ny": p.ny,
-                   "levels": p.levels, "nrhs": nr, "batch": B, "precision": args.precision,
+                   "levels": p.levels, "nrhs": nr, "batch": B, "instances": nr if inst else 1,
+                   "precision": args.precision,
                    "workspace_gb": mem_gb},
         "outer_iterations": {"min": min(x["outer_iterations"] for x in stats),
                              "max": max(x["outer_iterations"] for x in stats)},
         "max_true_relres": max(x["true_relres"] for x in stats),
         "fp64_gpu": fp64,
+        "instances_one_at_a_time": alone,
         "e2e": {"value": nr / e2e_s, "unit": "rhs/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": int(launches),
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

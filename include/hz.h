@@ -141,6 +141,13 @@ typedef struct {
                             and the stopping test are those of the scaled system; the
                             preconditioner is built from A_h as usual); 0 (default): the
                             ghost-eliminated rows as they are.  Sommerfeld grids only */
+  int per_rhs_k;         /* 1: multi-instance batch.  k_dev of hz_setup holds max_rhs wavenumber
+                            fields, [max_rhs][ny][nx], and right-hand side b of every call
+                            solves (or applies) the problem with field b: same grid, spacing and
+                            configuration, but its own coarse wavenumbers, multigrid coarsest
+                            inverse and statistics, while every sweep stays one launch over the
+                            whole batch.  Calls then take nrhs <= max_rhs and use fields
+                            0 .. nrhs-1.  0 (default): one field shared by every right-hand side */
 } hz_config;
 
 /* Per-right-hand-side solve statistics. */
@@ -168,7 +175,8 @@ int hz_config_init(hz_config* cfg);
  * spacing 2^(l-1) h, wavenumber injected at coincident nodes, exact Galerkin coarse
  * stencils (Section 3.3, Appendix A; 1-D recursion with p = [1,4,6,4,1]/8), multigrid
  * sub-hierarchies with an FP64 dense coarsest inverse, and all workspace for nrhs <=
- * cfg->max_rhs.  k_dev: nx*ny real FP64 wavenumbers, device, read during the call only.
+ * cfg->max_rhs.  k_dev: nx*ny real FP64 wavenumbers (cfg->per_rhs_k: max_rhs such fields
+ * back to back), device, read during the call only.
  * stream: cudaStream_t used by every later call on the handle.
  * (Dirichlet grids: n_l = (n_{l-1} - 1) / 2, wavenumber injected at fine unknown 2I + 1.)
  * Errors: HZ_EINVAL (sizes not coarsenable, h <= 0, non-finite or non-positive k,
@@ -300,7 +308,8 @@ typedef struct hz_server_s* hz_server;
 typedef struct {
   hz_grid grid;            /* finest grid, HZ_BC_SOMMERFELD or HZ_BC_DIRICHLET (interior unknowns) */
   hz_config config;        /* solver configuration; config.max_rhs >= nrhs */
-  const double* k_host;    /* nx*ny real FP64 wavenumbers, host; copied by hz_submit */
+  const double* k_host;    /* nx*ny real FP64 wavenumbers (config.per_rhs_k: config.max_rhs
+                              fields back to back), host; copied by hz_submit */
   const double* b_host;    /* nrhs*nx*ny HZ_C128 right-hand sides, host; copied by hz_submit */
   double* u_host;          /* nrhs*nx*ny HZ_C128 solutions, host, caller-owned; written by the
                               server before the request is reported finished (zero initial guess) */

@@ -36,6 +36,7 @@ __all__ = [
     "wedge",
     "wedge_square",
     "random_field",
+    "random_instances",
     "point_source",
     "random_complex",
     "random_k",
@@ -51,7 +52,8 @@ class Problem:
     nx: int
     ny: int
     h: float
-    k: np.ndarray                  # (ny, nx) float64, k = 2*pi*f/c
+    k: np.ndarray                  # (ny, nx) float64, k = 2*pi*f/c; (nrhs, ny, nx) for a batch of
+                                   # instances, right-hand side r with field r
     b: np.ndarray                  # (nrhs, ny, nx) complex128
     levels: int
     negdef_from_level: int         # first level treated as negative definite (0 = none)
@@ -189,6 +191,24 @@ def random_field(n: int = 4097, h: float = 5.0, seed: int = 3, kh_max: float = 0
                    meta={"freq": freq, "seed": seed})
 
 
+def random_instances(n: int = 1025, count: int = 16, h: float = 5.0, levels: int = 4,
+                     negdef_from_level: int = 4, seed0: int = 100) -> Problem:
+    """``count`` independent random-velocity problems on one n x n grid (a multi-instance
+    batch): instance r draws its velocity model with seed seed0 + r, takes k_max h evenly from
+    0.2 to 0.3 and has one point source on the top row, moving from the centre to the right
+    with r; k has shape (count, n, n) and b (count, n, n)."""
+    ks, bs = [], []
+    for r in range(count):
+        c = random_velocity(n, h, seed0 + r)
+        kh = 0.2 + 0.1 * r / max(count - 1, 1)
+        freq = kh * float(c.min()) / (2.0 * math.pi * h)
+        ks.append(2.0 * math.pi * freq / c)
+        i = (n - 1) // 2 + r * ((n - 1) // 2) // max(count, 1)
+        bs.append(point_source(n, n, i, n - 1, h))
+    return Problem("random_instances", n, n, h, np.stack(ks), np.stack(bs), levels=levels,
+                   negdef_from_level=negdef_from_level, meta={"instances": count, "seed0": seed0})
+
+
 def random_complex(shape, seed: int) -> np.ndarray:
     """Complex128 array with independent standard-normal real and imaginary parts."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -215,6 +235,8 @@ def named(name: str) -> Problem:
         return random_field(513, 5.0, seed=3, levels=3, negdef_from_level=4)
     if name == "wedge_2049_64rhs":
         return wedge_square(2049, 64)
+    if name == "random_1025_16inst":
+        return random_instances(1025, 16, levels=4, negdef_from_level=4)
     if name == "mp1a_1023":
         # MP-1a at k h = 0.3125 (Section 4.3.1's resolution): k = 320 on 1023^2 interior unknowns;
         # levels 1023, 511, 255, 127, the fourth negative definite at this k h

@@ -54,6 +54,7 @@ class HzConfig(ctypes.Structure):
         ("timeout_s", ctypes.c_double), ("device_gmres", ctypes.c_int), ("reorth_eta", ctypes.c_double),
         ("graphs", ctypes.c_int), ("autotune", ctypes.c_int), ("cycle_m", ctypes.c_int),
         ("level_tol", ctypes.c_double * HZ_MAX_LEVELS), ("cslp_solver", ctypes.c_int), ("sym_rows", ctypes.c_int),
+        ("per_rhs_k", ctypes.c_int),
     ]
 
 
@@ -207,15 +208,22 @@ class SolveResult:
 class Helmholtz:
     """One Helmholtz instance (grid, wavenumber field, configuration) on the current device.
 
-    ``k`` is a real float64 CUDA tensor of shape (ny, nx).  Keyword arguments set
-    :class:`HzConfig` fields (``levels``, ``precision`` ('fp64' / 'mixed'), ``max_rhs`` ...).
+    ``k`` is a real float64 CUDA tensor of shape (ny, nx), or (I, ny, nx) for a multi-instance
+    batch: I problems on the same grid, right-hand side r of every call taking field r
+    (``per_rhs_k``; ``max_rhs`` becomes I).  Keyword arguments set :class:`HzConfig` fields
+    (``levels``, ``precision`` ('fp64' / 'mixed'), ``max_rhs`` ...).
     """
 
     def __init__(self, k, h: float, bc: str = "sommerfeld", stream=None, **cfg):
         import torch
-        if not (k.is_cuda and k.dtype == torch.float64 and k.dim() == 2 and k.is_contiguous()):
-            raise ValueError("k must be a contiguous 2-D float64 CUDA tensor")
-        self.ny, self.nx = int(k.shape[0]), int(k.shape[1])
+        if not (k.is_cuda and k.dtype == torch.float64 and k.dim() in (2, 3) and k.is_contiguous()):
+            raise ValueError("k must be a contiguous (ny, nx) or (instances, ny, nx) float64 CUDA tensor")
+        self.ny, self.nx = int(k.shape[-2]), int(k.shape[-1])
+        if k.dim() == 3:
+            if cfg.get("max_rhs", k.shape[0]) != k.shape[0]:
+                raise ValueError("a multi-instance batch takes max_rhs = number of wavenumber fields")
+            cfg["max_rhs"] = int(k.shape[0])
+            cfg["per_rhs_k"] = 1
         prec = cfg.pop("precision", "fp64")
         cfg["precision"] = {"fp64": HZ_PREC_FP64, "mixed": HZ_PREC_MIXED}.get(prec, prec)
         self.cfg = config(**cfg)
@@ -453,11 +461,16 @@ class Server:
         import numpy as np
         k = np.ascontiguousarray(k_np, dtype=np.float64)
         b = np.ascontiguousarray(b_np, dtype=np.complex128)
-        ny, nx = k.shape
+        ny, nx = k.shape[-2:]
         nrhs = 1 if b.ndim == 2 else b.shape[0]
         if b.shape[-2:] != (ny, nx):
-            raise ValueError("b must have k's shape (optionally with a leading rhs axis)")
+            raise ValueError("b must have k's grid shape (optionally with a leading rhs axis)")
         cfg = _precision(dict(cfg))
+        if k.ndim == 3:  # multi-instance request: right-hand side r takes wavenumber field r
+            if nrhs > k.shape[0] or cfg.get("max_rhs", k.shape[0]) != k.shape[0]:
+                raise ValueError("a multi-instance request takes max_rhs = fields >= nrhs")
+            cfg["max_rhs"] = int(k.shape[0])
+            cfg["per_rhs_k"] = 1
         cfg.setdefault("max_rhs", nrhs)
         u = np.empty_like(b)
         stats = (HzStats * nrhs)()

@@ -36,6 +36,8 @@ static int check_dtype(int dt) { return (dt == HZ_C128 || dt == HZ_C64) ? HZ_OK 
 static int check_nrhs(Handle* H, int nrhs, bool workspace) {
   if (nrhs < 1) return bad("nrhs must be >= 1");
   if (workspace && nrhs > H->nbmax) return bad("nrhs exceeds the handle's max_rhs");
+  if (H->cfg.per_rhs_k && nrhs > H->nbmax)
+    return bad("with per_rhs_k every right-hand side needs its own wavenumber field: nrhs <= max_rhs");
   return HZ_OK;
 }
 
@@ -93,6 +95,7 @@ int hz_setup(const hz_grid* grid, const double* k_dev, const hz_config* cfg, voi
   if (c.cycle_m < 1) return bad("cycle_m must be >= 1");
   if (c.cslp_solver != HZ_CSLP_GMRES && c.cslp_solver != HZ_CSLP_BICGSTAB) return bad("unknown cslp_solver");
   if (c.sym_rows != 0 && c.sym_rows != 1) return bad("sym_rows must be 0 or 1");
+  if (c.per_rhs_k != 0 && c.per_rhs_k != 1) return bad("per_rhs_k must be 0 or 1");
   if (c.sym_rows && g.bc != HZ_BC_SOMMERFELD) return bad("sym_rows scales Sommerfeld boundary rows (Sommerfeld grids only)");
   if (!(c.l2_tol >= 0 && c.l2_tol < 1)) return bad("l2_tol must be in [0, 1)");
   for (int l = 1; l <= HZ_MAX_LEVELS; ++l) {

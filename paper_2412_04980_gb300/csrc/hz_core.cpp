@@ -198,8 +198,21 @@ OpDesc Level::opA(int dt) const {
   }
   d.k_d = k_d;
   d.k_f = k_f;
+  d.kstride = kstride;
   (void)dt;
   return d;
+}
+
+// The operator of right-hand side q alone (its own wavenumber field), for launches on one
+// right-hand side.
+static OpDesc op_of_rhs(const OpDesc& d, int q) {
+  OpDesc o = d;
+  if (d.kstride) {
+    o.k_d += (size_t)q * d.kstride;
+    o.k_f += (size_t)q * d.kstride;
+    o.kstride = 0;
+  }
+  return o;
 }
 OpDesc Level::opM(int dt, double b1, double b2) const {
   OpDesc d = opA(dt);
@@ -269,8 +282,10 @@ static bool invert(std::vector<cd>& A, int n) {
 }
 
 // Dense inverse of a grid operator: columns from the FP64 level kernel applied to unit vectors.
-static int dense_inverse(Handle* h, const OpDesc& op, double** inv_out) {
-  const int N = (int)op.n();
+// With per-right-hand-side wavenumbers (op.kstride != 0) one inverse per field, `ninst` of them
+// back to back.
+static int dense_inverse(Handle* h, const OpDesc& op_all, int ninst, double** inv_out) {
+  const int N = (int)op_all.n();
   if (N > 2048) {
     set_error("multigrid coarsest grid has " + std::to_string(N) + " unknowns (limit 2048)");
     return HZ_ENOTSUP;
@@ -282,29 +297,31 @@ static int dense_inverse(Handle* h, const OpDesc& op, double** inv_out) {
     cudaFree(E);
     return status_of(cudaErrorMemoryAllocation, "dense_inverse");
   }
-  std::vector<cd> hostE((size_t)N * N, 0.0);
-  for (int i = 0; i < N; ++i) hostE[(size_t)i * N + i] = 1.0;
-  int st = HZ_OK;
-  cudaError_t e = cudaMemcpyAsync(E, hostE.data(), bytes, cudaMemcpyHostToDevice, h->ctx.s);
-  if (e == cudaSuccess) e = launch_level_op(h->ctx, op, 0, C128, C128, C128, E, nullptr, Y, 0.0, N);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hostE.data(), Y, bytes, cudaMemcpyDeviceToHost, h->ctx.s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->ctx.s);
+  void* p = nullptr;
+  int st = dalloc(h, &p, bytes * (op_all.kstride ? ninst : 1));
+  std::vector<cd> unit((size_t)N * N, 0.0), cols((size_t)N * N), A((size_t)N * N);
+  for (int i = 0; i < N; ++i) unit[(size_t)i * N + i] = 1.0;
+  cudaError_t e = cudaMemcpyAsync(E, unit.data(), bytes, cudaMemcpyHostToDevice, h->ctx.s);
+  for (int q = 0; q < (op_all.kstride ? ninst : 1) && st == HZ_OK && e == cudaSuccess; ++q) {
+    e = launch_level_op(h->ctx, op_of_rhs(op_all, q), 0, C128, C128, C128, E, nullptr, Y, 0.0, N);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cols.data(), Y, bytes, cudaMemcpyDeviceToHost, h->ctx.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->ctx.s);
+    if (e != cudaSuccess) break;
+    for (int c = 0; c < N; ++c)
+      for (int r = 0; r < N; ++r) A[(size_t)r * N + c] = cols[(size_t)c * N + r];
+    if (!invert(A, N)) {
+      set_error("singular multigrid coarsest operator");
+      st = HZ_EBREAKDOWN;
+      break;
+    }
+    e = cudaMemcpyAsync((char*)p + (size_t)q * bytes, A.data(), bytes, cudaMemcpyHostToDevice, h->ctx.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->ctx.s);
+  }
   cudaFree(E);
   cudaFree(Y);
   if (e != cudaSuccess) return status_of(e, "dense_inverse");
-  std::vector<cd> A((size_t)N * N);
-  for (int c = 0; c < N; ++c)
-    for (int r = 0; r < N; ++r) A[(size_t)r * N + c] = hostE[(size_t)c * N + r];
-  if (!invert(A, N)) {
-    set_error("singular multigrid coarsest operator");
-    return HZ_EBREAKDOWN;
-  }
-  void* p;
-  CS(dalloc(h, &p, bytes));
-  CK(cudaMemcpyAsync(p, A.data(), bytes, cudaMemcpyHostToDevice, h->ctx.s));
-  CK(cudaStreamSynchronize(h->ctx.s));
+  if (st) return st;
   *inv_out = reinterpret_cast<double*>(p);
-  (void)st;
   return HZ_OK;
 }
 
@@ -334,12 +351,17 @@ static bool mg_coarsens(int mx, int my, int coarsest_side, int bc) {
   return std::min(mx, my) >= (bc == HZ_BC_DIRICHLET ? 3 : 5);
 }
 
-// Wavenumbers of the next coarser grid: injection at the coincident nodes.
-static std::vector<double> inject(const std::vector<double>& k, int nx, int ny, int bc) {
+// Wavenumbers of the next coarser grid: injection at the coincident nodes, for each of the
+// `nf` fields stored back to back.
+static std::vector<double> inject(const std::vector<double>& k, int nx, int ny, int bc, int nf = 1) {
   const int cx = coarse_side(nx, bc), cy = coarse_side(ny, bc), o = bc == HZ_BC_DIRICHLET ? 1 : 0;
-  std::vector<double> out((size_t)cx * cy);
-  for (int j = 0; j < cy; ++j)
-    for (int i = 0; i < cx; ++i) out[(size_t)j * cx + i] = k[(size_t)(2 * j + o) * nx + 2 * i + o];
+  std::vector<double> out((size_t)nf * cx * cy);
+  for (int f = 0; f < nf; ++f) {
+    const double* kf = k.data() + (size_t)f * nx * ny;
+    double* of = out.data() + (size_t)f * cx * cy;
+    for (int j = 0; j < cy; ++j)
+      for (int i = 0; i < cx; ++i) of[(size_t)j * cx + i] = kf[(size_t)(2 * j + o) * nx + 2 * i + o];
+  }
   return out;
 }
 
@@ -373,6 +395,7 @@ int gmres_grid_want(int nx, int ny) {
 // cooperative grid is taken at its largest), used for admission against a memory budget.
 size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
   const int ml = cfg.levels, nb = cfg.max_rhs;
+  const size_t nf = cfg.per_rhs_k ? (size_t)nb : 1;  // wavenumber fields
   const bool mixed = cfg.precision == HZ_PREC_MIXED;
   size_t total = 0, maxnv = 2;
   if (cfg.sym_rows) total += (size_t)nb * g.nx * g.ny * 16;  // D b
@@ -381,7 +404,7 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
   for (int l = 1; l <= ml; ++l) {
     const size_t n = (size_t)nx * ny, bn = (size_t)nb * n;
     const size_t eb = (l == 1 || !mixed) ? 16 : 8, ep = mixed ? 8 : 16, ex = ep;
-    total += n * 12;  // k in FP64 and FP32
+    total += n * 12 * nf;  // k in FP64 and FP32 (per field)
     int cap;
     double tol_unused;
     level_schedule(cfg, l, n, &tol_unused, &cap);
@@ -397,10 +420,10 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
         mx = coarse_side(mx, g.bc);
         my = coarse_side(my, g.bc);
         const size_t m = (size_t)mx * my;
-        total += m * 12 + 2 * (size_t)nb * m * ep + (general ? 2 * (size_t)nb * m * ep : 0);
+        total += m * 12 * nf + 2 * (size_t)nb * m * ep + (general ? 2 * (size_t)nb * m * ep : 0);
       }
       const size_t nc = (size_t)mx * my;
-      total += nc * nc * 16;
+      total += nc * nc * 16 * nf;
     } else {
       const int capg = std::max(1, krylov_cap(cfg.c_it, n));
       maxnv = std::max(maxnv, (size_t)capg + 1);
@@ -438,8 +461,9 @@ int setup(Handle* h, const double* k_dev) {
   const int nb = h->nbmax;
   const bool mixed = cfg.precision == HZ_PREC_MIXED;
   CK(cudaGetDevice(&h->device));
-  // host copy of k, validated
-  std::vector<double> k((size_t)g.nx * g.ny);
+  // host copy of k (one field, or one per right-hand side), validated
+  const int nf = cfg.per_rhs_k ? nb : 1;
+  std::vector<double> k((size_t)nf * g.nx * g.ny);
   CK(cudaMemcpy(k.data(), k_dev, k.size() * 8, cudaMemcpyDeviceToHost));
   for (double v : k)
     if (!(std::isfinite(v) && v > 0)) {
@@ -460,6 +484,7 @@ int setup(Handle* h, const double* k_dev) {
     L.ks = std::ldexp(1.0, 2 * (l - 1));
     galerkin_masks(l, &L.R, L.m, L.L);
     CS(upload_k(h, kl, &L.k_d, &L.k_f));
+    L.kstride = cfg.per_rhs_k ? L.n : 0;
     if (l == 1) {
       L.dvec = C128;
       L.dpre = mixed ? C64 : C128;
@@ -468,7 +493,7 @@ int setup(Handle* h, const double* k_dev) {
       L.dvec = L.dpre = L.dx = mixed ? C64 : C128;
     }
     if (l < ml) {
-      kl = inject(kl, nx, ny, g.bc);
+      kl = inject(kl, nx, ny, g.bc, nf);
       nx = coarse_side(nx, g.bc);
       ny = coarse_side(ny, g.bc);
     }
@@ -503,13 +528,12 @@ int setup(Handle* h, const double* k_dev) {
       MGLevel m0;
       m0.op = L.opM(L.dpre, cfg.beta1, cfg.beta2);
       L.mg.push_back(m0);
-      std::vector<double> km = kl;  // placeholder, recomputed below
       // wavenumber of this level on the host again (inject from fine k)
-      km = k;
+      std::vector<double> km = k;
       {
         int fx = g.nx, fy = g.ny;
         for (int q = 1; q < l; ++q) {
-          km = inject(km, fx, fy, g.bc);
+          km = inject(km, fx, fy, g.bc, nf);
           fx = coarse_side(fx, g.bc);
           fy = coarse_side(fy, g.bc);
         }
@@ -519,7 +543,7 @@ int setup(Handle* h, const double* k_dev) {
       const bool general = !(cfg.mg_nu1 == 1 && cfg.mg_nu2 == 1);
       for (;;) {
         if (!mg_coarsens(mx, my, cfg.mg_coarsest_side, g.bc)) break;
-        km = inject(km, mx, my, g.bc);
+        km = inject(km, mx, my, g.bc, nf);
         mx = coarse_side(mx, g.bc);
         my = coarse_side(my, g.bc);
         Hm *= 2.0;
@@ -538,6 +562,7 @@ int setup(Handle* h, const double* k_dev) {
         CS(upload_k(h, km, &kd, &kf));
         q.op.k_d = kd;
         q.op.k_f = kf;
+        q.op.kstride = cfg.per_rhs_k ? (size_t)mx * my : 0;
         CS(dalloc(h, &q.f, (size_t)nb * mx * my * ep));
         CS(dalloc(h, &q.e, (size_t)nb * mx * my * ep));
         L.mg.push_back(q);
@@ -549,7 +574,8 @@ int setup(Handle* h, const double* k_dev) {
         }
       OpDesc last = L.mg.back().op;
       L.ninv = (int)last.n();
-      CS(dense_inverse(h, last, &L.inv));
+      L.invstride = last.kstride ? (size_t)L.ninv * L.ninv : 0;
+      CS(dense_inverse(h, last, nf, &L.inv));
     } else {
       L.capg = std::max(1, krylov_cap(cfg.c_it, L.n));
       maxnv = std::max(maxnv, (size_t)L.capg + 1);
@@ -688,7 +714,7 @@ int autotune_gmres(Handle* h) {
       CK(cudaMemcpyAsync(L.t, hb.data(), L.n * eb, cudaMemcpyHostToDevice, h->ctx.s));
       CK(cudaStreamSynchronize(h->ctx.s));
     }
-    OpDesc M = L.opM(L.dpre, h->cfg.beta1, h->cfg.beta2);
+    OpDesc M = op_of_rhs(L.opM(L.dpre, h->cfg.beta1, h->cfg.beta2), 0);
     const int K = std::min(L.capg, 24);
     const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
     // candidates: every fitting tile shape (at most as many tiles as the setup's default, whose
@@ -796,10 +822,10 @@ int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, 
   const size_t eb = elem_bytes(dt);
   if (nm == 1) {  // the level itself is the coarsest: exact dense solve
     if (add) {
-      CK(launch_dense(c, L.inv, L.ninv, dt, f, L.r, nb));
+      CK(launch_dense(c, L.inv, L.ninv, dt, f, L.r, nb, L.invstride));
       CK(launch_add(c, dt, L.r, dt, add, dt, out, (size_t)nb * L.n));
     } else {
-      CK(launch_dense(c, L.inv, L.ninv, dt, f, out, nb));
+      CK(launch_dense(c, L.inv, L.ninv, dt, f, out, nb, L.invstride));
     }
     return HZ_OK;
   }
@@ -809,7 +835,7 @@ int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, 
       CK(launch_mg_down(c, L.mg[m].op, dt, fm, L.mg[m + 1].f, om, nb));
       fm = L.mg[m + 1].f;
     }
-    CK(launch_dense(c, L.inv, L.ninv, dt, L.mg[nm - 1].f, L.mg[nm - 1].e, nb));
+    CK(launch_dense(c, L.inv, L.ninv, dt, L.mg[nm - 1].f, L.mg[nm - 1].e, nb, L.invstride));
     for (int m = nm - 2; m >= 0; --m) {
       const void* fmm = (m == 0) ? f : L.mg[m].f;
       void* y = (m == 0) ? out : L.mg[m].e;
@@ -822,7 +848,7 @@ int vcycle(Handle* h, int l, int dt, const void* f, void* out, const void* add, 
     MGLevel& q = L.mg[m];
     const size_t nn = (size_t)nb * q.op.n();
     if (m == nm - 1) {
-      CK(launch_dense(c, L.inv, L.ninv, dt, fm, um, nb));
+      CK(launch_dense(c, L.inv, L.ninv, dt, fm, um, nb, L.invstride));
       return HZ_OK;
     }
     void* a = um;
@@ -1103,12 +1129,12 @@ int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
                                  L.capg, h->cfg.cslp_tol, L.gcl, true, nb, eta2));
     } else if (L.gtiles > 0) {  // tile-owned form, one cooperative launch per right-hand side
       for (int q = 0; q < nb; ++q)
-        CK(launch_gmres_tile(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb, (char*)x + (size_t)q * L.n * eb,
+        CK(launch_gmres_tile(h->ctx, op_of_rhs(M, q), dt, (const char*)b + (size_t)q * L.n * eb, (char*)x + (size_t)q * L.n * eb,
                              L.Vg, L.wg, L.gflag, L.gpartA, L.gpartB, L.gR, L.gst + q, L.capg, h->cfg.cslp_tol,
                              L.gtx, L.gty, eta2));
     } else {  // one cooperative launch per right-hand side
       for (int q = 0; q < nb; ++q)
-        CK(launch_gmres_persistent(h->ctx, M, dt, (const char*)b + (size_t)q * L.n * eb,
+        CK(launch_gmres_persistent(h->ctx, op_of_rhs(M, q), dt, (const char*)b + (size_t)q * L.n * eb,
                                    (char*)x + (size_t)q * L.n * eb, L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride,
                                    L.gR, L.gst + q, L.capg, h->cfg.cslp_tol, L.ggrid, false, 1, eta2));
     }

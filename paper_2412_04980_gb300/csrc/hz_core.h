@@ -35,11 +35,13 @@ struct Level {
   double m[7] = {}, L[7] = {};
   double* k_d = nullptr;
   float* k_f = nullptr;
+  size_t kstride = 0;                        // per_rhs_k: n (field of rhs b at k + b n), else 0
   int dvec = C128, dpre = C128, dx = C128;   // basis, preconditioner temporaries, stored x_j
   // multigrid CSLP (l <= mg_max_level)
   std::vector<MGLevel> mg;
   double* inv = nullptr;                     // dense FP64 inverse of the coarsest MG operator
   int ninv = 0;
+  size_t invstride = 0;                      // per_rhs_k: one inverse per field, ninv^2 apart
   // deflated / CSLP FGMRES of this level
   int cap = 0;                               // iteration cap per cycle
   double tol = 0.0;                          // relative tolerance of a coarse solve (0 = exactly cap iterations)

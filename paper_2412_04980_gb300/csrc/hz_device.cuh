@@ -74,6 +74,8 @@ struct OpP {
   T ksr, ksi;       // ks * sigma
   T m[7], l[7];     // 1-D masks, index d + R (R >= 2)
   const T* k;       // wavenumber, nx*ny
+  size_t kstride;   // elements between the wavenumber fields of consecutive right-hand sides
+                    // (0: one field shared by the batch); kernels offset k by their rhs index
 };
 
 // Physical boundary sides a node touches.  Dirichlet grids hold interior unknowns only, so

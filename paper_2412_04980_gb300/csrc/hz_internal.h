@@ -78,7 +78,8 @@ struct ProfScope {
   ~ProfScope();
 };
 
-// Host description of one grid operator (see hzd::OpP).
+// Host description of one grid operator (see hzd::OpP).  With kstride != 0 right-hand side b
+// of a launch takes the wavenumber field k + b kstride (multi-instance batches).
 struct OpDesc {
   int nx = 0, ny = 0, R = 1, bc = 0;
   int srow = 0;  // 1: Sommerfeld boundary rows scaled by 1/2 per boundary side (radius-1 rows)
@@ -86,6 +87,7 @@ struct OpDesc {
   double m[7] = {}, l[7] = {};
   const double* k_d = nullptr;
   const float* k_f = nullptr;
+  size_t kstride = 0;  // nodes between the wavenumber fields of consecutive right-hand sides (0: shared)
   size_t n() const { return (size_t)nx * ny; }
 };
 
@@ -124,8 +126,10 @@ cudaError_t launch_fw(Ctx& c, int dt, int nx, int ny, const void* r, void* rc, i
 cudaError_t launch_prolong_add(Ctx& c, int dt, int nx, int ny, const void* ec, void* u, int nrhs, int bc = 0);
 
 // ---- vector launchers (kern_vec.cu) -------------------------------------------------
-// Dense FP64 complex matvec y = A x with dtype conversions (coarsest multigrid solve).
-cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, void* y, int nrhs);
+// Dense FP64 complex matvec y = A x with dtype conversions (coarsest multigrid solve); right-hand
+// side b takes the matrix A + b astride complex elements (astride 0: one matrix for the batch).
+cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, void* y, int nrhs,
+                         size_t astride = 0);
 // Convert between dtypes: y (ty) = x (tx), n complex elements.
 cudaError_t launch_convert(Ctx& c, int tx, int ty, const void* x, void* y, size_t n);
 // y (ty) = x (tx) + z (tz)  (all n elements)

@@ -821,6 +821,7 @@ __global__ void __launch_bounds__(NT) k_gmres(OpP<T> P, const cx<T>* __restrict_
     partB += (size_t)q * G * pstride;
     Rg += q * rgs;
     st += q;
+    P.k += q * P.kstride;
   } else {
     bid = blockIdx.x;
     G = gridDim.x;
@@ -1520,6 +1521,7 @@ OpP<T> mkop(const hz::OpDesc& d) {
   }
   if constexpr (sizeof(T) == 8) p.k = reinterpret_cast<const T*>(d.k_d);
   else p.k = reinterpret_cast<const T*>(d.k_f);
+  p.kstride = d.kstride;
   return p;
 }
 

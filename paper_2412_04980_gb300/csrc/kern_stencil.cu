@@ -46,6 +46,7 @@ OpP<T> make_op(const hz::OpDesc& d) {
   }
   if constexpr (sizeof(T) == 8) p.k = reinterpret_cast<const T*>(d.k_d);
   else p.k = reinterpret_cast<const T*>(d.k_f);
+  p.kstride = d.kstride;
   return p;
 }
 
@@ -101,6 +102,7 @@ template <typename T, typename TI, typename TO, int R, int MODE>
 __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __restrict__ x,
                                                        const cx<TI>* __restrict__ f, cx<TO>* __restrict__ y,
                                                        T omega) {
+  P.k += (size_t)blockIdx.z * P.kstride;  // this right-hand side's wavenumber field
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny;
   x += off;
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __r
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_jacobi_zero(OpP<T> P, const cx<T>* __restrict__ f, cx<T>* __restrict__ y,
                                                      T omega) {
+  P.k += (size_t)blockIdx.y * P.kstride;  // this right-hand side's wavenumber field
   const size_t n = (size_t)P.nx * P.ny;
   const size_t off = (size_t)blockIdx.y * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -159,6 +162,7 @@ template <typename T, typename TV, int R>
 __global__ void __launch_bounds__(BX* BY) k_defl_prolong_resid(OpP<T> P, const cx<T>* __restrict__ vtil, int ncx,
                                                                  int ncy, const cx<TV>* __restrict__ v,
                                                                  cx<T>* __restrict__ tout, cx<T>* __restrict__ rtil) {
+  P.k += (size_t)blockIdx.z * P.kstride;  // this right-hand side's wavenumber field
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny;
   const size_t offc = (size_t)blockIdx.z * ncx * ncy;
@@ -303,6 +307,7 @@ constexpr int DXC = 32, DYC = 8;
 template <typename T, int R>
 __global__ void __launch_bounds__(BX* BY) k_mg_down(OpP<T> P, const cx<T>* __restrict__ f, cx<T>* __restrict__ fc,
                                                       int ncx, int ncy, T omega) {
+  P.k += (size_t)blockIdx.z * P.kstride;  // this right-hand side's wavenumber field
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int OX = 2 * DXC + 1, OY = 2 * DYC + 1;
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny, offc = (size_t)blockIdx.z * ncx * ncy;
@@ -365,6 +370,7 @@ template <typename T, int R>
 __global__ void __launch_bounds__(BX* BY) k_mg_up(OpP<T> P, const cx<T>* __restrict__ f, const cx<T>* __restrict__ ec,
                                                     int ncx, int ncy, cx<T>* __restrict__ y, T omega,
                                                     const cx<T>* __restrict__ add) {
+  P.k += (size_t)blockIdx.z * P.kstride;  // this right-hand side's wavenumber field
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t off = (size_t)blockIdx.z * P.nx * P.ny, offc = (size_t)blockIdx.z * ncx * ncy;
   f += off;
@@ -566,6 +572,7 @@ __device__ __forceinline__ void mg_down_band(const OpP<T>& P, const cx<T>* __res
 template <typename T>
 __global__ void __launch_bounds__(256) k_mg_down_r1(OpP<T> P, const cx<T>* __restrict__ f, cx<T>* __restrict__ fc,
                                                     int ncx, int ncy, T omega, int RB) {
+  P.k += (size_t)blockIdx.z * P.kstride;  // this right-hand side's wavenumber field
   const int lane = threadIdx.x & 31;
   const int strip = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (30 * strip >= ncx) return;  // whole warp
@@ -740,6 +747,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_mg_up_r1(OpP<T> P, const cx<T>* __restrict__ f, const cx<T>* __restrict__ ec,
                                                   int ncx, int ncy, cx<T>* __restrict__ y, T omega,
                                                   const cx<T>* __restrict__ add, int RB) {
+  P.k += (size_t)blockIdx.z * P.kstride;  // this right-hand side's wavenumber field
   const int lane = threadIdx.x & 31;
   const int strip = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int dof = P.bc != 0;

@@ -289,14 +289,16 @@ __global__ void __launch_bounds__(NT) k_add(const cx<TX>* __restrict__ x, const 
     y[e] = cvt<TY>(cvt<T>(x[e]) + cvt<T>(z[e]));
 }
 
-// y = A x with A dense complex double (row-major n x n); one warp per row; batch in blockIdx.y
+// y = A x with A dense complex double (row-major n x n); one warp per row; batch in blockIdx.y,
+// right-hand side b with the matrix A + b astride (astride 0: one matrix for the batch)
 template <typename T>
-__global__ void __launch_bounds__(NT) k_dense(const cx<double>* __restrict__ A, int n, const cx<T>* __restrict__ x,
-                                              cx<T>* __restrict__ y) {
+__global__ void __launch_bounds__(NT) k_dense(const cx<double>* __restrict__ A, size_t astride, int n,
+                                              const cx<T>* __restrict__ x, cx<T>* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const size_t off = (size_t)blockIdx.y * n;
   if (row >= n) return;
+  A += blockIdx.y * astride;
   double sr = 0, si = 0;
   for (int c = lane; c < n; c += 32) {
     cx<double> a = A[(size_t)row * n + c];
@@ -453,14 +455,14 @@ cudaError_t launch_add(Ctx& c, int tx, const void* x, int tz, const void* z, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, void* y, int nrhs) {
+cudaError_t launch_dense(Ctx& c, const double* A, int n, int dt, const void* x, void* y, int nrhs, size_t astride) {
   dim3 grid((n + NT / 32 - 1) / (NT / 32), nrhs);
-  ProfScope ps(c, F_DENSE, (double)n * n * 16.0);
+  ProfScope ps(c, F_DENSE, (double)n * n * 16.0 * (astride ? nrhs : 1));
   if (dt == C128)
-    k_dense<double><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(A), n,
+    k_dense<double><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(A), astride, n,
                                           reinterpret_cast<const cx<double>*>(x), reinterpret_cast<cx<double>*>(y));
   else
-    k_dense<float><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(A), n,
+    k_dense<float><<<grid, NT, 0, c.s>>>(reinterpret_cast<const cx<double>*>(A), astride, n,
                                          reinterpret_cast<const cx<float>*>(x), reinterpret_cast<cx<float>*>(y));
   return cudaGetLastError();
 }

@@ -36,10 +36,11 @@ static __device__ __align__(256) double g_partials[kParts * 2 * kMaxRhs];
 // partial sums of |b - A u|^2 and |b|^2, Sommerfeld 5-point rows with ghost points
 __global__ void __launch_bounds__(kNT) k_resid_norm(int nx, int ny, double c, double H, const double* __restrict__ k,
                                                     const cx<double>* __restrict__ b, const cx<double>* __restrict__ u,
-                                                    double* __restrict__ part, int bc) {
+                                                    double* __restrict__ part, int bc, size_t kstride) {
   __shared__ double sr[kNT / 32], sb[kNT / 32];
   const size_t n = (size_t)nx * ny;
   const size_t off = (size_t)blockIdx.y * n;
+  k += blockIdx.y * kstride;  // per-right-hand-side wavenumber fields (kstride 0: shared)
   double r2 = 0, b2 = 0;
   for (size_t i = blockIdx.x * (size_t)kNT + threadIdx.x; i < n; i += (size_t)gridDim.x * kNT) {
     const int gy = (int)(i / nx), gx = (int)(i - (size_t)gy * nx);
@@ -167,6 +168,10 @@ extern "C" int hz_true_residual_noalloc(hz_handle hp, const void* b, const void*
     return HZ_EINVAL;
   }
   hz::Handle* H = &hp->h;
+  if (H->cfg.per_rhs_k && nrhs > H->nbmax) {
+    hz::set_error("with per_rhs_k every right-hand side needs its own wavenumber field: nrhs <= max_rhs");
+    return HZ_EINVAL;
+  }
   // an error left by earlier, unrelated work is reported as such, not as this call's failure
   cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) {
@@ -196,7 +201,8 @@ extern "C" int hz_true_residual_noalloc(hz_handle hp, const void* b, const void*
   const int nparts = (int)(nb < kParts ? (nb > 0 ? nb : 1) : kParts);
   k_resid_norm<<<dim3(nparts, nrhs), kNT, 0, H->ctx.s>>>(L.nx, L.ny, 1.0 / (H->g.h * H->g.h), H->g.h, L.k_d,
                                                          reinterpret_cast<const cx<double>*>(b),
-                                                         reinterpret_cast<const cx<double>*>(u), part, H->g.bc);
+                                                         reinterpret_cast<const cx<double>*>(u), part, H->g.bc,
+                                                         L.kstride);
   e = cudaGetLastError();
   if (e != cudaSuccess) return hz::status_of(e, "k_resid_norm");
   k_resid_finish<<<nrhs, kNT, 0, H->ctx.s>>>(part, nparts, relres_dev);

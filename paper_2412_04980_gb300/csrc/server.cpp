@@ -74,15 +74,15 @@ int run_request(hz_server_s* S, Req* r) {
   cudaStream_t s = nullptr;
   int st = status_of(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
   if (st) return st;
-  const size_t n = (size_t)r->grid.nx * r->grid.ny;
+  const size_t n = (size_t)r->grid.nx * r->grid.ny, nk = r->k.size();
   void *kd = nullptr, *bd = nullptr, *ud = nullptr;
   hz_handle h = nullptr;
   std::vector<hz_stats> stats(r->nrhs);
   do {
-    if ((st = status_of(cudaMalloc(&kd, n * 8), "cudaMalloc"))) break;
+    if ((st = status_of(cudaMalloc(&kd, nk * 8), "cudaMalloc"))) break;
     if ((st = status_of(cudaMalloc(&bd, (size_t)r->nrhs * n * 16), "cudaMalloc"))) break;
     if ((st = status_of(cudaMalloc(&ud, (size_t)r->nrhs * n * 16), "cudaMalloc"))) break;
-    if ((st = status_of(cudaMemcpyAsync(kd, r->k.data(), n * 8, cudaMemcpyHostToDevice, s), "copy k"))) break;
+    if ((st = status_of(cudaMemcpyAsync(kd, r->k.data(), nk * 8, cudaMemcpyHostToDevice, s), "copy k"))) break;
     if ((st = status_of(cudaMemcpyAsync(bd, r->b.data(), (size_t)r->nrhs * n * 16, cudaMemcpyHostToDevice, s), "copy b")))
       break;
     if ((st = status_of(cudaStreamSynchronize(s), "sync"))) break;
@@ -211,12 +211,13 @@ int hz_submit(hz_server S, const hz_request* q, uint64_t* ticket) {
   r->nrhs = q->nrhs;
   r->tol = q->tol;
   const size_t n = (size_t)q->grid.nx * q->grid.ny;
-  r->k.assign(q->k_host, q->k_host + n);
+  const size_t nk = n * (q->config.per_rhs_k ? (size_t)q->config.max_rhs : 1);  // wavenumber fields
+  r->k.assign(q->k_host, q->k_host + nk);
   r->b.assign(q->b_host, q->b_host + 2 * n * q->nrhs);
   r->u_out = q->u_host;
   r->stats_out = q->stats_host;
   // footprint: handle workspace + the request's own device copies of k, b, u
-  r->bytes = estimate_bytes(q->grid, q->config) + n * 8 + 2 * n * 16 * (size_t)q->nrhs;
+  r->bytes = estimate_bytes(q->grid, q->config) + nk * 8 + 2 * n * 16 * (size_t)q->nrhs;
   if (r->bytes > S->budget) {
     set_error("request footprint exceeds the server memory budget");
     return HZ_ENOMEM;

@@ -157,7 +157,7 @@ def test_config_validation_of_new_fields(L):
     h = ctypes.c_void_p()
     g = hz.HzGrid(9, 9, 0.1, 0)
     for bad in (dict(device_gmres=5), dict(device_gmres=-1), dict(autotune=2), dict(reorth_eta=1.5),
-                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1), dict(cslp_solver=2), dict(sym_rows=2),
+                dict(cycle_m=0), dict(l2_tol=1.0), dict(l2_tol=-0.1), dict(cslp_solver=2), dict(sym_rows=2), dict(per_rhs_k=2),
                 dict(levels=3, level_tol={2: 0.1}), dict(levels=3, level_tol={3: 0.1}),
                 dict(levels=4, level_tol={3: 1.0}), dict(levels=4, level_tol={3: float("nan")})):
         c = hz.config(**bad)
