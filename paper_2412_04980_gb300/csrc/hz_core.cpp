@@ -643,6 +643,7 @@ int setup(Handle* h, const double* k_dev) {
   CS(noalloc_prepare(h));
   CK(cudaStreamSynchronize(h->ctx.s));
   if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_gmres(h));
+  if (cfg.device_gmres == 1 && cfg.autotune) CS(autotune_batch(h));
   if (cfg.autotune) CS(autotune_mg(h));
   // the first level >= 3 from which every level runs one-iteration device cycles and a device
   // CSLP inverse (multigrid or persistent GMRES): its coarse solve issues no host decision
@@ -672,8 +673,33 @@ std::mutex g_tune_mu;
 // slice-distributed grid
 std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune;
 
+// (nx, ny, precision, radius, cap, batch) -> CTAs per cluster of the cluster form for a batch of
+// that many right-hand sides, or 0 when one right-hand side at a time on the whole grid was faster
+std::map<std::tuple<int, int, int, int, int, int>, int> g_tune_batch;
+
 // tiles along a side of n nodes for tile width t (the last tile takes the remainder node)
 static int tile_count(int n, int t) { return n > 1 ? (n - 1 + t - 1) / t : 1; }
+
+// Fill the first nb right-hand sides of a level's CSLP input (L.t) with one fixed pseudo-random
+// vector (xorshift32, values in [-1, 1)).
+static int fill_tune_input(Handle* h, Level& L, int nb) {
+  const size_t eb = elem_bytes(L.dpre);
+  std::vector<float> hb(2 * L.n);
+  uint32_t r = 12345u;
+  for (auto& v : hb) {
+    r ^= r << 13;
+    r ^= r >> 17;
+    r ^= r << 5;
+    v = (float)((double)r / 2147483648.0 - 1.0);
+  }
+  std::vector<double> hd;
+  if (eb == 16) hd.assign(hb.begin(), hb.end());
+  const void* src = eb == 16 ? (const void*)hd.data() : (const void*)hb.data();
+  for (int q = 0; q < nb; ++q)
+    CK(cudaMemcpyAsync((char*)L.t + (size_t)q * L.n * eb, src, L.n * eb, cudaMemcpyHostToDevice, h->ctx.s));
+  CK(cudaStreamSynchronize(h->ctx.s));
+  return HZ_OK;
+}
 }  // namespace
 
 int autotune_gmres(Handle* h) {
@@ -777,6 +803,92 @@ int autotune_gmres(Handle* h) {
 
 // Band heights of the radius-1 multigrid sweeps, timed once per level shape and precision on the
 // handle's own multigrid buffers (their contents are rewritten by every V-cycle before use).
+// Batches of max_rhs >= kClusterMinRhs right-hand sides on levels that can run the cluster form:
+// time the batch as one launch with clusters of 16, 8 and 4 CTAs (a cluster per right-hand side;
+// with 16 right-hand sides, clusters of 16 need two waves on 152 SMs, clusters of 8 fit in one)
+// and as one whole-grid launch per right-hand side, min(cap, 24) iterations each, twice; keep
+// the fastest per level shape and batch size.
+int autotune_batch(Handle* h) {
+  const int nb = h->nbmax;
+  if (nb < kClusterMinRhs) return HZ_OK;
+  for (auto& L : h->lv) {
+    if (L.gcl <= 0) continue;
+    const auto key = std::make_tuple(L.nx, L.ny, L.dpre, L.R, L.capg, nb);
+    auto adopt = [&](int C) {
+      if (C > 0) {
+        L.gcl = C;
+      } else {
+        L.gseq = true;
+      }
+    };
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_batch.find(key);
+      if (it != g_tune_batch.end()) {
+        adopt(it->second);
+        continue;
+      }
+    }
+    CS(fill_tune_input(h, L, nb));
+    const size_t eb = elem_bytes(L.dpre);
+    const OpDesc M = L.opM(L.dpre, h->cfg.beta1, h->cfg.beta2);
+    const int K = std::min(L.capg, 24);
+    const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
+    std::vector<int> cand;
+    for (int C = L.gcl; C >= 4; C /= 2) cand.push_back(C);
+    if (L.ggrid > 0) cand.push_back(0);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<float> ms(cand.size(), 0.0f);
+    int st = HZ_OK;
+    for (size_t c = 0; c < cand.size() && st == HZ_OK; ++c) {
+      for (int rep = 0; rep < 2 && st == HZ_OK; ++rep) {
+        st = status_of(cudaMemsetAsync(L.rt, 0, (size_t)nb * L.n * eb, h->ctx.s), "autotune");
+        if (!st) st = status_of(cudaEventRecord(e0, h->ctx.s), "autotune");
+        cudaError_t e = cudaSuccess;
+        if (!st && cand[c] > 0) {
+          e = launch_gmres_persistent(h->ctx, M, L.dpre, L.t, L.rt, L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB,
+                                      L.gpstride, L.gR, L.gst, K, 0.0, cand[c], true, nb, eta2);
+        } else if (!st) {
+          for (int q = 0; q < nb && e == cudaSuccess; ++q) {
+            const void* bq = (const char*)L.t + (size_t)q * L.n * eb;
+            void* xq = (char*)L.rt + (size_t)q * L.n * eb;
+            e = L.gtiles > 0 ? launch_gmres_tile(h->ctx, op_of_rhs(M, q), L.dpre, bq, xq, L.Vg, L.wg, L.gflag,
+                                                 L.gpartA, L.gpartB, L.gR, L.gst + q, K, 0.0, L.gtx, L.gty, eta2)
+                             : launch_gmres_persistent(h->ctx, op_of_rhs(M, q), L.dpre, bq, xq, L.Vg, L.wg, L.wg2,
+                                                       L.gpartA, L.gpartB, L.gpstride, L.gR, L.gst + q, K, 0.0,
+                                                       L.ggrid, false, 1, eta2);
+          }
+        }
+        if (!st) st = status_of(e, "autotune launch");
+        if (!st) st = status_of(cudaEventRecord(e1, h->ctx.s), "autotune");
+        if (!st) st = wait_event(h, e1);
+        if (!st) st = status_of(cudaEventElapsedTime(&ms[c], e0, e1), "autotune");  // the second run counts
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    std::vector<GmresState> gs(nb);
+    CK(cudaMemcpy(gs.data(), L.gst, sizeof(GmresState) * nb, cudaMemcpyDeviceToHost));
+    CK(cudaMemsetAsync(L.gst, 0, sizeof(GmresState) * nb, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    for (int q = 0; q < nb; ++q)
+      if (gs[q].err) {
+        set_error("a grid barrier of the persistent GMRES kernel exceeded its wait budget");
+        return HZ_ETIMEOUT;
+      }
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+      if (ms[c] < ms[best]) best = c;
+    adopt(cand[best]);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_batch[key] = cand[best];
+  }
+  return HZ_OK;
+}
+
 int autotune_mg(Handle* h) {
   for (auto& L : h->lv) {
     const int nm = (int)L.mg.size();
@@ -1123,7 +1235,7 @@ int cslp_gmres(Handle* h, int l, const void* b, void* x, int nb, int* its_out) {
     const size_t eb = elem_bytes(dt);
     const double eta2 = h->cfg.reorth_eta >= 1.0 ? 2.0 : h->cfg.reorth_eta * h->cfg.reorth_eta;
     const bool use_cluster =
-        L.gcl > 0 && (h->cfg.device_gmres == 3 || nb >= kClusterMinRhs || L.ggrid <= 0);
+        L.gcl > 0 && (h->cfg.device_gmres == 3 || (nb >= kClusterMinRhs && !L.gseq) || L.ggrid <= 0);
     if (use_cluster) {  // one launch, one thread-block cluster per right-hand side
       CK(launch_gmres_persistent(h->ctx, M, dt, b, x, L.Vg, L.wg, L.wg2, L.gpartA, L.gpartB, L.gpstride, L.gR, L.gst,
                                  L.capg, h->cfg.cslp_tol, L.gcl, true, nb, eta2));

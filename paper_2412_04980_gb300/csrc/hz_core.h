@@ -74,6 +74,7 @@ struct Level {
   double* bpart = nullptr;
   int ggrid = 0;                             // CTAs of the cooperative-grid form (0: host-driven GMRES)
   int gcl = 0;                               // CTAs per cluster of the cluster form (0: not used)
+  bool gseq = false;                         // batches faster one right-hand side at a time (autotune)
   int gtiles = 0, gtx = 0, gty = 0;          // tile-owned form: CTAs (= tiles) and tile shape (0: not used)
   OpDesc opA(int dt) const;
   OpDesc opM(int dt, double b1, double b2) const;
@@ -128,6 +129,9 @@ int setup(Handle* h, const double* k_dev);
 int noalloc_prepare(Handle* h);
 // Keep the faster persistent GMRES form per level (tile-owned or slice-distributed).
 int autotune_gmres(Handle* h);
+// Keep the faster of the cluster form (16, 8 or 4 CTAs per right-hand side) and one whole-grid
+// launch per right-hand side for batches of max_rhs right-hand sides.
+int autotune_batch(Handle* h);
 // Keep the fastest band height of the radius-1 multigrid sweeps per level shape (autotune).
 int autotune_mg(Handle* h);
 int gmres_grid_want(int nx, int ny);
