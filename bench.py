@@ -133,8 +133,10 @@ def parse():
     ap.add_argument("--level", type=int, default=1,
                     help="--micro gmres: deflation level whose CSLP GMRES runs (>= 3 keeps the level's own "
                          "radius-3 operator; the levels above get minimal Krylov workspace)")
-    ap.add_argument("--batch", type=int, default=16,
-                    help="right-hand sides per lockstep sub-batch for multi-source workloads")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="right-hand sides per lockstep sub-batch for multi-source workloads (0: the "
+                         "largest divisor of the right-hand-side count whose workspace fits the free device "
+                         "memory)")
     ap.add_argument("--serve", action="store_true",
                     help="serving trace: mixed requests with Poisson arrivals through hz_server_*")
     ap.add_argument("--requests", type=int, default=32)
@@ -585,6 +587,15 @@ def batched(args, p):
     torch.cuda.set_device(dev)
     inst = p.k.ndim == 3
     B = p.nrhs if inst else args.batch
+    if B <= 0:  # largest sub-batch whose workspace (plus the right-hand sides and solutions) fits
+        free, _ = torch.cuda.mem_get_info(dev)
+        vec = p.nx * p.ny * 16
+        B = p.nrhs
+        while B > 1 and (p.nrhs % B or hz.estimate_bytes(p.nx, p.ny, p.h, levels=p.levels,
+                                                         negdef_from_level=p.negdef_from_level,
+                                                         precision=args.precision, max_rhs=B)
+                         + 2 * p.nrhs * vec > 0.97 * free):
+            B -= 1
     k = torch.from_numpy(p.k).to(dev)
     b_all = torch.from_numpy(p.b).to(dev)
     u_all = torch.empty_like(b_all)
@@ -633,14 +644,16 @@ def batched(args, p):
     H.profile_enable(dom_id, False)
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     assert all(x["status"] == 0 and x["true_relres"] <= 1e-6 for x in stats)
-    # end to end: host right-hand sides in, host solutions out, through hz_solve_host
+    # end to end: host right-hand sides in, host solutions out, through hz_solve_host (which holds
+    # its own device copies of b and u: the solutions of the timed steps are released first)
+    del u_all
+    torch.cuda.empty_cache()
     b_host = p.b
     t0 = time.perf_counter()
     for i in range(0, nr, B):
         H.solve_host(b_host[i:i + B], tol=1e-6)
     e2e_s = time.perf_counter() - t0
     H.close()
-    del u_all
     torch.cuda.empty_cache()
     alone = None
     if inst:  # the first four instances one at a time, each on a handle of its own
