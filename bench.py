@@ -141,6 +141,12 @@ def parse():
                     help="serving trace: mixed requests with Poisson arrivals through hz_server_*")
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--serve-sizes", default="257,513,1025,2049")
+    ap.add_argument("--serve-burst", action="store_true",
+                    help="serving: all requests queued at t = 0, --max-active concurrent solves, once without "
+                         "and once with request merging (--serve-batch right-hand sides)")
+    ap.add_argument("--trace-seed", type=int, default=2024, help="seed of the serving trace")
+    ap.add_argument("--serve-batch", type=int, default=16,
+                    help="right-hand sides of a merged solve in the --serve-burst pass with merging")
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=160.0)
     ap.add_argument("--load", type=float, default=1.0,
@@ -505,10 +511,11 @@ def serve_trace(n_req: int, sizes, seed: int = 2024):
     return out
 
 
-def run_trace(hz, reqs, arrivals, max_active, budget, precision):
-    """Submit reqs at the given arrival offsets (seconds; None = all at once) to a fresh server;
-    returns per-request latency and the server's report."""
-    srv = hz.Server(budget_bytes=budget, max_active=max_active)
+def run_trace(hz, reqs, arrivals, max_active, budget, precision, batch_rhs=0):
+    """Submit reqs at the given arrival offsets (seconds; None = all at once) to a fresh server
+    (batch_rhs > 1: compatible queued requests merge into solves of up to that many right-hand
+    sides); returns per-request latency and the server's report."""
+    srv = hz.Server(budget_bytes=budget, max_active=max_active, batch_rhs=batch_rhs)
     tickets = []
     t0 = time.perf_counter()
     for i, p in enumerate(reqs):
@@ -532,7 +539,37 @@ def run_trace(hz, reqs, arrivals, max_active, budget, precision):
             "p50_ms": statistics.median(lat),
             "p99_ms": lat_sorted[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)],
             "peak_gb": rep["peak_bytes"] / 2 ** 30, "completed": rep["completed"], "failed": rep["failed"],
-            "max_true_relres": worst, "max_active": max_active, "precision": precision}
+            "max_true_relres": worst, "max_active": max_active, "precision": precision, "batch_rhs": batch_rhs,
+            "merged_solves": rep["merged_solves"], "merged_requests": rep["merged_requests"]}
+
+
+def serve_burst(args):
+    """Closed burst of the serving trace: every request queued at t = 0, --max-active concurrent
+    solves, mixed precision; once as submitted and once with compatible requests merged into
+    multi-instance solves of up to --serve-batch right-hand sides."""
+    import torch
+
+    import paper_2412_04980_gb300 as hz
+
+    torch.cuda.set_device(0)
+    sizes = [int(x) for x in args.serve_sizes.split(",")]
+    reqs = serve_trace(args.requests, sizes, seed=args.trace_seed)
+    budget = int(args.budget_gb * 2 ** 30)
+    warm = serve_trace(1, [min(sizes)], seed=7)
+    run_trace(hz, warm, None, 1, budget, "mixed")
+    plain = run_trace(hz, reqs, None, args.max_active, budget, "mixed")
+    merged = run_trace(hz, reqs, None, args.max_active, budget, "mixed", batch_rhs=args.serve_batch)
+    line = {"metric": "serving, closed burst: solve requests/s and p50/p99 latency at a 1e-6 relative residual",
+            "mode": "serve_burst", "value": merged["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32+f64 (FP32 preconditioner, FP64 outer)",
+            "config": {"workload": "closed burst of seeded random-velocity solve requests, all queued at t = 0",
+                       "requests": len(reqs), "sizes": sizes, "sources_per_request": "1-8 (uniform)",
+                       "rhs_total": sum(p.nrhs for p in reqs), "trace_seed": args.trace_seed,
+                       "budget_gb": args.budget_gb, "max_active": args.max_active,
+                       "requests_per_size": {str(n): sum(1 for p in reqs if p.nx == n) for n in sizes}},
+            "p50_ms": merged["p50_ms"], "p99_ms": merged["p99_ms"],
+            "passes": {"concurrent": plain, "concurrent_merged": merged}}
+    print(json.dumps(line))
 
 
 def serve(args):
@@ -781,6 +818,8 @@ def main():
 
     if args.micro:
         return micro(args)
+    if args.serve_burst:
+        return serve_burst(args)
     if args.serve:
         return serve(args)
 

@@ -327,6 +327,8 @@ typedef struct {
   double solves_per_s;     /* completed requests / (last completion - first submit) */
   size_t peak_bytes;       /* largest sum of admitted footprints seen */
   size_t budget_bytes;     /* the budget given to hz_server_create */
+  long long merged_solves;   /* solves that ran several requests as one batch */
+  long long merged_requests; /* requests that ran in such merged solves */
 } hz_server_stats;
 
 /* Device bytes hz_setup would allocate for this grid and configuration (bytes requested
@@ -338,6 +340,15 @@ int hz_estimate_bytes(const hz_grid* grid, const hz_config* cfg, size_t* bytes);
  * (at most that many requests run at once) and a device-memory budget in bytes.
  * Errors: HZ_EINVAL (null out, max_active < 1, zero budget), HZ_ENOMEM, HZ_ECUDA. */
 int hz_server_create(size_t mem_budget_bytes, int max_active, hz_server* out);
+
+/* Merge compatible requests (same grid, tolerance and configuration apart from max_rhs and
+ * per_rhs_k) that are queued when a worker takes one of them into one multi-instance solve of
+ * at most max_batch_rhs right-hand sides (every right-hand side keeps its request's wavenumber
+ * field: per_rhs_k), as long as the merged footprint fits the remaining budget.  Each request
+ * still gets its own solution, statistics and status; they equal its solve alone up to the
+ * summation order of the GMRES form the batch size selects.  0 or 1 (the default): no merging.
+ * Errors: HZ_EINVAL (null server, max_batch_rhs outside [0, 1024]). */
+int hz_server_set_batching(hz_server s, int max_batch_rhs);
 
 /* Queue a request; *ticket identifies it.  k and b are copied before the call returns; u_host
  * and stats_host must stay valid until the request is reported finished.

@@ -89,6 +89,7 @@ class HzServerStats(ctypes.Structure):
         ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("queued", ctypes.c_longlong),
         ("active", ctypes.c_int), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
         ("solves_per_s", ctypes.c_double), ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+        ("merged_solves", ctypes.c_longlong), ("merged_requests", ctypes.c_longlong),
     ]
 
     def as_dict(self) -> dict:
@@ -139,6 +140,7 @@ _SIGS = {
     "hz_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_D)]),
     "hz_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(_D)]),
     "hz_server_report": (_I, [_P, ctypes.POINTER(HzServerStats)]),
+    "hz_server_set_batching": (_I, [_P, _I]),
     "hz_server_destroy": (_I, [_P]),
 }
 
@@ -450,11 +452,15 @@ def estimate_bytes(nx: int, ny: int, h: float, bc: int = HZ_BC_SOMMERFELD, **cfg
 
 class Server:
     """Concurrent solves on the current device (hz_server_*): ``submit`` copies k and b and
-    returns a ticket; ``wait`` blocks until the solution is in the numpy array it returns."""
+    returns a ticket; ``wait`` blocks until the solution is in the numpy array it returns.
+    ``batch_rhs`` > 1 merges compatible queued requests into multi-instance solves of up to that
+    many right-hand sides (hz_server_set_batching)."""
 
-    def __init__(self, budget_bytes: int, max_active: int = 2):
+    def __init__(self, budget_bytes: int, max_active: int = 2, batch_rhs: int = 0):
         self._s = ctypes.c_void_p()
         _check(lib().hz_server_create(int(budget_bytes), int(max_active), ctypes.byref(self._s)), "hz_server_create")
+        if batch_rhs:
+            _check(lib().hz_server_set_batching(self._s, int(batch_rhs)), "hz_server_set_batching")
         self._live = {}
 
     def submit(self, k_np, b_np, h: float, tol: float = 1e-6, bc: str = "sommerfeld", **cfg) -> int:

@@ -8,6 +8,13 @@
 // reused as soon as they free up.  Work of concurrent requests overlaps on the GPU; every
 // request's arithmetic is independent of the others, so its result equals the result of
 // running it alone.
+//
+// With batching on (hz_server_set_batching), a worker that takes a request also takes the queued
+// requests with the same grid, configuration and tolerance, in arrival order, while the merged
+// right-hand sides stay within the batch limit and the merged footprint within the budget.  The
+// group runs as one multi-instance solve (per_rhs_k: every right-hand side keeps its request's
+// wavenumber field), so each sweep is one launch over all of them; the results are scattered back
+// to the requests, each with its own statistics and status.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -54,6 +61,8 @@ struct Req {
 struct hz_server_s {
   size_t budget = 0, used = 0, peak = 0;
   int max_active = 1, active = 0, device = 0;
+  int batch_rhs = 0;                 // right-hand sides of a merged solve (<= 1: no merging)
+  long long merged_solves = 0, merged_requests = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Req*> queue;
@@ -104,10 +113,113 @@ int run_request(hz_server_s* S, Req* r) {
   return st;
 }
 
+// Requests that may share one multi-instance solve: same grid and tolerance, and the same
+// configuration apart from max_rhs and per_rhs_k.
+bool same_grid_config(const Req* a, const Req* b) {
+  const hz_grid &g = a->grid, &h = b->grid;
+  if (g.nx != h.nx || g.ny != h.ny || g.h != h.h || g.bc != h.bc || a->tol != b->tol) return false;
+  const hz_config &x = a->cfg, &y = b->cfg;
+  if (x.levels != y.levels || x.precision != y.precision || x.beta1 != y.beta1 || x.beta2 != y.beta2 ||
+      x.restart != y.restart || x.max_outer != y.max_outer || x.l2_tol != y.l2_tol || x.l2_maxit != y.l2_maxit ||
+      x.cslp_tol != y.cslp_tol || x.c_it != y.c_it || x.coarsest_tol != y.coarsest_tol ||
+      x.negdef_from_level != y.negdef_from_level || x.mg_max_level != y.mg_max_level || x.mg_omega != y.mg_omega ||
+      x.mg_nu1 != y.mg_nu1 || x.mg_nu2 != y.mg_nu2 || x.mg_coarsest_side != y.mg_coarsest_side ||
+      x.timeout_s != y.timeout_s || x.device_gmres != y.device_gmres || x.reorth_eta != y.reorth_eta ||
+      x.graphs != y.graphs || x.autotune != y.autotune || x.cycle_m != y.cycle_m ||
+      x.cslp_solver != y.cslp_solver || x.sym_rows != y.sym_rows)
+    return false;
+  for (int l = 0; l < HZ_MAX_LEVELS; ++l)
+    if (x.level_tol[l] != y.level_tol[l]) return false;
+  return true;
+}
+
+// Footprint of a merged solve of nb right-hand sides: handle workspace with one wavenumber field
+// per right-hand side, plus the device copies of the fields, b and u.
+size_t group_bytes(const Req* r, int nb) {
+  hz_config c = r->cfg;
+  c.max_rhs = nb;
+  c.per_rhs_k = 1;
+  const size_t n = (size_t)r->grid.nx * r->grid.ny;
+  return estimate_bytes(r->grid, c) + (size_t)nb * n * (8 + 2 * 16);
+}
+
+// Run a group of compatible requests as one multi-instance solve on its own stream and handle.
+// Returns the status of the shared part (set-up, copies); per-request statuses go to st_out.
+int run_group(const std::vector<Req*>& grp, std::vector<int>& st_out) {
+  const Req* r0 = grp[0];
+  const size_t n = (size_t)r0->grid.nx * r0->grid.ny;
+  int nb = 0;
+  for (const Req* r : grp) nb += r->nrhs;
+  // wavenumber field of every right-hand side (its request's field), right-hand sides in order
+  std::vector<double> k((size_t)nb * n), b((size_t)nb * n * 2);
+  size_t o = 0;
+  for (const Req* r : grp) {
+    for (int q = 0; q < r->nrhs; ++q) {
+      const double* src = r->k.data() + (r->cfg.per_rhs_k ? (size_t)q * n : 0);
+      std::memcpy(k.data() + (o + q) * n, src, n * 8);
+    }
+    std::memcpy(b.data() + o * n * 2, r->b.data(), (size_t)r->nrhs * n * 16);
+    o += r->nrhs;
+  }
+  hz_config cfg = r0->cfg;
+  cfg.max_rhs = nb;
+  cfg.per_rhs_k = 1;
+  cudaStream_t s = nullptr;
+  int st = status_of(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (st) return st;
+  void *kd = nullptr, *bd = nullptr, *ud = nullptr;
+  hz_handle h = nullptr;
+  std::vector<hz_stats> stats(nb);
+  int sst = HZ_OK;
+  do {
+    if ((st = status_of(cudaMalloc(&kd, (size_t)nb * n * 8), "cudaMalloc"))) break;
+    if ((st = status_of(cudaMalloc(&bd, (size_t)nb * n * 16), "cudaMalloc"))) break;
+    if ((st = status_of(cudaMalloc(&ud, (size_t)nb * n * 16), "cudaMalloc"))) break;
+    if ((st = status_of(cudaMemcpyAsync(kd, k.data(), (size_t)nb * n * 8, cudaMemcpyHostToDevice, s), "copy k"))) break;
+    if ((st = status_of(cudaMemcpyAsync(bd, b.data(), (size_t)nb * n * 16, cudaMemcpyHostToDevice, s), "copy b")))
+      break;
+    if ((st = status_of(cudaStreamSynchronize(s), "sync"))) break;
+    if ((st = hz_setup(&r0->grid, (const double*)kd, &cfg, s, &h))) break;
+    sst = hz_solve(h, bd, ud, nb, r0->tol, 0, stats.data());
+    if (sst != HZ_OK && sst != HZ_ENOTCONV && sst != HZ_EBREAKDOWN) {
+      st = sst;
+      break;
+    }
+    o = 0;
+    for (const Req* r : grp) {
+      st = status_of(cudaMemcpyAsync(r->u_out, (const char*)ud + o * n * 16, (size_t)r->nrhs * n * 16,
+                                     cudaMemcpyDeviceToHost, s),
+                     "copy u");
+      if (st) break;
+      o += r->nrhs;
+    }
+    if (!st) st = status_of(cudaStreamSynchronize(s), "sync");
+  } while (false);
+  if (h) hz_destroy(h);
+  if (kd) cudaFree(kd);
+  if (bd) cudaFree(bd);
+  if (ud) cudaFree(ud);
+  cudaStreamDestroy(s);
+  st_out.assign(grp.size(), st);
+  if (st) return st;
+  o = 0;
+  for (size_t i = 0; i < grp.size(); ++i) {
+    const Req* r = grp[i];
+    int rs = HZ_OK;  // the first failing right-hand side decides, as hz_solve does
+    for (int q = 0; q < r->nrhs && rs == HZ_OK; ++q) rs = stats[o + q].status;
+    st_out[i] = rs;
+    if (r->stats_out) std::memcpy(r->stats_out, stats.data() + o, sizeof(hz_stats) * r->nrhs);
+    o += r->nrhs;
+  }
+  return HZ_OK;
+}
+
 void worker(hz_server_s* S) {
   cudaSetDevice(S->device);
   for (;;) {
     Req* r = nullptr;
+    std::vector<Req*> grp;
+    size_t gbytes = 0;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       for (;;) {
@@ -122,29 +234,66 @@ void worker(hz_server_s* S) {
         if (r) break;
         S->cv_work.wait(lk);
       }
-      S->used += r->bytes;
+      grp.push_back(r);
+      gbytes = r->bytes;
+      if (S->batch_rhs > 1 && r->nrhs < S->batch_rhs) {
+        // compatible queued requests join while the batch and the budget allow
+        int nb = r->nrhs;
+        for (auto it = S->queue.begin(); it != S->queue.end();) {
+          Req* q = *it;
+          if (nb + q->nrhs <= S->batch_rhs && same_grid_config(r, q)) {
+            const size_t gb = group_bytes(r, nb + q->nrhs);
+            if (S->used + gb <= S->budget) {
+              grp.push_back(q);
+              nb += q->nrhs;
+              gbytes = gb;
+              it = S->queue.erase(it);
+              continue;
+            }
+          }
+          ++it;
+        }
+        if (grp.size() > 1) {
+          S->merged_solves += 1;
+          S->merged_requests += (long long)grp.size();
+        }
+      }
+      S->used += gbytes;
       S->peak = std::max(S->peak, S->used);
       S->active += 1;
-      r->t_start = Clock::now();
+      for (Req* q : grp) q->t_start = Clock::now();
     }
-    const int st = run_request(S, r);
-    std::vector<double>().swap(r->k);  // host copies are no longer needed
-    std::vector<double>().swap(r->b);
+    std::vector<int> sts(1, HZ_OK);
+    if (grp.size() == 1) {
+      sts[0] = run_request(S, r);
+    } else {
+      run_group(grp, sts);
+    }
+    const std::string msg = last_error_message();
+    for (Req* q : grp) {
+      std::vector<double>().swap(q->k);  // host copies are no longer needed
+      std::vector<double>().swap(q->b);
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      r->t_end = Clock::now();
-      r->status = st;
-      if (st != HZ_OK) r->err = last_error_message();
-      r->done = true;
-      S->used -= r->bytes;
-      S->active -= 1;
-      if (st == HZ_OK) {
-        S->completed += 1;
-        S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_end - r->t_submit).count());
-      } else {
-        S->failed += 1;
+      const Clock::time_point t_end = Clock::now();
+      for (size_t i = 0; i < grp.size(); ++i) {
+        Req* q = grp[i];
+        const int st = sts[i];
+        q->t_end = t_end;
+        q->status = st;
+        if (st != HZ_OK) q->err = msg;
+        q->done = true;
+        if (st == HZ_OK) {
+          S->completed += 1;
+          S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_end - q->t_submit).count());
+        } else {
+          S->failed += 1;
+        }
       }
-      S->t_last = r->t_end;
+      S->used -= gbytes;
+      S->active -= 1;
+      S->t_last = t_end;
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
@@ -285,6 +434,20 @@ int hz_server_report(hz_server S, hz_server_stats* out) {
   out->solves_per_s = span > 0 ? S->completed / span : 0.0;
   out->peak_bytes = S->peak;
   out->budget_bytes = S->budget;
+  out->merged_solves = S->merged_solves;
+  out->merged_requests = S->merged_requests;
+  return HZ_OK;
+}
+
+int hz_server_set_batching(hz_server S, int max_batch_rhs) {
+  if (!S || max_batch_rhs < 0 || max_batch_rhs > 1024) {
+    set_error("hz_server_set_batching: null server or max_batch_rhs outside [0, 1024]");
+    return HZ_EINVAL;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->batch_rhs = max_batch_rhs;
+  }
   return HZ_OK;
 }
 

@@ -162,3 +162,47 @@ def test_dirichlet_request_in_mix(hz):
         u, st, _ = srv.wait(t, timeout_s=600)
         assert np.array_equal(u, u0)
     srv.close()
+
+
+def test_batching_merges_compatible_requests(hz):
+    """With batching on, requests of one grid and configuration that are queued together run as
+    one multi-instance solve.  A 513^2 request keeps the single worker busy while five 129^2
+    requests of the same configuration (different wavenumber fields, 1-3 sources) queue up; they
+    merge (the report counts merged solves).  Each merged result matches its solve alone to the
+    solve tolerance (solution within 1e-5, outer iterations within one) and reaches 1e-6 with the
+    oracle's operator.  A request with another level count is never merged with them."""
+    big = mp.random_field(513, 5.0, seed=9, kh_max=0.3, levels=3, negdef_from_level=4, nsrc=4)
+    smalls = [mp.random_field(129, 5.0, seed=20 + i, kh_max=0.25 + 0.02 * i, levels=3, negdef_from_level=4,
+                              nsrc=1 + i % 3) for i in range(5)]
+    other = mp.random_field(129, 5.0, seed=40, kh_max=0.3, levels=2, negdef_from_level=4)
+    S = hz.Server(64 << 30, max_active=1, batch_rhs=16)
+
+    def cfg(p):
+        return dict(levels=p.levels, negdef_from_level=4, precision="mixed")
+
+    tb = S.submit(big.k, big.b, big.h, **cfg(big))
+    ts = [S.submit(p.k, p.b, p.h, **cfg(p)) for p in smalls]
+    to = S.submit(other.k, other.b, other.h, **cfg(other))
+    _, stb, _ = S.wait(tb)
+    assert all(x["status"] == 0 for x in stb)
+    outs = [S.wait(t) for t in ts]
+    uo, sto, _ = S.wait(to)
+    rep = S.report()
+    assert rep["merged_solves"] >= 1 and rep["merged_requests"] >= 2, rep
+    assert rep["completed"] == 7 and rep["failed"] == 0
+    for p, (u, st, _) in zip(smalls, outs):
+        H = hz.Helmholtz(dev(p.k), p.h, max_rhs=p.nrhs, **cfg(p))
+        ua, sta = H.solve(dev(p.b), tol=1e-6)
+        ua = ua.cpu().numpy()
+        H.close()
+        for r in range(p.nrhs):
+            assert st[r]["status"] == 0
+            rel = np.linalg.norm(p.b[r] - apply_helmholtz(u[r], p.k, p.h)) / np.linalg.norm(p.b[r])
+            assert rel <= 1e-6
+            assert rel2(u[r], ua[r]) <= 1e-5
+            assert abs(st[r]["outer_iterations"] - sta[r]["outer_iterations"]) <= 1
+    H = hz.Helmholtz(dev(other.k), other.h, **cfg(other))
+    ua, _ = H.solve(dev(other.b), tol=1e-6)
+    assert np.array_equal(uo, ua.cpu().numpy())
+    H.close()
+    S.close()
