@@ -111,7 +111,9 @@ typedef struct {
                             3: always clusters; 4: always the slice-distributed grid;
                             0: host-driven Arnoldi steps.  Every form runs with FP32
                             (HZ_PREC_MIXED) and FP64 vectors, except the tile-owned one
-                            (FP32 only) */
+                            (FP32 only).  With cslp_solver = HZ_CSLP_BICGSTAB, any non-zero
+                            value runs each Bi-CGSTAB solve as one persistent cooperative launch
+                            per right-hand side; 0 keeps the launch-per-step kernels */
   double reorth_eta;     /* classical Gram-Schmidt runs a second pass when the orthogonalised
                             vector keeps less than reorth_eta of its norm ("twice is enough"
                             test), default 0.1; 1 = always two passes, 0 = one pass */

@@ -359,7 +359,8 @@ int hz_cslp_bicgstab(hz_handle hp, int level, int dtype, const void* b, void* x,
   for (int q = 0; q < nrhs; ++q) H_->st[q] = RhsStats();
   int st = status_of(cudaMemsetAsync(x, 0, (size_t)nrhs * L.n * elem_bytes(dtype), H_->ctx.s), "hz_cslp_bicgstab");
   if (st) return st;
-  return cslp_bicgstab(H_, level, b, x, nrhs, iterations);
+  st = cslp_bicgstab(H_, level, b, x, nrhs, iterations);
+  return st ? st : collect_gmres_stats(H_, nrhs);
 }
 
 const char* hz_strerror(int s) {

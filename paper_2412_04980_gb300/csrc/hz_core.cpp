@@ -59,7 +59,7 @@ int status_of(cudaError_t e, const char* where) {
 
 static const char* kFamilies[F_COUNT] = {"level_op", "mg_down", "mg_up",  "defl_restrict", "defl_prolong",
                                          "multidot", "axpy",    "reduce", "dense",         "misc",
-                                         "gmres_persistent"};
+                                         "gmres_persistent", "bicgstab_persistent"};
 const char* family_name(int f) { return (f >= 0 && f < F_COUNT) ? kFamilies[f] : "?"; }
 
 // ---------------------------------------------------------------------------------- profiler
@@ -429,7 +429,9 @@ size_t estimate_bytes(const hz_grid& g, const hz_config& cfg) {
       maxnv = std::max(maxnv, (size_t)capg + 1);
       const bool bicg = cfg.cslp_solver == HZ_CSLP_BICGSTAB;
       const bool dev = cfg.device_gmres != 0 && !bicg;
-      if (bicg) total += 5 * bn * ep + sizeof(BicgState) * (size_t)nb + bicg_part_bytes(n, nb);
+      if (bicg)
+        total += std::max(5 * bn, 7 * n) * ep + sizeof(BicgState) * (size_t)nb + bicg_part_bytes(n, nb) +
+                 (cfg.device_gmres ? sizeof(BicgBarrier) + sizeof(double) * 8 * 1024 : 0);
       // upper bound: the cluster form keeps per-rhs workspace
       const bool clus = cluster_form_possible(cfg, n);
       const size_t gbr = (dev && !clus) ? n : bn;
@@ -581,11 +583,24 @@ int setup(Handle* h, const double* k_dev) {
       maxnv = std::max(maxnv, (size_t)L.capg + 1);
       if (cfg.cslp_solver == HZ_CSLP_BICGSTAB) {
         void* p;
-        CS(dalloc(h, &L.bcg, 5 * bn * ep));
+        // launch-per-step kernels: r, p, v, s, t batches; persistent form: r, two p, two v, s, t of
+        // one right-hand side at a time
+        CS(dalloc(h, &L.bcg, std::max(5 * bn, 7 * L.n) * ep));
         CS(dalloc(h, &p, sizeof(BicgState) * (size_t)nb));
         L.bst = (BicgState*)p;
+        CK(cudaMemsetAsync(L.bst, 0, sizeof(BicgState) * (size_t)nb, h->ctx.s));
         CS(dalloc(h, &p, bicg_part_bytes(L.n, nb)));
         L.bpart = (double*)p;
+        if (cfg.device_gmres) {
+          L.bgrid = std::min(bicg_persist_grid(L.dpre, L.R, L.nx, L.ny), 1024);
+          if (L.bgrid > 0) {
+            CS(dalloc(h, &p, sizeof(BicgBarrier)));
+            L.bbar = (BicgBarrier*)p;
+            CK(cudaMemsetAsync(L.bbar, 0, sizeof(BicgBarrier), h->ctx.s));
+            CS(dalloc(h, &p, sizeof(double) * 8 * (size_t)L.bgrid));
+            L.bgpart = (double*)p;
+          }
+        }
       } else if (cfg.device_gmres) {
         L.ggrid = std::min(gmres_max_grid(L.dpre, L.R, L.capg, L.n), gmres_grid_want(L.nx, L.ny));
         L.gcl = cluster_form_possible(cfg, L.n) ? gmres_cluster_size(L.dpre, L.R, L.capg) : 0;
@@ -650,7 +665,7 @@ int setup(Handle* h, const double* k_dev) {
   if (cfg.graphs) {
     for (int l = ml; l >= 3; --l) {
       const Level& L = h->lv[l - 1];
-      const bool dev_cslp = l <= cfg.mg_max_level || L.ggrid > 0 || L.gcl > 0 || L.gtiles > 0;
+      const bool dev_cslp = l <= cfg.mg_max_level || L.ggrid > 0 || L.gcl > 0 || L.gtiles > 0 || L.bgrid > 0;
       if (!(L.cap == 1 && L.m1cnt && dev_cslp)) break;
       h->graph_level = l;
     }
@@ -1166,6 +1181,31 @@ static int cycle(Handle* h, Scalars& sc, int dvec, int dx, size_t n, int nb, voi
 }
 
 int collect_gmres_stats(Handle* h, int nb) {
+  for (auto& L : h->lv) {  // persistent Bi-CGSTAB: iterations, non-finite ends, barrier timeouts
+    if (L.bgrid <= 0) continue;
+    std::vector<BicgState> bs(nb);
+    BicgBarrier bb;
+    CK(cudaMemcpyAsync(bs.data(), L.bst, sizeof(BicgState) * nb, cudaMemcpyDeviceToHost, h->ctx.s));
+    CK(cudaMemcpyAsync(&bb, L.bbar, sizeof(bb), cudaMemcpyDeviceToHost, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    double nonfinite = 0;
+    for (int q = 0; q < nb; ++q) {
+      h->st[q].cslp_it[L.l - 1] += (int)bs[q].total_its;
+      nonfinite += bs[q].nonfinite;
+      bs[q].total_its = 0;
+      bs[q].nonfinite = 0;
+    }
+    CK(cudaMemcpyAsync(L.bst, bs.data(), sizeof(BicgState) * nb, cudaMemcpyHostToDevice, h->ctx.s));
+    CK(cudaStreamSynchronize(h->ctx.s));
+    if (bb.err) {
+      set_error("a grid barrier of the persistent Bi-CGSTAB kernel exceeded its wait budget");
+      return HZ_ETIMEOUT;
+    }
+    if (nonfinite > 0) {
+      set_error("non-finite residual in the Bi-CGSTAB CSLP solve");
+      return HZ_EBREAKDOWN;
+    }
+  }
   for (auto& L : h->lv) {
     if (!L.m1cnt) continue;
     std::vector<int> cnt(2 * (size_t)nb);
@@ -1287,6 +1327,20 @@ int cslp_bicgstab(Handle* h, int l, const void* b, void* x, int nb, int* its_out
   Ctx& c = h->ctx;
   const int dt = L.dpre;
   const size_t n = L.n, bn = (size_t)nb * n, eb = elem_bytes(dt);
+  if (L.bgrid > 0) {  // persistent form: one cooperative launch per right-hand side, no host decision
+    const OpDesc Mq = L.opM(dt, h->cfg.beta1, h->cfg.beta2);
+    for (int q = 0; q < nb; ++q)
+      CK(launch_bicg_persist(c, op_of_rhs(Mq, q), dt, (const char*)b + (size_t)q * n * eb,
+                             (char*)x + (size_t)q * n * eb, L.bcg, L.bgpart, L.bst + q, L.bbar, L.capg,
+                             h->cfg.cslp_tol, L.bgrid));
+    if (its_out) {
+      std::vector<BicgState> bs(nb);
+      CK(cudaMemcpyAsync(bs.data(), L.bst, sizeof(BicgState) * nb, cudaMemcpyDeviceToHost, c.s));
+      CK(cudaStreamSynchronize(c.s));
+      for (int q = 0; q < nb; ++q) its_out[q] = (int)bs[q].its;
+    }
+    return HZ_OK;
+  }
   char* base = (char*)L.bcg;
   const size_t stride = (size_t)h->nbmax * n * eb;
   void *r = base, *p = base + stride, *v = base + 2 * stride, *s = base + 3 * stride, *t = base + 4 * stride;

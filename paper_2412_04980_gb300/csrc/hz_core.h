@@ -72,6 +72,9 @@ struct Level {
   void* bcg = nullptr;
   BicgState* bst = nullptr;
   double* bpart = nullptr;
+  int bgrid = 0;                             // persistent Bi-CGSTAB: CTAs of its cooperative grid (0: not used)
+  BicgBarrier* bbar = nullptr;               // its grid barrier
+  double* bgpart = nullptr;                  // its partial sums (8 per CTA)
   int ggrid = 0;                             // CTAs of the cooperative-grid form (0: host-driven GMRES)
   int gcl = 0;                               // CTAs per cluster of the cluster form (0: not used)
   bool gseq = false;                         // batches faster one right-hand side at a time (autotune)

@@ -26,6 +26,7 @@ enum Family {
   F_DENSE,          // dense coarsest multigrid solve
   F_MISC,           // conversions, copies
   F_GMRES,          // persistent whole-solve GMRES kernel
+  F_BICG,           // persistent whole-solve Bi-CGSTAB kernel
   F_COUNT
 };
 const char* family_name(int f);
@@ -168,8 +169,29 @@ struct BicgState {
   double bn2, rn2, tol2;  // ||b||^2, ||r||^2, (tol ||b||)^2
   double done;            // 0 running, 1 converged, 2 stopped by a breakdown
   double its;             // completed iterations
-  double pad[3];
+  double total_its;       // persistent form: iterations accumulated since the last statistics read
+  double nonfinite;       // persistent form: solves that ended on a non-finite residual since then
+  double pad;
 };
+// Grid barrier of the persistent Bi-CGSTAB kernel (device memory, zeroed; one per level).
+struct BicgBarrier {
+  unsigned count;  // arrivals (own 128-byte line)
+  unsigned pad0[31];
+  unsigned gen;    // generation, polled by the waiting CTAs (own line)
+  unsigned pad1[31];
+  int err;         // 1: a wait exceeded its clock budget
+  int pad2[31];
+};
+static_assert(sizeof(BicgBarrier) == 384, "BicgBarrier is three 128-byte lines");
+// Persistent form: CTAs of the cooperative grid for an nx x ny level (one tile of 32 x 16 per CTA
+// and round, at most the co-resident limit), 0 if it cannot be launched.
+int bicg_persist_grid(int dt, int R, int nx, int ny);
+// x += BiCGSTAB(M, b) for one right-hand side in one cooperative launch of `grid` CTAs (whole
+// solve, tolerance tol, at most cap iterations); work: 7 n elements of dtype dt (r, two p, two v,
+// s, t); part: 8 * grid doubles; st: this right-hand side's state (its, rn2, done, and the running
+// totals total_its / nonfinite); bar: the level's barrier.
+cudaError_t launch_bicg_persist(Ctx& c, const OpDesc& M, int dt, const void* b, void* x, void* work, double* part,
+                                BicgState* st, BicgBarrier* bar, int cap, double tol, int grid);
 int bicg_parts(size_t n);                  // CTAs per right-hand side of the reduction passes
 size_t bicg_part_bytes(size_t n, int nb);  // partial-sum buffer
 // rho = ||b||^2 and the stop test's reference (r = r_hat = b is the caller's copy)

