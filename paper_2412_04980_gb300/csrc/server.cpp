@@ -25,6 +25,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -151,7 +152,15 @@ int run_group(const std::vector<Req*>& grp, std::vector<int>& st_out) {
   int nb = 0;
   for (const Req* r : grp) nb += r->nrhs;
   // wavenumber field of every right-hand side (its request's field), right-hand sides in order
-  std::vector<double> k((size_t)nb * n), b((size_t)nb * n * 2);
+  std::vector<double> k, b;
+  try {
+    k.resize((size_t)nb * n);
+    b.resize((size_t)nb * n * 2);
+  } catch (const std::bad_alloc&) {
+    set_error("host memory for a merged solve could not be allocated");
+    st_out.assign(grp.size(), HZ_ENOMEM);
+    return HZ_ENOMEM;
+  }
   size_t o = 0;
   for (const Req* r : grp) {
     for (int q = 0; q < r->nrhs; ++q) {
@@ -354,15 +363,22 @@ int hz_submit(hz_server S, const hz_request* q, uint64_t* ticket) {
     set_error("hz_submit: known boundary type, config.max_rhs >= nrhs and tol in (0, 1) required");
     return HZ_EINVAL;
   }
-  auto r = std::make_unique<Req>();
+  std::unique_ptr<Req> r;
+  try {  // the host copies of k and b can be large: a failed allocation is the caller's HZ_ENOMEM
+    r = std::make_unique<Req>();
+    const size_t n = (size_t)q->grid.nx * q->grid.ny;
+    r->k.assign(q->k_host, q->k_host + n * (q->config.per_rhs_k ? (size_t)q->config.max_rhs : 1));
+    r->b.assign(q->b_host, q->b_host + 2 * n * q->nrhs);
+  } catch (const std::bad_alloc&) {
+    set_error("hz_submit: host memory for the request's copies of k and b could not be allocated");
+    return HZ_ENOMEM;
+  }
   r->grid = q->grid;
   r->cfg = q->config;
   r->nrhs = q->nrhs;
   r->tol = q->tol;
   const size_t n = (size_t)q->grid.nx * q->grid.ny;
-  const size_t nk = n * (q->config.per_rhs_k ? (size_t)q->config.max_rhs : 1);  // wavenumber fields
-  r->k.assign(q->k_host, q->k_host + nk);
-  r->b.assign(q->b_host, q->b_host + 2 * n * q->nrhs);
+  const size_t nk = r->k.size();  // wavenumber fields
   r->u_out = q->u_host;
   r->stats_out = q->stats_host;
   // footprint: handle workspace + the request's own device copies of k, b, u
