@@ -100,6 +100,26 @@ def test_estimate_bytes_host_only(L):
     # Bi-CGSTAB keeps five vectors per Krylov level in place of the persistent GMRES workspace
     assert e(513, levels=5, cslp_solver="bicgstab") != e(513, levels=5)
     assert L.hz_estimate_bytes(None, None, None) == hz.HZ_EINVAL
+    # multi-instance batches keep one wavenumber field per right-hand side on every level
+    # (FP64 + FP32 copies, 12 bytes per node) and one coarsest multigrid inverse per field
+    one, per = e(513, levels=3, max_rhs=4), e(513, levels=3, max_rhs=4, per_rhs_k=1)
+    nodes = 513 ** 2 + 257 ** 2 + 129 ** 2
+    assert per - one >= 3 * 12 * nodes
+    assert e(513, levels=3, max_rhs=1, per_rhs_k=1) == e(513, levels=3, max_rhs=1)
+
+
+def test_random_instances_inputs():
+    """The multi-instance workload generator: one field and one source per instance, fields
+    differ between instances (their own seeds), k_max h runs from 0.2 to 0.3."""
+    import math
+
+    import model_problems as mp
+    p = mp.random_instances(65, count=4, levels=2, negdef_from_level=4)
+    assert p.k.shape == (4, 65, 65) and p.b.shape == (4, 65, 65) and p.nrhs == 4
+    assert all(not (p.k[0] == p.k[r]).all() for r in range(1, 4))
+    khmax = [float(p.k[r].max()) * p.h for r in range(4)]
+    assert all(math.isclose(a, b, rel_tol=1e-12) for a, b in zip(khmax, [0.2, 0.2 + 0.1 / 3, 0.2 + 0.2 / 3, 0.3]))
+    assert all((p.b[r] != 0).sum() == 1 for r in range(4))
 
 
 def test_server_rejects_bad_arguments(L):
