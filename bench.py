@@ -454,6 +454,9 @@ def micro(args):
         H = hz.Helmholtz(k, p.h, levels=lev + (1 if args.micro in ("prolong", "restrict") else 0), precision=prec,
                          max_rhs=args.nrhs, restart=1, l2_maxit=1, negdef_from_level=p.negdef_from_level, **extra)
     else:
+        # the outer FGMRES basis is not used by the building blocks: keep it at one vector
+        if args.micro != "gmres":
+            extra.setdefault("restart", 1)
         H = hz.Helmholtz(k, p.h, levels=1, precision=prec, max_rhs=args.nrhs, **extra)
     ny_, nx_ = H.level_size(lev)
     shape = (ny_, nx_) if args.nrhs == 1 else (args.nrhs, ny_, nx_)
