@@ -97,6 +97,25 @@ struct UpSrc {
   }
 };
 
+// The radius-1 row of tile_op at tile cell (ox, oy) with the node's wavenumber k given (loaded by
+// the caller ahead of the tile barrier); same arithmetic as tile_op.
+template <typename T>
+__device__ __forceinline__ cx<T> op1_k(const TileView<T, 1>& t, const OpP<T>& P, int ox, int oy, T k) {
+  const int WX = t.WX();
+  const cx<T>* uc = t.U + (oy + 1) * WX + (ox + 1);
+  const cx<T> s = (uc[1] + uc[-1]) + (uc[WX] + uc[-WX]);
+  const T k2 = k * k;
+  const T dr = fma(-P.ksr, k2, T(4) * P.c);
+  const T di = P.ksi * k2;
+  const cx<T> u = *uc;
+  cx<T> v = mk<T>(fma(dr, u.re, fma(di, u.im, -P.c * s.re)), fma(dr, u.im, fma(-di, u.re, -P.c * s.im)));
+  if (P.srow) {
+    const int g = bsides(P, t.ox0 + ox, t.oy0 + oy);
+    if (g) v = (g == 1 ? T(0.5) : T(0.25)) * v;
+  }
+  return v;
+}
+
 // ---------------------------------------------------------------------------------------
 template <typename T, typename TI, typename TO, int R, int MODE>
 __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __restrict__ x,
@@ -110,28 +129,43 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __r
   if (MODE != 0) f += off;
   const int ox0 = blockIdx.x * OXT, oy0 = blockIdx.y * OYT;
   TileView<T, R> t = make_tile<T, R>(smem, OXT, OYT, ox0, oy0);
-  tile_fill<T, R>(t, P, GlobalSrc<T, TI>{x, P.nx});
-  auto emit = [&](int ox, int oy, cx<T> v) {
+  // fi: f at the node (modes 1 and 2)
+  auto emit = [&](int ox, int oy, cx<T> v, cx<T> fi) {
     const int gx = ox0 + ox, gy = oy0 + oy;
     const size_t i = (size_t)gy * P.nx + gx;
     cx<T> out;
     if (MODE == 0) {
       out = v;
     } else {
-      cx<T> r = cvt<T>(f[i]) - v;
+      cx<T> r = fi - v;
       if (MODE == 1) out = r;
       else out = t.u(ox + R, oy + R) + omega * cdiv(r, op_diag<T, R>(P, gx, gy));
     }
     y[i] = cvt<TO>(out);
   };
-  if (R == 1) {
+  if constexpr (R == 1) {
+    // the wavenumbers (and f) of this thread's outputs are loaded with the staged values, ahead
+    // of the tile barrier: one round of global-load latency per tile instead of two
+    constexpr int NP = OYT / BY;
+    T kr[NP];
+    cx<T> fr[NP];
 #pragma unroll
-    for (int p = 0; p < OYT / BY; ++p) {
+    for (int p = 0; p < NP; ++p) {
+      const int gx = ox0 + threadIdx.x, gy = oy0 + threadIdx.y + p * BY;
+      const bool in = gx < P.nx && gy < P.ny;
+      const size_t i = (size_t)gy * P.nx + gx;
+      kr[p] = in ? __ldg(P.k + i) : T(0);
+      fr[p] = (MODE != 0 && in) ? cvt<T>(f[i]) : mk<T>(T(0), T(0));
+    }
+    tile_fill<T, R>(t, P, GlobalSrc<T, TI>{x, P.nx});
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
       const int ox = threadIdx.x, oy = threadIdx.y + p * BY;
       if (ox0 + ox >= P.nx || oy0 + oy >= P.ny) continue;
-      emit(ox, oy, tile_op<T, R>(t, P, ox, oy));
+      emit(ox, oy, op1_k<T>(t, P, ox, oy, kr[p]), fr[p]);
     }
   } else {
+    tile_fill<T, R>(t, P, GlobalSrc<T, TI>{x, P.nx});
     const int tid = threadIdx.y * BX + threadIdx.x;
     constexpr int SEG = R == 2 ? 2 : 4;
     for (int it = tid; it < OXT * (OYT / SEG); it += BX * BY) {
@@ -140,7 +174,10 @@ __global__ void __launch_bounds__(BX* BY) k_level_op(OpP<T> P, const cx<TI>* __r
       if (ox0 + ox >= P.nx || cnt <= 0) continue;
       cx<T> v[4];
       tile_op_seg<T, R, SEG>(t, P, ox, sy, cnt, v);
-      for (int q = 0; q < cnt; ++q) emit(ox, sy + q, v[q]);
+      for (int q = 0; q < cnt; ++q) {
+        const size_t i = (size_t)(oy0 + sy + q) * P.nx + ox0 + ox;
+        emit(ox, sy + q, v[q], MODE != 0 ? cvt<T>(f[i]) : mk<T>(T(0), T(0)));
+      }
     }
   }
 }
