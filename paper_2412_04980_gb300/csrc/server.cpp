@@ -145,7 +145,8 @@ size_t group_bytes(const Req* r, int nb) {
 }
 
 // Run a group of compatible requests as one multi-instance solve on its own stream and handle.
-// Returns the status of the shared part (set-up, copies); per-request statuses go to st_out.
+// Returns the status of the shared part (set-up, copies); st_out always receives one status per
+// request of the group.
 int run_group(const std::vector<Req*>& grp, std::vector<int>& st_out) {
   const Req* r0 = grp[0];
   const size_t n = (size_t)r0->grid.nx * r0->grid.ny;
@@ -175,7 +176,10 @@ int run_group(const std::vector<Req*>& grp, std::vector<int>& st_out) {
   cfg.per_rhs_k = 1;
   cudaStream_t s = nullptr;
   int st = status_of(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
-  if (st) return st;
+  if (st) {
+    st_out.assign(grp.size(), st);
+    return st;
+  }
   void *kd = nullptr, *bd = nullptr, *ud = nullptr;
   hz_handle h = nullptr;
   std::vector<hz_stats> stats(nb);
@@ -277,6 +281,7 @@ void worker(hz_server_s* S) {
       sts[0] = run_request(S, r);
     } else {
       run_group(grp, sts);
+      sts.resize(grp.size(), HZ_ECUDA);  // one status per request, whatever path run_group took
     }
     const std::string msg = last_error_message();
     for (Req* q : grp) {
