@@ -42,9 +42,12 @@ requested residual on small grids; a level solved with as many iterations as
 unknowns (or to 1e-12) reproduces the preconditioner built on a dense inverse of
 that level; W-cycle and per-level-tolerance runs keep their call and iteration
 counts.  Iteration counts against the paper's tables: the three-level k = 100
-constant-wavenumber entries of Section 4.3.1 within one iteration; the four-
-and five-level entries differ by 2-3 iterations (setup details live in other
-papers), and the wedge geometry is synthetic: parity unpinned there.
+constant-wavenumber entries of Section 4.3.1 within one iteration; the pattern
+the paper draws from the k = 100 rows (five levels need no more outer
+iterations than four, three the fewest) holds, with every entry within three.
+The exact four- and five-level counts, 2-3 iterations above the paper (setup
+details live in other papers), and the wedge tables (synthetic geometry) stay
+parity unpinned.
 """
 from __future__ import annotations
 
